@@ -1,0 +1,188 @@
+/*
+ * pgdto.h -- C ABI of the GB300 (sm_103a) PGD-TO optimizer step.
+ *
+ * Method: projected gradient descent for topology optimisation with a regularised
+ * dual projection (arXiv 2511.13905).  One step (Alg. 3) computes
+ *   1. the step size alpha_t: the fallback alpha_fb / ||grad f||_inf at t = 0 or after
+ *      the warm-up when a constraint is violated by more than tol_N (Sec. 3.4), else the
+ *      spectral step of eq. final_alpha (BB1 when s^T y > eps_alpha, else eq. alpha);
+ *   2. the PR+ conjugate-gradient direction d_t of eq. CG;
+ *   3. the trial point z = x_t + omega alpha_t d_t;
+ *   4. the projection of z onto lo <= x <= hi and the rows linearised about x_t,
+ *      a_j^T x <= b_j with b_j = G_j - g_j(x_t) + a_j^T x_t (Sec. 3.2, eq. linearized),
+ *      regularised as in Sec. 3.2.3 and solved in its dual:
+ *        x(lam) = clip(z - A^T lam, lo, hi),  lam >= 0 (lam = -y of Thm 2),
+ *        r_j(lam) = a_j^T x(lam) - b_j - 2 lam_j / C <= 0,  lam_j r_j = 0   (eq. h);
+ *      single and independent rows by a per-row root search (Alg. 1, Sec. 3.2.2),
+ *      coupled rows by Alg. 2 (single-row candidates, then semismooth Newton on the
+ *      m x m Jacobian A D A^T + (2/C) I of eq. reg_jacobian);
+ *   5. x_{t+1} = x(lam*) and the ratio ||x_{t+1} - x_t|| / ||x_{t+1}||.
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are CUDA global-memory pointers valid in the current context;
+ *     FP32 arrays are dense, element i at offset i.  Pointers 16-byte aligned take the
+ *     vectorised path; others work but are slower.
+ *   - A holds the constraint gradients.  Dense layout (modes SINGLE, COUPLED): m rows
+ *     of n floats, row j at A + j*n.  Segmented layout (mode INDEPENDENT): one float
+ *     per variable, the coefficient of the row whose segment contains it.
+ *   - Work is enqueued on the handle's CUDA stream and runs asynchronously.  When an
+ *     info pointer is non-NULL the call waits for the stream and fills it.
+ *   - No entry point aborts, traps or prints.  Errors come back as pgdto_status;
+ *     device-side conditions (a grid barrier that timed out, non-finite input, an
+ *     iteration limit) are reported through the status returned by the call that
+ *     waits (info != NULL, pgdto_last_info, pgdto_poll).
+ *   - Caller-owned buffers must stay valid until the stream work completes.
+ */
+#ifndef PGDTO_H
+#define PGDTO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PGDTO_OK = 0,
+    PGDTO_ERR_ARG = 1,          /* invalid argument; nothing was enqueued */
+    PGDTO_ERR_OOM = 2,          /* device or pinned allocation failed */
+    PGDTO_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    PGDTO_ERR_NONFINITE = 4,    /* NaN or Inf in an input reduction; outputs not meaningful */
+    PGDTO_ERR_TIMEOUT = 5,      /* a device-side wait ran out of its budget; outputs not meaningful */
+    PGDTO_ERR_BUSY = 6,         /* server full or request still running */
+    PGDTO_NOT_CONVERGED = 7,    /* iteration limit reached; best iterate returned and flagged */
+    PGDTO_ERR_UNSUPPORTED = 8   /* combination not available on this device */
+} pgdto_status;
+
+typedef enum {
+    PGDTO_AUTO = 0,         /* SINGLE if m == 1, INDEPENDENT if segments given, else COUPLED */
+    PGDTO_SINGLE = 1,       /* one row (Alg. 1) */
+    PGDTO_INDEPENDENT = 2,  /* rows with disjoint supports (Sec. 3.2.2), segmented layout */
+    PGDTO_COUPLED = 3       /* general rows, m <= 4 (Alg. 2) */
+} pgdto_mode;
+
+/* Parameters; pgdto_params_default fills the paper's defaults. */
+typedef struct {
+    double C;               /* regularisation, 1e12 (Sec. 3.2.3, Sec. 3.5) */
+    double alpha_max;       /* step cap, 1e2 (Sec. 3.5) */
+    double alpha_fallback;  /* fallback step numerator, 0.2 (Sec. 3.3) */
+    double tol_B;           /* Alg. 1 tolerance, 1e-8; used relative to the bracket here */
+    double tol_N;           /* Alg. 2 / fallback tolerance, 1e-6 (Sec. 3.5) */
+    double omega;           /* global relaxation, 1.0 (Sec. 3.4) */
+    double eps_alpha;       /* BB1 threshold on s^T y, 1e-6 (Sec. 3.4) */
+    double c1;              /* Armijo constant of the Newton line search, 1e-4 (App. A.3.3) */
+    double c2;              /* curvature constant, 0.9 (App. A.3.3; recorded, not enforced) */
+    double tol_lambda;      /* relative width at which a dual root search stops, 1e-10 */
+    int t_warmup;           /* steps before the fallback rule applies, 50 (Sec. 3.4) */
+    int maxiter_newton;     /* Alg. 2 maxiter (the paper gives none), 50 */
+    int max_passes;         /* cap on root-search passes per projection, 64 */
+    int barrier_timeout_ms; /* budget of each device-side wait, 2000 */
+    pgdto_mode mode;        /* PGDTO_AUTO */
+} pgdto_params;
+
+/* Per-call report. */
+typedef struct {
+    double alpha;           /* step size taken (omega not applied) */
+    double beta;            /* PR+ coefficient */
+    double lambda[4];       /* dual solution, lam = -y >= 0 */
+    double b[4];            /* right-hand sides used, b_j = G_j - g_j(x_t) + a_j^T x_t */
+    double viol[4];         /* a_j^T x_{t+1} - b_j (regularised optimum: 2 lam_j / C) */
+    double rel_change;      /* ||x_{t+1} - x_t||_2 / ||x_{t+1}||_2 (Alg. 3 stopping ratio) */
+    double phi_inf;         /* max_j |Phi_j| at exit (coupled) or max_j |r_j| (root search) */
+    int passes;             /* passes over the projection data after the trial-point pass */
+    int newton_iters;       /* Alg. 2 stage 2 iterations */
+    int stage;              /* 0 root search, 1 Alg. 2 stage 1 accepted, 2 Newton */
+    int branch;             /* step-size rule: 0 fallback, 1 BB1, 2 Lipschitz */
+    int status;             /* pgdto_status of the device work */
+    int t;                  /* iteration index the step used */
+} pgdto_info;
+
+typedef struct pgdto_handle pgdto_handle;
+
+/* Fill *p with the defaults listed above.  PGDTO_ERR_ARG if p is NULL. */
+pgdto_status pgdto_params_default(pgdto_params* p);
+
+/*
+ * Create a handle for problems with n variables and m constraint rows.
+ *   n >= 1; 1 <= m <= 4; lo < hi, both finite.
+ *   seg_offsets: host array of m + 1 offsets, 0 = s_0 < s_1 < ... < s_m = n, for the
+ *     segmented INDEPENDENT layout (row j owns variables [s_j, s_{j+1})); NULL for
+ *     dense rows.  Copied; the caller keeps ownership.
+ *   params: NULL for defaults.  cuda_stream: the cudaStream_t to enqueue on (NULL =
+ *     legacy default stream).
+ * The handle owns the optimizer state (x_prev, g_prev, d_prev, the iteration index t)
+ * and a device workspace, about 4 n floats plus a fixed part.  Allocation failure
+ * returns PGDTO_ERR_OOM and leaves *h NULL.
+ */
+pgdto_status pgdto_create(pgdto_handle** h, int64_t n, int m, const int64_t* seg_offsets,
+                          float lo, float hi, const pgdto_params* params, void* cuda_stream);
+
+/* Free the handle after waiting for its stream.  NULL is ignored. */
+void pgdto_destroy(pgdto_handle* h);
+
+/* Replace the stream the handle enqueues on. */
+pgdto_status pgdto_set_stream(pgdto_handle* h, void* cuda_stream);
+
+/*
+ * Load optimizer state (checkpoint resume, or a prior step computed elsewhere):
+ * x_prev = rho_{t-1}, g_prev = grad f(rho_{t-1}), d_prev = d_{t-1}, device pointers of
+ * n floats, copied on the stream; NULL means zeros.  t is the iteration index the next
+ * pgdto_step takes (t = 0 starts Alg. 3 from scratch and ignores the arrays).
+ */
+pgdto_status pgdto_set_state(pgdto_handle* h, const float* x_prev, const float* g_prev,
+                             const float* d_prev, int t);
+
+/* Copy the state out to device buffers (each may be NULL); *t receives the next index. */
+pgdto_status pgdto_get_state(pgdto_handle* h, float* x_prev, float* g_prev, float* d_prev, int* t);
+
+/*
+ * One Alg. 3 iteration (steps 1-5 above) at index t = the handle's counter, which then
+ * advances.
+ *   x       device, n floats: rho_t on entry, rho_{t+1} on return (in place).
+ *   grad_f  device, n floats: grad f(rho_t).
+ *   A       device constraint gradients grad g_j(rho_t), layout of the handle's mode.
+ *   g_val   host, m doubles: g_j(rho_t) (for linear rows a_j^T rho_t).
+ *   G       host, m doubles: the bounds G_j.
+ *   info    NULL for an asynchronous call; otherwise filled after the stream is waited on.
+ * The state moves to (rho_t, grad f(rho_t), d_t).  Returns PGDTO_ERR_ARG for NULL
+ * pointers, or the device status when info is non-NULL.
+ */
+pgdto_status pgdto_step(pgdto_handle* h, float* x, const float* grad_f, const float* A,
+                        const double* g_val, const double* G, pgdto_info* info);
+
+/*
+ * The same step with HOST buffers (for callers whose sensitivities live on the host):
+ * x, grad_f and A are copied to handle-owned device buffers on the stream, the step
+ * runs, and rho_{t+1} is copied back into x.  Page-locked host memory gives the fastest
+ * copies.  Always waits for the stream before returning.
+ */
+pgdto_status pgdto_step_host(pgdto_handle* h, float* x, const float* grad_f, const float* A,
+                             const double* g_val, const double* G, pgdto_info* info);
+
+/*
+ * The regularised projection alone (Alg. 1 / Alg. 2 on given data, Sec. 3.2):
+ *   z       device, n floats, the point to project.
+ *   A       device, layout of the handle's mode.
+ *   b       host, m doubles, right-hand sides.
+ *   x_out   device, n floats: x(lam*) = clip(z - A^T lam*, lo, hi).  May alias z.
+ *   lambda_out  host, m doubles or NULL; written only when info is non-NULL or after
+ *           pgdto_last_info (it is read back from the device).
+ * Does not touch the optimizer state.
+ */
+pgdto_status pgdto_project(pgdto_handle* h, const float* z, const float* A, const double* b,
+                           float* x_out, double* lambda_out, pgdto_info* info);
+
+/* Wait for the handle's stream and report the last step or projection. */
+pgdto_status pgdto_last_info(pgdto_handle* h, pgdto_info* info, double* lambda_out);
+
+/* Number of the library's kernels launched by this handle so far (for accounting). */
+int64_t pgdto_kernel_launches(const pgdto_handle* h);
+
+/* Library version string, e.g. "pgdto-gb300 0.1 sm_103a". */
+const char* pgdto_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PGDTO_H */

@@ -1,0 +1,210 @@
+"""ctypes binding of libpgdto.so (include/pgdto.h), same names as the C ABI.
+
+Argument marshalling only: tensors are passed as raw device (or host) pointers, the
+CUDA stream as torch's current stream handle, and every computation runs in the
+library's kernels.  There is no CPU path: if the library is missing, ``load`` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpgdto.so")
+
+PGDTO_OK = 0
+PGDTO_ERR_ARG = 1
+PGDTO_ERR_OOM = 2
+PGDTO_ERR_CUDA = 3
+PGDTO_ERR_NONFINITE = 4
+PGDTO_ERR_TIMEOUT = 5
+PGDTO_ERR_BUSY = 6
+PGDTO_NOT_CONVERGED = 7
+PGDTO_ERR_UNSUPPORTED = 8
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NONFINITE", 5: "ERR_TIMEOUT",
+                6: "ERR_BUSY", 7: "NOT_CONVERGED", 8: "ERR_UNSUPPORTED"}
+
+MODES = {"auto": 0, "single": 1, "independent": 2, "coupled": 3}
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_double), ("alpha_max", ctypes.c_double), ("alpha_fallback", ctypes.c_double),
+                ("tol_B", ctypes.c_double), ("tol_N", ctypes.c_double), ("omega", ctypes.c_double),
+                ("eps_alpha", ctypes.c_double), ("c1", ctypes.c_double), ("c2", ctypes.c_double),
+                ("tol_lambda", ctypes.c_double), ("t_warmup", ctypes.c_int), ("maxiter_newton", ctypes.c_int),
+                ("max_passes", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int), ("mode", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("lambda_", ctypes.c_double * 4),
+                ("b", ctypes.c_double * 4), ("viol", ctypes.c_double * 4), ("rel_change", ctypes.c_double),
+                ("phi_inf", ctypes.c_double), ("passes", ctypes.c_int), ("newton_iters", ctypes.c_int),
+                ("stage", ctypes.c_int), ("branch", ctypes.c_int), ("status", ctypes.c_int), ("t", ctypes.c_int)]
+
+    def as_dict(self, m=4):
+        return {"alpha": self.alpha, "beta": self.beta, "lambda": list(self.lambda_)[:m], "b": list(self.b)[:m],
+                "viol": list(self.viol)[:m], "rel_change": self.rel_change, "phi_inf": self.phi_inf,
+                "passes": self.passes, "newton_iters": self.newton_iters, "stage": self.stage,
+                "branch": self.branch, "status": self.status, "t": self.t}
+
+
+class PgdtoError(RuntimeError):
+    def __init__(self, status, where):
+        super().__init__("%s returned %s" % (where, STATUS_NAMES.get(status, status)))
+        self.status = status
+
+
+_lib = None
+P = ctypes.c_void_p
+D = ctypes.POINTER(ctypes.c_double)
+
+
+def load(path=None):
+    """Load libpgdto.so once; raise if it is absent (build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libpgdto.so not found at %s: build it first (python -c 'import __graft_entry__ "
+                           "as g; g.build()'); there is no fallback" % path)
+    lib = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    sig = {
+        "pgdto_params_default": (ctypes.c_int, [ctypes.POINTER(Params)]),
+        "pgdto_create": (ctypes.c_int, [ctypes.POINTER(H), ctypes.c_int64, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.c_float, ctypes.c_float,
+                                        ctypes.POINTER(Params), P]),
+        "pgdto_destroy": (None, [H]),
+        "pgdto_set_stream": (ctypes.c_int, [H, P]),
+        "pgdto_set_state": (ctypes.c_int, [H, P, P, P, ctypes.c_int]),
+        "pgdto_get_state": (ctypes.c_int, [H, P, P, P, ctypes.POINTER(ctypes.c_int)]),
+        "pgdto_step": (ctypes.c_int, [H, P, P, P, D, D, ctypes.POINTER(Info)]),
+        "pgdto_step_host": (ctypes.c_int, [H, P, P, P, D, D, ctypes.POINTER(Info)]),
+        "pgdto_project": (ctypes.c_int, [H, P, P, D, P, D, ctypes.POINTER(Info)]),
+        "pgdto_last_info": (ctypes.c_int, [H, ctypes.POINTER(Info), D]),
+        "pgdto_kernel_launches": (ctypes.c_int64, [H]),
+        "pgdto_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def declared_symbols():
+    """Function names declared in include/pgdto.h (parsed from the header text)."""
+    import re
+    hdr = os.path.join(os.path.dirname(HERE), "include", "pgdto.h")
+    with open(hdr) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"\b(pgdto_[a-z_0-9]+)\s*\(", text)))
+
+
+def params_default(**overrides):
+    p = Params()
+    load().pgdto_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "mode" and isinstance(v, str):
+            v = MODES[v]
+        setattr(p, k, v)
+    return p
+
+
+def _dptr(t):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _darr(vals, m):
+    arr = (ctypes.c_double * max(m, 1))()
+    for j, v in enumerate(list(vals)[:m]):
+        arr[j] = float(v)
+    return arr
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Handle:
+    """Owns a pgdto_handle (optimizer state + device workspace) for fixed n, m, mode."""
+
+    def __init__(self, n, m, seg=None, lo=0.0, hi=1.0, params=None, stream=None, **param_overrides):
+        self.lib = load()
+        self.n, self.m = int(n), int(m)
+        p = params if params is not None else params_default(**param_overrides)
+        segarr = None
+        if seg is not None:
+            segarr = (ctypes.c_int64 * (self.m + 1))(*[int(s) for s in seg])
+        h = ctypes.c_void_p()
+        st = self.lib.pgdto_create(ctypes.byref(h), self.n, self.m, segarr, float(lo), float(hi),
+                                   ctypes.byref(p), _stream_ptr(stream))
+        if st != PGDTO_OK:
+            raise PgdtoError(st, "pgdto_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pgdto_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream=None):
+        return self.lib.pgdto_set_stream(self.h, _stream_ptr(stream))
+
+    def set_state(self, x_prev=None, g_prev=None, d_prev=None, t=0):
+        st = self.lib.pgdto_set_state(self.h, _dptr(x_prev), _dptr(g_prev), _dptr(d_prev), int(t))
+        if st != PGDTO_OK:
+            raise PgdtoError(st, "pgdto_set_state")
+
+    def get_state(self, x_prev=None, g_prev=None, d_prev=None):
+        t = ctypes.c_int()
+        st = self.lib.pgdto_get_state(self.h, _dptr(x_prev), _dptr(g_prev), _dptr(d_prev), ctypes.byref(t))
+        if st != PGDTO_OK:
+            raise PgdtoError(st, "pgdto_get_state")
+        return t.value
+
+    def step(self, x, grad_f, A, g_val, G, want_info=True):
+        """One optimizer step on device tensors; returns (status, Info or None)."""
+        info = Info() if want_info else None
+        st = self.lib.pgdto_step(self.h, _dptr(x), _dptr(grad_f), _dptr(A), _darr(g_val, self.m),
+                                 _darr(G, self.m), ctypes.byref(info) if info is not None else None)
+        return st, info
+
+    def step_host(self, x, grad_f, A, g_val, G):
+        """The step on host (CPU, ideally pinned) tensors; x is updated in place."""
+        info = Info()
+        st = self.lib.pgdto_step_host(self.h, _dptr(x), _dptr(grad_f), _dptr(A), _darr(g_val, self.m),
+                                      _darr(G, self.m), ctypes.byref(info))
+        return st, info
+
+    def project(self, z, A, b, x_out, want_info=True):
+        """Projection alone; returns (status, lambda list or None, Info or None)."""
+        info = Info() if want_info else None
+        lam = (ctypes.c_double * self.m)() if want_info else None
+        st = self.lib.pgdto_project(self.h, _dptr(z), _dptr(A), _darr(b, self.m), _dptr(x_out), lam,
+                                    ctypes.byref(info) if info is not None else None)
+        return st, (list(lam) if lam is not None else None), info
+
+    def last_info(self):
+        info = Info()
+        lam = (ctypes.c_double * self.m)()
+        st = self.lib.pgdto_last_info(self.h, ctypes.byref(info), lam)
+        return st, list(lam), info
+
+    def kernel_launches(self):
+        return int(self.lib.pgdto_kernel_launches(self.h))

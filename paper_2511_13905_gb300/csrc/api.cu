@@ -1,0 +1,399 @@
+// api.cu -- the C ABI of include/pgdto.h: argument checks, handle and workspace
+// ownership, state rotation, launches on the caller's stream, and the report read-back.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pgdto.h"
+#include "kernels.h"
+
+using namespace pgdto;
+
+struct pgdto_handle {
+    int64_t n;
+    int m;
+    pgdto_mode mode;
+    int64_t seg[kMaxRows + 1];
+    float lo, hi;
+    pgdto_params p;
+    cudaStream_t stream;
+    int device;
+    int blocks;               // cooperative grid size
+    long long timeout_cycles;
+    int t;                    // iteration index of the next step
+    // device buffers owned by the handle
+    float* x_prev;
+    float* g_prev;
+    float* d[2];              // d_{t-1} in d[cur], d_t written to d[1 - cur]
+    int cur;
+    float* z;
+    float* zlo;
+    void* work;               // SegWork or CoupledWork
+    size_t work_bytes;
+    size_t ctrl_bytes;
+    DeviceInfo* dev_info;
+    // host-buffer entry: device staging for x, grad f and A
+    float* hx;
+    float* hg;
+    float* hA;
+    int64_t a_len;            // floats in A for this mode
+    int64_t launches;
+    int last_was_project;
+};
+
+static pgdto_status cuda_fail(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) return PGDTO_ERR_OOM;
+    return PGDTO_ERR_CUDA;
+}
+
+#define CK(call)                                  \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+extern "C" pgdto_status pgdto_params_default(pgdto_params* p) {
+    if (!p) return PGDTO_ERR_ARG;
+    p->C = 1e12;
+    p->alpha_max = 1e2;
+    p->alpha_fallback = 0.2;
+    p->tol_B = 1e-8;
+    p->tol_N = 1e-6;
+    p->omega = 1.0;
+    p->eps_alpha = 1e-6;
+    p->c1 = 1e-4;
+    p->c2 = 0.9;
+    p->tol_lambda = 1e-10;
+    p->t_warmup = 50;
+    p->maxiter_newton = 50;
+    p->max_passes = 64;
+    p->barrier_timeout_ms = 2000;
+    p->mode = PGDTO_AUTO;
+    return PGDTO_OK;
+}
+
+extern "C" const char* pgdto_version(void) { return "pgdto-gb300 0.1 sm_103a"; }
+
+static void free_handle(pgdto_handle* h) {
+    if (!h) return;
+    cudaFree(h->x_prev);
+    cudaFree(h->g_prev);
+    cudaFree(h->d[0]);
+    cudaFree(h->d[1]);
+    cudaFree(h->z);
+    cudaFree(h->zlo);
+    cudaFree(h->work);
+    cudaFree(h->hx);
+    cudaFree(h->hg);
+    cudaFree(h->hA);
+    delete h;
+}
+
+static bool params_ok(const pgdto_params& p) {
+    return p.C > 0 && isfinite(p.C) && p.alpha_max > 0 && p.alpha_fallback > 0 && p.tol_N >= 0 && p.omega > 0 &&
+           p.eps_alpha >= 0 && p.tol_lambda > 0 && p.tol_lambda < 1e-2 && p.t_warmup >= 0 &&
+           p.maxiter_newton >= 1 && p.max_passes >= 1 && p.max_passes <= 100000 && p.barrier_timeout_ms >= 1;
+}
+
+extern "C" pgdto_status pgdto_create(pgdto_handle** out, int64_t n, int m, const int64_t* seg_offsets, float lo,
+                                     float hi, const pgdto_params* params, void* cuda_stream) {
+    if (!out) return PGDTO_ERR_ARG;
+    *out = nullptr;
+    if (n < 1 || m < 1 || m > kMaxRows) return PGDTO_ERR_ARG;
+    if (!(isfinite(lo) && isfinite(hi) && lo < hi)) return PGDTO_ERR_ARG;
+    pgdto_params p;
+    if (params) {
+        p = *params;
+    } else {
+        pgdto_params_default(&p);
+    }
+    if (!params_ok(p)) return PGDTO_ERR_ARG;
+    pgdto_mode mode = p.mode;
+    if (mode == PGDTO_AUTO) mode = (m == 1) ? PGDTO_SINGLE : (seg_offsets ? PGDTO_INDEPENDENT : PGDTO_COUPLED);
+    if (mode == PGDTO_SINGLE && m != 1) return PGDTO_ERR_ARG;
+    if (mode == PGDTO_INDEPENDENT && !seg_offsets) return PGDTO_ERR_ARG;
+    if (mode == PGDTO_COUPLED && seg_offsets) return PGDTO_ERR_ARG;
+    pgdto_handle* h = new pgdto_handle();
+    memset(h, 0, sizeof(*h));
+    h->n = n;
+    h->m = m;
+    h->mode = mode;
+    h->lo = lo;
+    h->hi = hi;
+    h->p = p;
+    h->stream = (cudaStream_t)cuda_stream;
+    if (mode == PGDTO_INDEPENDENT) {
+        if (seg_offsets[0] != 0 || seg_offsets[m] != n) {
+            delete h;
+            return PGDTO_ERR_ARG;
+        }
+        for (int j = 0; j < m; ++j)
+            if (seg_offsets[j + 1] <= seg_offsets[j]) {
+                delete h;
+                return PGDTO_ERR_ARG;
+            }
+        for (int j = 0; j <= m; ++j) h->seg[j] = seg_offsets[j];
+        h->a_len = n;
+    } else if (mode == PGDTO_SINGLE) {
+        h->seg[0] = 0;
+        h->seg[1] = n;
+        h->a_len = n;
+    } else {
+        h->a_len = n * (int64_t)m;
+    }
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e);
+    }
+    int clock_khz = 0;
+    cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, h->device);
+    if (clock_khz <= 0) clock_khz = 2000000;
+    h->timeout_cycles = (long long)clock_khz * (long long)p.barrier_timeout_ms;
+    if (mode == PGDTO_COUPLED) {
+        h->blocks = max_blocks_coupled(h->device);
+        h->work_bytes = coupled_work_bytes();
+        h->ctrl_bytes = coupled_work_ctrl_bytes();
+    } else {
+        h->blocks = max_blocks_seg(h->device);
+        h->work_bytes = seg_work_bytes();
+        h->ctrl_bytes = seg_work_ctrl_bytes();
+    }
+    if (h->blocks < 1) {
+        delete h;
+        return PGDTO_ERR_UNSUPPORTED;
+    }
+    const size_t nb = (size_t)n * sizeof(float);
+    if ((e = cudaMalloc(&h->x_prev, nb)) != cudaSuccess || (e = cudaMalloc(&h->g_prev, nb)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d[0], nb)) != cudaSuccess || (e = cudaMalloc(&h->d[1], nb)) != cudaSuccess ||
+        (e = cudaMalloc(&h->z, nb)) != cudaSuccess || (e = cudaMalloc(&h->zlo, nb)) != cudaSuccess ||
+        (e = cudaMalloc(&h->work, h->work_bytes)) != cudaSuccess) {
+        free_handle(h);
+        return cuda_fail(e);
+    }
+    h->dev_info = mode == PGDTO_COUPLED ? coupled_work_info((CoupledWork*)h->work) : seg_work_info((SegWork*)h->work);
+    if ((e = cudaMemsetAsync(h->work, 0, h->work_bytes, h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->x_prev, 0, nb, h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->g_prev, 0, nb, h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->d[0], 0, nb, h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->d[1], 0, nb, h->stream)) != cudaSuccess) {
+        free_handle(h);
+        return cuda_fail(e);
+    }
+    *out = h;
+    return PGDTO_OK;
+}
+
+extern "C" void pgdto_destroy(pgdto_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_handle(h);
+}
+
+extern "C" pgdto_status pgdto_set_stream(pgdto_handle* h, void* s) {
+    if (!h) return PGDTO_ERR_ARG;
+    h->stream = (cudaStream_t)s;
+    return PGDTO_OK;
+}
+
+extern "C" int64_t pgdto_kernel_launches(const pgdto_handle* h) { return h ? h->launches : -1; }
+
+extern "C" pgdto_status pgdto_set_state(pgdto_handle* h, const float* x_prev, const float* g_prev,
+                                        const float* d_prev, int t) {
+    if (!h || t < 0) return PGDTO_ERR_ARG;
+    const size_t nb = (size_t)h->n * sizeof(float);
+    float* dcur = h->d[h->cur];
+    if (x_prev) CK(cudaMemcpyAsync(h->x_prev, x_prev, nb, cudaMemcpyDeviceToDevice, h->stream));
+    else CK(cudaMemsetAsync(h->x_prev, 0, nb, h->stream));
+    if (g_prev) CK(cudaMemcpyAsync(h->g_prev, g_prev, nb, cudaMemcpyDeviceToDevice, h->stream));
+    else CK(cudaMemsetAsync(h->g_prev, 0, nb, h->stream));
+    if (d_prev) CK(cudaMemcpyAsync(dcur, d_prev, nb, cudaMemcpyDeviceToDevice, h->stream));
+    else CK(cudaMemsetAsync(dcur, 0, nb, h->stream));
+    h->t = t;
+    return PGDTO_OK;
+}
+
+extern "C" pgdto_status pgdto_get_state(pgdto_handle* h, float* x_prev, float* g_prev, float* d_prev, int* t) {
+    if (!h) return PGDTO_ERR_ARG;
+    const size_t nb = (size_t)h->n * sizeof(float);
+    if (x_prev) CK(cudaMemcpyAsync(x_prev, h->x_prev, nb, cudaMemcpyDeviceToDevice, h->stream));
+    if (g_prev) CK(cudaMemcpyAsync(g_prev, h->g_prev, nb, cudaMemcpyDeviceToDevice, h->stream));
+    if (d_prev) CK(cudaMemcpyAsync(d_prev, h->d[h->cur], nb, cudaMemcpyDeviceToDevice, h->stream));
+    if (t) *t = h->t;
+    return PGDTO_OK;
+}
+
+// Read the device report; clear the sticky device error once it has been reported.
+static pgdto_status read_info(pgdto_handle* h, pgdto_info* info, double* lambda_out) {
+    DeviceInfo di;
+    cudaError_t e = cudaMemcpyAsync(&di, h->dev_info, sizeof(di), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int ctrl[4];
+    e = cudaMemcpyAsync(ctrl, h->work, sizeof(ctrl), cudaMemcpyDeviceToHost, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int status = di.status;
+    const int sticky = ctrl[2];
+    const int aborted = ctrl[3];
+    if (aborted && status == PGDTO_OK) status = sticky ? sticky : PGDTO_ERR_TIMEOUT;
+    if (sticky != 0 || aborted) {
+        // errors are reported once; the next call starts from a clean control block
+        cudaMemsetAsync(h->work, 0, h->ctrl_bytes, h->stream);
+        cudaStreamSynchronize(h->stream);
+        if (status == PGDTO_OK) status = sticky;
+    }
+    if (info) {
+        static_assert(sizeof(DeviceInfo) == sizeof(pgdto_info), "report layouts differ");
+        memcpy(info, &di, sizeof(di));
+        info->status = status;
+    }
+    if (lambda_out)
+        for (int j = 0; j < h->m; ++j) lambda_out[j] = di.lambda[j];
+    return (pgdto_status)status;
+}
+
+extern "C" pgdto_status pgdto_last_info(pgdto_handle* h, pgdto_info* info, double* lambda_out) {
+    if (!h) return PGDTO_ERR_ARG;
+    return read_info(h, info, lambda_out);
+}
+
+static pgdto_status launch(pgdto_handle* h, bool proj, float* x, const float* g, const float* A, const double* bconst,
+                           const float* z_in, float* x_out, bool force_fallback) {
+    cudaError_t e;
+    if (h->mode == PGDTO_COUPLED) {
+        CoupledArgs a;
+        memset(&a, 0, sizeof(a));
+        a.n = h->n;
+        a.m = h->m;
+        a.t = h->t;
+        a.proj = proj ? 1 : 0;
+        a.force_fallback = force_fallback ? 1 : 0;
+        a.lo = h->lo;
+        a.hi = h->hi;
+        a.x = x;
+        a.g = g;
+        a.A = A;
+        a.x_prev = h->x_prev;
+        a.g_prev = h->g_prev;
+        a.d_prev = h->d[h->cur];
+        a.d_new = h->d[1 - h->cur];
+        a.z = h->z;
+        a.zlo = h->zlo;
+        a.z_in = z_in;
+        a.x_out = x_out;
+        for (int j = 0; j < h->m; ++j) a.bconst[j] = bconst[j];
+        a.C = h->p.C;
+        a.alpha_max = h->p.alpha_max;
+        a.alpha_fb = h->p.alpha_fallback;
+        a.eps_alpha = h->p.eps_alpha;
+        a.omega = h->p.omega;
+        a.tol_lambda = h->p.tol_lambda;
+        a.tol_N = h->p.tol_N;
+        a.c1 = h->p.c1;
+        a.max_passes = h->p.max_passes;
+        a.maxiter_newton = h->p.maxiter_newton;
+        a.timeout_cycles = h->timeout_cycles;
+        a.ws = (CoupledWork*)h->work;
+        e = launch_coupled(a, h->blocks, h->stream);
+    } else {
+        SegArgs a;
+        memset(&a, 0, sizeof(a));
+        a.n = h->n;
+        a.nrows = h->m;
+        a.t = h->t;
+        a.proj = proj ? 1 : 0;
+        a.force_fallback = force_fallback ? 1 : 0;
+        for (int j = 0; j <= h->m; ++j) a.seg[j] = h->seg[j];
+        a.lo = h->lo;
+        a.hi = h->hi;
+        a.x = x;
+        a.g = g;
+        a.A = A;
+        a.x_prev = h->x_prev;
+        a.g_prev = h->g_prev;
+        a.d_prev = h->d[h->cur];
+        a.d_new = h->d[1 - h->cur];
+        a.z = h->z;
+        a.zlo = h->zlo;
+        a.z_in = z_in;
+        a.x_out = x_out;
+        for (int j = 0; j < h->m; ++j) a.bconst[j] = bconst[j];
+        a.C = h->p.C;
+        a.alpha_max = h->p.alpha_max;
+        a.alpha_fb = h->p.alpha_fallback;
+        a.eps_alpha = h->p.eps_alpha;
+        a.omega = h->p.omega;
+        a.tol_lambda = h->p.tol_lambda;
+        a.max_passes = h->p.max_passes;
+        a.timeout_cycles = h->timeout_cycles;
+        a.ws = (SegWork*)h->work;
+        e = launch_seg(a, h->blocks, h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->launches += 1;
+    return PGDTO_OK;
+}
+
+extern "C" pgdto_status pgdto_step(pgdto_handle* h, float* x, const float* grad_f, const float* A,
+                                   const double* g_val, const double* G, pgdto_info* info) {
+    if (!h || !x || !grad_f || !A || !g_val || !G) return PGDTO_ERR_ARG;
+    double bconst[kMaxRows] = {0, 0, 0, 0};
+    double viol = 0.0;
+    for (int j = 0; j < h->m; ++j) {
+        if (!(isfinite(g_val[j]) && isfinite(G[j]))) return PGDTO_ERR_NONFINITE;
+        bconst[j] = G[j] - g_val[j];
+        viol = fmax(viol, g_val[j] - G[j]);
+    }
+    // Alg. 3: fallback step at t = 0, or after the warm-up when a constraint is violated
+    const bool fallback = h->t == 0 || (h->t >= h->p.t_warmup && viol > h->p.tol_N);
+    pgdto_status s = launch(h, false, x, grad_f, A, bconst, nullptr, nullptr, fallback);
+    if (s != PGDTO_OK) return s;
+    h->cur = 1 - h->cur;  // d_t becomes d_prev
+    h->t += 1;
+    h->last_was_project = 0;
+    if (info) return read_info(h, info, nullptr);
+    return PGDTO_OK;
+}
+
+extern "C" pgdto_status pgdto_step_host(pgdto_handle* h, float* x, const float* grad_f, const float* A,
+                                        const double* g_val, const double* G, pgdto_info* info) {
+    if (!h || !x || !grad_f || !A || !g_val || !G) return PGDTO_ERR_ARG;
+    const size_t nb = (size_t)h->n * sizeof(float);
+    const size_t ab = (size_t)h->a_len * sizeof(float);
+    if (!h->hx) {
+        cudaError_t e;
+        if ((e = cudaMalloc(&h->hx, nb)) != cudaSuccess || (e = cudaMalloc(&h->hg, nb)) != cudaSuccess ||
+            (e = cudaMalloc(&h->hA, ab)) != cudaSuccess) {
+            cudaFree(h->hx);
+            cudaFree(h->hg);
+            cudaFree(h->hA);
+            h->hx = h->hg = h->hA = nullptr;
+            return cuda_fail(e);
+        }
+    }
+    CK(cudaMemcpyAsync(h->hx, x, nb, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->hg, grad_f, nb, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->hA, A, ab, cudaMemcpyHostToDevice, h->stream));
+    pgdto_status s = pgdto_step(h, h->hx, h->hg, h->hA, g_val, G, nullptr);
+    if (s != PGDTO_OK) return s;
+    CK(cudaMemcpyAsync(x, h->hx, nb, cudaMemcpyDeviceToHost, h->stream));
+    return read_info(h, info, nullptr);
+}
+
+extern "C" pgdto_status pgdto_project(pgdto_handle* h, const float* z, const float* A, const double* b, float* x_out,
+                                      double* lambda_out, pgdto_info* info) {
+    if (!h || !z || !A || !b || !x_out) return PGDTO_ERR_ARG;
+    double bb[kMaxRows] = {0, 0, 0, 0};
+    for (int j = 0; j < h->m; ++j) {
+        if (!isfinite(b[j])) return PGDTO_ERR_NONFINITE;
+        bb[j] = b[j];
+    }
+    pgdto_status s = launch(h, true, nullptr, nullptr, A, bb, z, x_out, false);
+    if (s != PGDTO_OK) return s;
+    h->last_was_project = 1;
+    if (info || lambda_out) return read_info(h, info, lambda_out);
+    return PGDTO_OK;
+}

@@ -1,0 +1,253 @@
+// dev_common.cuh -- device building blocks shared by the PGD-TO kernels (sm_103a).
+//
+//  * double-float ("DF") accumulation: a value kept as an unevaluated sum hi + lo of two
+//    floats, combined with Knuth's TwoSum and Dekker's FastTwoSum (error-free transforms),
+//    so reductions over millions of FP32 terms keep ~44 bits without FP64 arithmetic
+//    (FP64 throughput is a small fraction of FP32 on this part);
+//  * warp / block reductions of DF values;
+//  * a grid-wide "last block reduces" step: every block writes its partial sums, arrives
+//    on a counter, and the last block to arrive reduces all partials in a fixed order,
+//    runs the scalar update and releases the others.  Waits are bounded: a block that has
+//    waited longer than its budget records PGDTO_ERR_TIMEOUT, raises an abort flag and
+//    returns, so a fault elsewhere never hangs the GPU.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pgdto {
+
+constexpr int kThreads = 512;
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxBlocks = 1024;
+constexpr int kMaxVals = 136;   // DF values per grid reduction (4 rows x 2 x 16 points + spare)
+constexpr int kMaxMax = 8;      // float max values per grid reduction
+
+// status codes shared with include/pgdto.h
+enum : int { kOk = 0, kErrNonfinite = 4, kErrTimeout = 5, kNotConverged = 7 };
+
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_zero() { return DF{0.0f, 0.0f}; }
+
+// Knuth TwoSum: s = fl(a + b), e = (a + b) - s exactly.
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return DF{s, e};
+}
+
+// Dekker FastTwoSum, valid when |a| >= |b| (or a == 0).
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return DF{s, e};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF s = two_sum(a.hi, b.hi);
+    float lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return fast_two_sum(s.hi, lo);
+}
+
+__device__ __forceinline__ DF df_add_f(DF a, float b) {
+    DF s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
+
+// Split a double into hi + lo floats (hi = nearest float, lo = nearest float of the rest).
+__device__ __host__ __forceinline__ void split_double(double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+__device__ __forceinline__ DF warp_reduce_df(DF v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        DF u;
+        u.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        u.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = df_add(v, u);
+    }
+    return v;
+}
+
+__device__ __forceinline__ float warp_reduce_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// ------------------------------------------------------------------ memory ordering
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+    return *reinterpret_cast<const volatile int*>(p);
+}
+
+// ------------------------------------------------------------------ grid control block
+
+struct GridCtrl {
+    unsigned count;    // arrivals in the current round
+    unsigned gen;      // round counter, bumped by the last block
+    int status;        // sticky pgdto_status of device work
+    int abort;         // raised by a block that gave up; every wait then returns
+    unsigned long long launches;  // kernels that ran to completion (diagnostics)
+    int pad[10];
+};
+
+// Partial sums of one grid reduction: DF values (SoA over blocks) and float maxima.
+struct Partials {
+    float2 v[kMaxVals][kMaxBlocks];
+    float mx[kMaxMax][kMaxBlocks];
+};
+
+// Per-block scratch for reductions (shared memory).
+struct BlockScratch {
+    DF warp_vals[kMaxVals][kWarps];
+    float warp_max[kMaxMax][kWarps];
+    DF tot[kMaxVals];
+    float totmax[kMaxMax];
+    int flag;
+    unsigned gen;
+};
+
+// Reduce NV per-thread DF values and NM per-thread maxima (mx may be null when NM == 0);
+// the block totals land in sc.tot[voff + i] and sc.totmax[moff + i].
+template <int NV, int NM>
+__device__ __forceinline__ void block_reduce(const DF (&v)[NV], const float* mx, BlockScratch& sc, int voff = 0,
+                                             int moff = 0) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        DF r = warp_reduce_df(v[i]);
+        if (lane == 0) sc.warp_vals[i][warp] = r;
+    }
+#pragma unroll
+    for (int i = 0; i < NM; ++i) {
+        float r = warp_reduce_max(mx[i]);
+        if (lane == 0) sc.warp_max[i][warp] = r;
+    }
+    __syncthreads();
+    for (int i = warp; i < NV; i += kWarps) {
+        DF r = lane < kWarps ? sc.warp_vals[i][lane] : df_zero();
+        r = warp_reduce_df(r);
+        if (lane == 0) sc.tot[voff + i] = r;
+    }
+    for (int i = warp; i < NM; i += kWarps) {
+        float r = lane < kWarps ? sc.warp_max[i][lane] : -INFINITY;
+        r = warp_reduce_max(r);
+        if (lane == 0) sc.totmax[moff + i] = r;
+    }
+    __syncthreads();
+}
+
+// Grid-wide reduction of sc.tot[0..nv) / sc.totmax[0..nm) followed by a scalar update.
+// Every block calls it with its block totals in sc.  The last block to arrive reduces all
+// partials in block order (deterministic), calls update(sc) with the grid totals in
+// sc.tot / sc.totmax on thread 0, and releases the others.  Returns false if the wait
+// was abandoned (timeout or abort); the caller must then return.
+template <class Update>
+__device__ bool grid_reduce_update(GridCtrl* ctrl, Partials* part, BlockScratch& sc, int nv, int nm,
+                                   long long timeout_cycles, Update&& update) {
+    const int tid = threadIdx.x;
+    const int nb = gridDim.x;
+    for (int i = tid; i < nv; i += blockDim.x) part->v[i][blockIdx.x] = make_float2(sc.tot[i].hi, sc.tot[i].lo);
+    for (int i = tid; i < nm; i += blockDim.x) part->mx[i][blockIdx.x] = sc.totmax[i];
+    __syncthreads();
+    if (tid == 0) {
+        unsigned g = ld_acquire_u32(&ctrl->gen);
+        __threadfence();
+        unsigned old = atomicAdd(&ctrl->count, 1u);
+        sc.gen = g;
+        sc.flag = (old == (unsigned)(nb - 1)) ? 1 : 0;
+    }
+    __syncthreads();
+    if (sc.flag) {
+        __threadfence();
+        const int lane = tid & 31, warp = tid >> 5;
+        for (int i = warp; i < nv; i += kWarps) {
+            DF acc = df_zero();
+            for (int b = lane; b < nb; b += 32) {
+                float2 p = __ldcg(&part->v[i][b]);
+                acc = df_add(acc, DF{p.x, p.y});
+            }
+            acc = warp_reduce_df(acc);
+            if (lane == 0) sc.tot[i] = acc;
+        }
+        for (int i = warp; i < nm; i += kWarps) {
+            float acc = -INFINITY;
+            for (int b = lane; b < nb; b += 32) acc = fmaxf(acc, __ldcg(&part->mx[i][b]));
+            acc = warp_reduce_max(acc);
+            if (lane == 0) sc.totmax[i] = acc;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            update(sc);
+            __threadfence();
+            ctrl->count = 0u;
+            __threadfence();
+            st_release_u32(&ctrl->gen, sc.gen + 1u);
+        }
+        __syncthreads();
+        return true;
+    }
+    if (tid == 0) {
+        long long t0 = clock64();
+        int ok = 1;
+        unsigned spins = 0;
+        while (ld_acquire_u32(&ctrl->gen) == sc.gen) {
+            if (ld_volatile_i32(&ctrl->abort)) {
+                ok = 0;
+                break;
+            }
+            if (((++spins) & 63u) == 0u && clock64() - t0 > timeout_cycles) {
+                atomicExch(&ctrl->status, kErrTimeout);
+                atomicExch(&ctrl->abort, 1);
+                ok = 0;
+                break;
+            }
+        }
+        sc.flag = ok;
+    }
+    __syncthreads();
+    return sc.flag != 0;
+}
+
+// Copy a small struct written by the last block (global) into shared memory through L2.
+template <class T>
+__device__ __forceinline__ void load_cg(T& dst, const T* src) {
+    static_assert(sizeof(T) % 4 == 0, "word-sized struct expected");
+    const unsigned* s = reinterpret_cast<const unsigned*>(src);
+    unsigned* d = reinterpret_cast<unsigned*>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x) d[i] = __ldcg(s + i);
+    __syncthreads();
+}
+
+// Contiguous chunk [cb, ce) of [s, e) owned by block `blk` of `nb`, multiple of 4 long.
+__device__ __forceinline__ void block_chunk(int64_t s, int64_t e, int blk, int nb, int64_t& cb, int64_t& ce) {
+    int64_t len = e - s;
+    int64_t per = (len + nb - 1) / nb;
+    per = (per + 3) & ~int64_t(3);
+    if (per < 4) per = 4;
+    cb = s + per * blk;
+    ce = cb + per;
+    if (cb > e) cb = e;
+    if (ce > e) ce = e;
+}
+
+}  // namespace pgdto

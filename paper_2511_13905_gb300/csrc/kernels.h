@@ -1,0 +1,90 @@
+// kernels.h -- host-visible kernel argument blocks and launch entry points (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pgdto {
+
+constexpr int kMaxRows = 4;
+
+// Report written by the last block of a step or projection; same layout as pgdto_info.
+struct DeviceInfo {
+    double alpha, beta;
+    double lambda[kMaxRows], b[kMaxRows], viol[kMaxRows];
+    double rel_change, phi_inf;
+    int passes, newton_iters, stage, branch, status, t;
+};
+
+struct SegWork;      // single / independent rows workspace (seg_kernels.cu)
+struct CoupledWork;  // coupled rows workspace (coupled_kernels.cu)
+
+// Arguments of the fused step / projection kernel for single and independent rows.
+struct SegArgs {
+    int64_t n;
+    int nrows;
+    int t;
+    int proj;            // 1: projection only (z_in, b given), 0: full step
+    int force_fallback;  // Alg. 3 fallback rule decided on the host (t == 0 or late violation)
+    int64_t seg[kMaxRows + 1];
+    float lo, hi;
+    float* x;            // step: rho_t in, rho_{t+1} out
+    const float* g;      // grad f(rho_t)
+    const float* A;      // one coefficient per variable
+    float* x_prev;       // state, overwritten with rho_t
+    float* g_prev;       // state, overwritten with grad f(rho_t)
+    const float* d_prev; // state d_{t-1}
+    float* d_new;        // d_t (the other buffer of the pair)
+    float* z;            // trial point scratch, rounded to FP32 (z_hi)
+    float* zlo;          // rounding residual of the trial point: z = z_hi + z_lo exactly enough
+    const float* z_in;   // projection input
+    float* x_out;        // projection output
+    double bconst[kMaxRows];  // step: G_j - g_j(x_t); projection: b_j
+    double C, alpha_max, alpha_fb, eps_alpha, omega, tol_lambda;
+    int max_passes;
+    long long timeout_cycles;
+    SegWork* ws;
+};
+
+// Arguments of the coupled-rows (Alg. 2) step / projection kernel.
+struct CoupledArgs {
+    int64_t n;
+    int m;
+    int t;
+    int proj;
+    int force_fallback;
+    float lo, hi;
+    float* x;
+    const float* g;
+    const float* A;      // m rows of n floats
+    float* x_prev;
+    float* g_prev;
+    const float* d_prev;
+    float* d_new;
+    float* z;
+    float* zlo;
+    const float* z_in;
+    float* x_out;
+    double bconst[kMaxRows];
+    double C, alpha_max, alpha_fb, eps_alpha, omega, tol_lambda, tol_N, c1;
+    int max_passes, maxiter_newton;
+    long long timeout_cycles;
+    CoupledWork* ws;
+};
+
+// Workspace management (sizes in bytes, device-resident, zero-initialised by the host).
+size_t seg_work_bytes();
+size_t coupled_work_bytes();
+DeviceInfo* seg_work_info(SegWork* ws);
+DeviceInfo* coupled_work_info(CoupledWork* ws);
+size_t seg_work_ctrl_bytes();       // leading GridCtrl block to clear after an error
+size_t coupled_work_ctrl_bytes();
+
+// Launch helpers: cooperative launch on `stream` with `blocks` CTAs of kThreads threads.
+cudaError_t launch_seg(const SegArgs& a, int blocks, cudaStream_t stream);
+cudaError_t launch_coupled(const CoupledArgs& a, int blocks, cudaStream_t stream);
+// Largest co-resident grid for each kernel on the current device.
+int max_blocks_seg(int device);
+int max_blocks_coupled(int device);
+
+}  // namespace pgdto

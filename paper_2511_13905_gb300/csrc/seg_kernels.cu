@@ -1,0 +1,766 @@
+// seg_kernels.cu -- fused PGD-TO step / projection for one row or independent rows.
+//
+// One cooperative launch runs the whole step (Alg. 3) for m = 1 (Alg. 1) and for rows
+// with disjoint supports (Sec. 3.2.2), each row owning a contiguous segment of x:
+//
+//   phase A  one pass over x, x_prev, g, g_prev: s^T s, s^T y, y^T y, g^T y, ||g_prev||^2,
+//            ||g||_inf  ->  alpha (eq. final_alpha / eq. alpha / fallback) and beta (eq. CG)
+//   phase B  one pass: d = -g + beta d_prev, z = x + omega alpha d; writes d, z and the
+//            state copies; per row a^T x_t (for b), r(0) (Alg. 1 feasibility test), the
+//            free-set curvature at 0 and the saturation bound of Alg. 1's bracket
+//   phase C  root-search passes over z and a: r(lam_k) = a^T clip(z - lam_k a) - b - 2 lam_k/C
+//            and its slope at K points per pass; the last block moves the bracket, stops
+//            when both ends lie on one linear piece, and picks the next points
+//   phase D  one pass: x_{t+1} = clip(x + c(beta d_prev - g) - lam a) evaluated in
+//            double-float arithmetic, a^T x_{t+1}, ||x_{t+1} - x_t||^2, ||x_{t+1}||^2
+//
+// The projection-only entry runs B (without the step part), C and D on a given z.
+// Each phase ends in one grid-wide reduction (dev_common.cuh).
+#include <float.h>
+#include <math.h>
+
+#include "dev_common.cuh"
+#include "kernels.h"
+
+namespace pgdto {
+
+constexpr int K = 8;           // trial points per root-search pass
+constexpr int kFoldEvery = 8;  // float4 groups accumulated in FP32 before folding into DF
+
+struct RowState {
+    double b, L, rL, SL, H, rH, SH, lam, rlast;
+    int active, passes, how, pad;
+};
+
+struct SegBcast {
+    double alpha, beta, c;
+    float c_hi, c_lo, beta_hi, beta_lo;
+    int branch, any_active, status, pad;
+    float pts[kMaxRows][K];
+    int active[kMaxRows];
+    float lam_hi[kMaxRows], lam_lo[kMaxRows];
+};
+
+struct SegWork {
+    GridCtrl ctrl;
+    SegBcast bc;
+    RowState rows[kMaxRows];
+    DeviceInfo info;
+    Partials part;
+};
+
+size_t seg_work_bytes() { return sizeof(SegWork); }
+size_t seg_work_ctrl_bytes() { return sizeof(GridCtrl); }
+DeviceInfo* seg_work_info(SegWork* ws) { return &ws->info; }
+
+__device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
+
+__device__ __forceinline__ bool all_finite(const BlockScratch& sc, int nv) {
+    for (int i = 0; i < nv; ++i)
+        if (!isfinite(sc.tot[i].hi)) return false;
+    return true;
+}
+
+// ----------------------------------------------------------------------- scalar updates
+
+// Step size and PR+ coefficient (Alg. 3; eq. final_alpha, eq. alpha, eq. CG).
+__device__ void update_step_scalars(const SegArgs& a, const BlockScratch& sc, SegWork* ws) {
+    volatile SegBcast* bc = &ws->bc;
+    const double ss = df_to_double(sc.tot[0]), sy = df_to_double(sc.tot[1]), yy = df_to_double(sc.tot[2]);
+    const double gy = df_to_double(sc.tot[3]), pp = df_to_double(sc.tot[4]), gg = df_to_double(sc.tot[5]);
+    const double gmax = (double)sc.totmax[0];
+    int status = kOk;
+    if (!(isfinite(ss) && isfinite(sy) && isfinite(yy) && isfinite(gy) && isfinite(pp) && isfinite(gg)))
+        status = kErrNonfinite;
+    const double fb = gmax > 0.0 ? fmin(a.alpha_max, a.alpha_fb / gmax) : a.alpha_max;
+    double alpha;
+    int branch;
+    if (a.force_fallback || a.t == 0 || ss == 0.0) {
+        alpha = fb;
+        branch = 0;
+    } else {
+        const double lip = yy == 0.0 ? INFINITY : sqrt(ss / yy);
+        if (sy > a.eps_alpha) {
+            alpha = fmin(fmin(ss / sy, 2.0 * lip), a.alpha_max);
+            branch = 1;
+        } else {
+            alpha = fmin(lip, a.alpha_max);
+            branch = 2;
+        }
+    }
+    const double beta = (a.t == 0 || pp == 0.0) ? 0.0 : fmax(gy / pp, 0.0);
+    const double c = a.omega * alpha;
+    float h, l;
+    bc->alpha = alpha;
+    bc->beta = beta;
+    bc->c = c;
+    split_double(c, h, l);
+    bc->c_hi = h;
+    bc->c_lo = l;
+    split_double(beta, h, l);
+    bc->beta_hi = h;
+    bc->beta_lo = l;
+    bc->branch = branch;
+    bc->status = status;
+    volatile DeviceInfo* inf = &ws->info;
+    inf->alpha = alpha;
+    inf->beta = beta;
+    inf->branch = branch;
+    inf->t = a.t;
+}
+
+__device__ __forceinline__ double float_ulp(double v) {
+    float f = (float)fabs(v);
+    return (double)nextafterf(f, INFINITY) - (double)f;
+}
+
+__device__ void sort8(float* p) {
+    for (int i = 1; i < K; ++i) {
+        float v = p[i];
+        int j = i - 1;
+        while (j >= 0 && p[j] > v) {
+            p[j + 1] = p[j];
+            --j;
+        }
+        p[j + 1] = v;
+    }
+}
+
+// Next K trial points inside (L, H): Newton from both ends of the bracket (exact when the
+// bracket is one linear piece), the secant point, and a uniform fill that guarantees the
+// bracket shrinks by at least a factor 6 per pass.
+__device__ void choose_points(const RowState& r, volatile float* out) {
+    const double L = r.L, H = r.H, w = H - L;
+    double c[K];
+    c[0] = L + r.rL / r.SL;
+    c[1] = H + r.rH / r.SH;
+    c[2] = L + r.rL * w / (r.rL - r.rH);
+    for (int q = 1; q <= 5; ++q) c[2 + q] = L + w * (double)q / 6.0;
+    float p[K];
+    for (int k = 0; k < K; ++k) {
+        double v = c[k];
+        if (!(v > L && v < H)) v = L + w * ((double)k + 0.5) / (double)K;
+        float f = (float)v;
+        if (!((double)f > L && (double)f < H)) {
+            f = (float)(0.5 * (L + H));
+            if (!((double)f > L && (double)f < H)) f = (float)H;
+        }
+        p[k] = f;
+    }
+    sort8(p);
+    for (int k = 0; k < K; ++k) out[k] = p[k];
+}
+
+__device__ void finish_row(RowState& r, double lam, int how, volatile SegBcast* bc, int j) {
+    r.lam = lam;
+    r.active = 0;
+    r.how = how;
+    float h, l;
+    split_double(lam, h, l);
+    bc->lam_hi[j] = h;
+    bc->lam_lo[j] = l;
+    bc->active[j] = 0;
+}
+
+// After phase B: feasibility at lam = 0, bracket [0, H] (Alg. 1), closed form when the row
+// is violated even with every variable at its row-minimising bound (regularised root).
+__device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, SegWork* ws) {
+    volatile SegBcast* bc = &ws->bc;
+    volatile RowState* rows = ws->rows;
+    const int nr = a.nrows;
+    int any = 0;
+    int status = a.proj ? kOk : bc->status;
+    for (int j = 0; j < nr; ++j) {
+        const double ax = a.proj ? 0.0 : df_to_double(sc.tot[4 * j + 0]);
+        const double r0s = df_to_double(sc.tot[4 * j + 1]);
+        const double sf = df_to_double(sc.tot[4 * j + 2]);
+        const double smin = df_to_double(sc.tot[4 * j + 3]);
+        const double lsat = (double)sc.totmax[j];
+        if (!(isfinite(ax) && isfinite(r0s) && isfinite(sf) && isfinite(smin))) status = kErrNonfinite;
+        RowState r = {};
+        r.b = a.bconst[j] + ax;
+        r.passes = 0;
+        r.rlast = 0.0;
+        const double r0 = r0s - r.b;
+        ws->info.b[j] = r.b;
+        if (!(r0 > 0.0)) {
+            r.rlast = r0;
+            finish_row(r, 0.0, 0, bc, j);
+        } else {
+            // every variable with a != 0 sits at its row-minimising bound for lam >= H
+            float Hf = (float)(lsat * (1.0 + 1e-5) + 1e-30);
+            if (!((double)Hf > 0.0)) Hf = FLT_MIN;
+            const double H = (double)Hf;
+            const double rH = smin - r.b - 2.0 * H / a.C;
+            if (rH > 0.0) {
+                r.rlast = 0.0;
+                finish_row(r, 0.5 * a.C * (smin - r.b), 1, bc, j);
+            } else {
+                r.L = 0.0;
+                r.rL = r0;
+                r.SL = sf + 2.0 / a.C;
+                r.H = H;
+                r.rH = rH;
+                r.SH = 2.0 / a.C;
+                r.lam = 0.0;
+                r.active = 1;
+                r.how = 2;
+                bc->active[j] = 1;
+                choose_points(r, bc->pts[j]);
+                any = 1;
+            }
+        }
+        rows[j].b = r.b;
+        rows[j].L = r.L;
+        rows[j].rL = r.rL;
+        rows[j].SL = r.SL;
+        rows[j].H = r.H;
+        rows[j].rH = r.rH;
+        rows[j].SH = r.SH;
+        rows[j].lam = r.lam;
+        rows[j].rlast = r.rlast;
+        rows[j].active = r.active;
+        rows[j].passes = r.passes;
+        rows[j].how = r.how;
+    }
+    if (status != kOk) any = 0;
+    bc->status = status;
+    bc->any_active = any;
+}
+
+// After a root-search pass: move the bracket, test convergence, choose the next points.
+__device__ void update_after_pass(const SegArgs& a, const BlockScratch& sc, SegWork* ws) {
+    volatile SegBcast* bc = &ws->bc;
+    volatile RowState* rows = ws->rows;
+    int any = 0;
+    for (int j = 0; j < a.nrows; ++j) {
+        if (!rows[j].active) continue;
+        RowState r;
+        r.b = rows[j].b;
+        r.L = rows[j].L;
+        r.rL = rows[j].rL;
+        r.SL = rows[j].SL;
+        r.H = rows[j].H;
+        r.rH = rows[j].rH;
+        r.SH = rows[j].SH;
+        r.passes = rows[j].passes + 1;
+        r.active = 1;
+        r.how = 2;
+        r.rlast = 0.0;
+        double exact = -1.0;
+        double rk[K], Sk[K], lk[K];
+        for (int k = 0; k < K; ++k) {
+            lk[k] = (double)bc->pts[j][k];
+            rk[k] = df_to_double(sc.tot[2 * K * j + k]) - r.b - 2.0 * lk[k] / a.C;
+            Sk[k] = df_to_double(sc.tot[2 * K * j + K + k]) + 2.0 / a.C;
+        }
+        // new lower end: the largest point with r > 0; new upper end: the smallest point
+        // above it with r <= 0 (points the rounding noise puts out of order are ignored)
+        for (int k = 0; k < K; ++k)
+            if (rk[k] > 0.0 && lk[k] > r.L && lk[k] < r.H) {
+                r.L = lk[k];
+                r.rL = rk[k];
+                r.SL = Sk[k];
+            }
+        for (int k = 0; k < K; ++k)
+            if (!(rk[k] > 0.0) && lk[k] > r.L && lk[k] < r.H) {
+                r.H = lk[k];
+                r.rH = rk[k];
+                r.SH = Sk[k];
+                if (rk[k] == 0.0) exact = lk[k];
+            }
+        const double NL = r.L + r.rL / r.SL;
+        const double NH = r.H + r.rH / r.SH;
+        const double w = r.H - r.L;
+        const double tol = a.tol_lambda * fmax(fabs(r.H), 1e-300);
+        double root = -1.0;
+        if (exact >= 0.0) {
+            root = exact;
+        } else if (fabs(NL - NH) <= tol) {
+            root = fmin(fmax(0.5 * (NL + NH), r.L), r.H);
+        } else if (w <= tol || w <= 4.0 * float_ulp(r.H)) {
+            root = fmin(fmax(0.5 * (NL + NH), r.L), r.H);
+        }
+        if (root < 0.0 && r.passes >= a.max_passes) {
+            root = fmin(fmax(r.L + r.rL * w / (r.rL - r.rH), r.L), r.H);
+            r.how = 3;  // not converged
+        }
+        if (root >= 0.0) {
+            r.rlast = fmax(fabs(r.rL), fabs(r.rH));
+            finish_row(r, root, r.how, bc, j);
+        } else {
+            choose_points(r, bc->pts[j]);
+            any = 1;
+        }
+        rows[j].L = r.L;
+        rows[j].rL = r.rL;
+        rows[j].SL = r.SL;
+        rows[j].H = r.H;
+        rows[j].rH = r.rH;
+        rows[j].SH = r.SH;
+        rows[j].lam = r.lam;
+        rows[j].rlast = r.rlast;
+        rows[j].active = r.active;
+        rows[j].passes = r.passes;
+        rows[j].how = r.how;
+    }
+    bc->any_active = any;
+}
+
+// After phase D: the report.
+__device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegWork* ws) {
+    volatile DeviceInfo* inf = &ws->info;
+    volatile RowState* rows = ws->rows;
+    volatile SegBcast* bc = &ws->bc;
+    int status = bc->status;
+    int passes = 0;
+    double phi = 0.0;
+    for (int j = 0; j < a.nrows; ++j) {
+        const double ax = df_to_double(sc.tot[j]);
+        inf->lambda[j] = rows[j].lam;
+        inf->viol[j] = ax - rows[j].b;
+        inf->b[j] = rows[j].b;
+        passes = max(passes, rows[j].passes);
+        phi = fmax(phi, fabs(rows[j].rlast));
+        if (rows[j].how == 3 && status == kOk) status = kNotConverged;
+        if (!isfinite(ax) && status == kOk) status = kErrNonfinite;
+    }
+    for (int j = a.nrows; j < kMaxRows; ++j) {
+        inf->lambda[j] = 0.0;
+        inf->viol[j] = 0.0;
+        inf->b[j] = 0.0;
+    }
+    if (!a.proj) {
+        const double dd = df_to_double(sc.tot[a.nrows]);
+        const double nn = df_to_double(sc.tot[a.nrows + 1]);
+        inf->rel_change = nn > 0.0 ? sqrt(dd / nn) : INFINITY;
+    } else {
+        inf->rel_change = 0.0;
+        inf->alpha = 0.0;
+        inf->beta = 0.0;
+        inf->branch = -1;
+        inf->t = -1;
+    }
+    inf->phi_inf = phi;
+    inf->passes = passes;
+    inf->newton_iters = 0;
+    inf->stage = 0;
+    inf->status = status;
+    if (status != kOk) atomicCAS(&ws->ctrl.status, kOk, status);
+    ws->ctrl.launches += 1ull;
+}
+
+// Early exit after a non-finite reduction: report and stop.
+__device__ void report_status_only(const SegArgs& a, SegWork* ws, int status) {
+    volatile DeviceInfo* inf = &ws->info;
+    inf->status = status;
+    inf->passes = 0;
+    atomicCAS(&ws->ctrl.status, kOk, status);
+    ws->ctrl.launches += 1ull;
+}
+
+// ----------------------------------------------------------------------- element passes
+
+template <int N>
+struct Acc {
+    float f[N];
+    DF d[N];
+    int cnt;
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            f[i] = 0.0f;
+            d[i] = df_zero();
+        }
+        cnt = 0;
+    }
+    __device__ __forceinline__ void fold() {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            d[i] = df_add_f(d[i], f[i]);
+            f[i] = 0.0f;
+        }
+        cnt = 0;
+    }
+    __device__ __forceinline__ void tick() {
+        if (++cnt == kFoldEvery) fold();
+    }
+};
+
+// Iterate the block's share [cb, ce): f4(v) for aligned float4 groups v (elements 4v..4v+3),
+// f1(i) for the unaligned head and tail, then tick() per group.
+template <bool VEC, class F4, class F1>
+__device__ __forceinline__ void for_chunk(int64_t cb, int64_t ce, F4&& f4, F1&& f1) {
+    if (VEC) {
+        int64_t vb = (cb + 3) & ~int64_t(3);
+        if (vb > ce) vb = ce;
+        int64_t ve = ce & ~int64_t(3);
+        if (ve < vb) ve = vb;
+        for (int64_t i = cb + threadIdx.x; i < vb; i += blockDim.x) f1(i);
+        for (int64_t v = (vb >> 2) + threadIdx.x; v < (ve >> 2); v += blockDim.x) f4(v);
+        for (int64_t i = ve + threadIdx.x; i < ce; i += blockDim.x) f1(i);
+    } else {
+        for (int64_t i = cb + threadIdx.x; i < ce; i += blockDim.x) f1(i);
+    }
+}
+
+#define LD4(p, v) (__ldcs(reinterpret_cast<const float4*>(p) + (v)))
+#define LD4L2(p, v) (__ldcg(reinterpret_cast<const float4*>(p) + (v)))
+
+template <bool VEC>
+__global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
+    __shared__ BlockScratch sc;
+    __shared__ SegBcast bc;
+    SegWork* ws = a.ws;
+    if (ld_volatile_i32(&ws->ctrl.abort)) return;
+    const int nb = gridDim.x, blk = blockIdx.x;
+    const float lo = a.lo, hi = a.hi;
+
+    if (!a.proj) {
+        // ------------------------------------------------------------ phase A
+        Acc<6> acc;
+        acc.init();
+        float gmax = 0.0f;
+        int64_t cb, ce;
+        block_chunk(0, a.n, blk, nb, cb, ce);
+        if (a.t > 0) {
+            auto e = [&](float x, float xp, float g, float gp) {
+                const float s = x - xp, y = g - gp;
+                acc.f[0] = fmaf(s, s, acc.f[0]);
+                acc.f[1] = fmaf(s, y, acc.f[1]);
+                acc.f[2] = fmaf(y, y, acc.f[2]);
+                acc.f[3] = fmaf(g, y, acc.f[3]);
+                acc.f[4] = fmaf(gp, gp, acc.f[4]);
+                acc.f[5] = fmaf(g, g, acc.f[5]);
+                gmax = fmaxf(gmax, fabsf(g));
+            };
+            for_chunk<VEC>(
+                cb, ce,
+                [&](int64_t v) {
+                    float4 x = LD4L2(a.x, v), xp = LD4(a.x_prev, v), g = LD4L2(a.g, v), gp = LD4(a.g_prev, v);
+                    e(x.x, xp.x, g.x, gp.x);
+                    e(x.y, xp.y, g.y, gp.y);
+                    e(x.z, xp.z, g.z, gp.z);
+                    e(x.w, xp.w, g.w, gp.w);
+                    acc.tick();
+                },
+                [&](int64_t i) {
+                    e(a.x[i], a.x_prev[i], a.g[i], a.g_prev[i]);
+                    acc.tick();
+                });
+        } else {
+            auto e = [&](float g) {
+                acc.f[5] = fmaf(g, g, acc.f[5]);
+                gmax = fmaxf(gmax, fabsf(g));
+            };
+            for_chunk<VEC>(
+                cb, ce,
+                [&](int64_t v) {
+                    float4 g = LD4L2(a.g, v);
+                    e(g.x);
+                    e(g.y);
+                    e(g.z);
+                    e(g.w);
+                    acc.tick();
+                },
+                [&](int64_t i) {
+                    e(a.g[i]);
+                    acc.tick();
+                });
+        }
+        acc.fold();
+        {
+            float mx[1] = {gmax};
+            block_reduce<6, 1>(acc.d, mx, sc);
+        }
+        if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 6, 1, a.timeout_cycles,
+                                [&](BlockScratch& s) { update_step_scalars(a, s, ws); }))
+            return;
+        load_cg(bc, &ws->bc);
+        if (bc.status != kOk) {
+            if (blk == 0 && threadIdx.x == 0) report_status_only(a, ws, bc.status);
+            return;
+        }
+    }
+
+    // ---------------------------------------------------------------- phase B
+    {
+        const float ch = a.proj ? 0.0f : bc.c_hi, bh = a.proj ? 0.0f : bc.beta_hi;
+        const bool first = a.t == 0;
+        for (int j = 0; j < a.nrows; ++j) {
+            Acc<4> acc;
+            acc.init();
+            float lsat = 0.0f;
+            int64_t cb, ce;
+            block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
+            auto e = [&](float z, float av, float x) {
+                acc.f[0] = fmaf(av, x, acc.f[0]);
+                const float xc = clampf(z, lo, hi);
+                acc.f[1] = fmaf(av, xc, acc.f[1]);
+                acc.f[2] = (z >= lo && z <= hi) ? fmaf(av, av, acc.f[2]) : acc.f[2];
+                acc.f[3] += av > 0.0f ? av * lo : (av < 0.0f ? av * hi : 0.0f);
+                if (av != 0.0f) {
+                    const float bp = (av > 0.0f ? z - lo : z - hi) / av;
+                    lsat = fmaxf(lsat, bp);
+                }
+            };
+            if (a.proj) {
+                for_chunk<VEC>(
+                    cb, ce,
+                    [&](int64_t v) {
+                        float4 z = LD4L2(a.z_in, v), av = LD4L2(a.A, v);
+                        e(z.x, av.x, 0.0f);
+                        e(z.y, av.y, 0.0f);
+                        e(z.z, av.z, 0.0f);
+                        e(z.w, av.w, 0.0f);
+                        acc.tick();
+                    },
+                    [&](int64_t i) {
+                        e(a.z_in[i], a.A[i], 0.0f);
+                        acc.tick();
+                    });
+            } else {
+                const float cl = bc.c_lo, bl = bc.beta_lo;
+                // d_t = beta d_prev - g and z = x + c d_t in double-float: the FP32 direction is
+                // the stored state, (z_hi, z_lo) the trial point the projection sees
+                auto st = [&](float x, float g, float dp, float av, float& dout, float& zh, float& zl) {
+                    float uh, ul;
+                    if (first) {
+                        uh = -g;
+                        ul = 0.0f;
+                    } else {
+                        const float p = bh * dp;
+                        const float pe = fmaf(bh, dp, -p);
+                        const DF s = two_sum(p, -g);
+                        uh = s.hi;
+                        ul = __fadd_rn(s.lo, fmaf(bl, dp, pe));
+                    }
+                    const DF u = fast_two_sum(uh, ul);
+                    const float vh = ch * u.hi;
+                    const float ve = fmaf(ch, u.hi, -vh);
+                    const float vl = __fadd_rn(ve, fmaf(ch, u.lo, cl * u.hi));
+                    const DF s = two_sum(x, vh);
+                    const DF z = fast_two_sum(s.hi, __fadd_rn(s.lo, vl));
+                    dout = u.hi;
+                    zh = z.hi;
+                    zl = z.lo;
+                    e(z.hi, av, x);
+                };
+                for_chunk<VEC>(
+                    cb, ce,
+                    [&](int64_t v) {
+                        float4 x = LD4L2(a.x, v), g = LD4L2(a.g, v), av = LD4L2(a.A, v);
+                        float4 dp = first ? make_float4(0.f, 0.f, 0.f, 0.f) : LD4(a.d_prev, v);
+                        float4 d, zh, zl;
+                        st(x.x, g.x, dp.x, av.x, d.x, zh.x, zl.x);
+                        st(x.y, g.y, dp.y, av.y, d.y, zh.y, zl.y);
+                        st(x.z, g.z, dp.z, av.z, d.z, zh.z, zl.z);
+                        st(x.w, g.w, dp.w, av.w, d.w, zh.w, zl.w);
+                        __stcs(reinterpret_cast<float4*>(a.d_new) + v, d);
+                        reinterpret_cast<float4*>(a.z)[v] = zh;
+                        reinterpret_cast<float4*>(a.zlo)[v] = zl;
+                        __stcs(reinterpret_cast<float4*>(a.x_prev) + v, x);
+                        __stcs(reinterpret_cast<float4*>(a.g_prev) + v, g);
+                        acc.tick();
+                    },
+                    [&](int64_t i) {
+                        const float x = a.x[i], g = a.g[i];
+                        float d, zh, zl;
+                        st(x, g, first ? 0.0f : a.d_prev[i], a.A[i], d, zh, zl);
+                        a.d_new[i] = d;
+                        a.z[i] = zh;
+                        a.zlo[i] = zl;
+                        a.x_prev[i] = x;
+                        a.g_prev[i] = g;
+                        acc.tick();
+                    });
+            }
+            acc.fold();
+            float mx[1] = {lsat};
+            block_reduce<4, 1>(acc.d, mx, sc, 4 * j, j);
+        }
+        if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 4 * a.nrows, a.nrows, a.timeout_cycles,
+                                [&](BlockScratch& s) { update_after_trial(a, s, ws); }))
+            return;
+        load_cg(bc, &ws->bc);
+        if (bc.status != kOk) {
+            if (blk == 0 && threadIdx.x == 0) report_status_only(a, ws, bc.status);
+            return;
+        }
+    }
+
+    // ---------------------------------------------------------------- phase C
+    const float* zsrc = a.proj ? a.z_in : a.z;
+    const bool has_lo = !a.proj;
+    while (bc.any_active) {
+        for (int j = 0; j < a.nrows; ++j) {
+            if (!bc.active[j]) continue;
+            float p[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) p[k] = bc.pts[j][k];
+            Acc<2 * K> acc;
+            acc.init();
+            int64_t cb, ce;
+            block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
+            auto e = [&](float z, float zl, float av) {
+                const float aa = av * av;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const float w = __fadd_rn(fmaf(-p[k], av, z), zl);
+                    acc.f[k] = fmaf(av, clampf(w, lo, hi), acc.f[k]);
+                    acc.f[K + k] += (w >= lo && w <= hi) ? aa : 0.0f;
+                }
+            };
+            if (has_lo) {
+                for_chunk<VEC>(
+                    cb, ce,
+                    [&](int64_t v) {
+                        float4 z = LD4L2(zsrc, v), zl = LD4L2(a.zlo, v), av = LD4L2(a.A, v);
+                        e(z.x, zl.x, av.x);
+                        e(z.y, zl.y, av.y);
+                        e(z.z, zl.z, av.z);
+                        e(z.w, zl.w, av.w);
+                        acc.tick();
+                    },
+                    [&](int64_t i) {
+                        e(zsrc[i], a.zlo[i], a.A[i]);
+                        acc.tick();
+                    });
+            } else {
+                for_chunk<VEC>(
+                    cb, ce,
+                    [&](int64_t v) {
+                        float4 z = LD4L2(zsrc, v), av = LD4L2(a.A, v);
+                        e(z.x, 0.0f, av.x);
+                        e(z.y, 0.0f, av.y);
+                        e(z.z, 0.0f, av.z);
+                        e(z.w, 0.0f, av.w);
+                        acc.tick();
+                    },
+                    [&](int64_t i) {
+                        e(zsrc[i], 0.0f, a.A[i]);
+                        acc.tick();
+                    });
+            }
+            acc.fold();
+            block_reduce<2 * K, 0>(acc.d, nullptr, sc, 2 * K * j, 0);
+        }
+        if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 2 * K * a.nrows, 0, a.timeout_cycles,
+                                [&](BlockScratch& s) { update_after_pass(a, s, ws); }))
+            return;
+        load_cg(bc, &ws->bc);
+    }
+
+    // ---------------------------------------------------------------- phase D
+    {
+        Acc<kMaxRows + 2> acc;
+        acc.init();
+        for (int j = 0; j < a.nrows; ++j) {
+            const float lh = bc.lam_hi[j], ll = bc.lam_lo[j];
+            int64_t cb, ce;
+            block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
+            float axj = 0.0f;
+            DF axd = df_zero();
+            int cnt = 0;
+            if (a.proj) {
+                auto e = [&](float z, float av) -> float {
+                    const float qh = lh * av;
+                    const float qe = fmaf(lh, av, -qh);
+                    const float ql = fmaf(ll, av, qe);
+                    const DF s = two_sum(z, -qh);
+                    const float w = __fadd_rn(s.hi, __fsub_rn(s.lo, ql));
+                    const float xo = clampf(w, lo, hi);
+                    axj = fmaf(av, xo, axj);
+                    return xo;
+                };
+                for_chunk<VEC>(
+                    cb, ce,
+                    [&](int64_t v) {
+                        float4 z = LD4L2(a.z_in, v), av = LD4L2(a.A, v);
+                        float4 o;
+                        o.x = e(z.x, av.x);
+                        o.y = e(z.y, av.y);
+                        o.z = e(z.z, av.z);
+                        o.w = e(z.w, av.w);
+                        reinterpret_cast<float4*>(a.x_out)[v] = o;
+                        if (++cnt == kFoldEvery) {
+                            axd = df_add_f(axd, axj);
+                            axj = 0.0f;
+                            cnt = 0;
+                        }
+                    },
+                    [&](int64_t i) { a.x_out[i] = e(a.z_in[i], a.A[i]); });
+            } else {
+                // x_{t+1} = clip(z - lam a) with z = z_hi + z_lo and lam = lam_hi + lam_lo
+                auto e = [&](float x, float zh, float zl, float av) -> float {
+                    const float t1 = fmaf(-lh, av, zh);
+                    const float t2 = fmaf(-ll, av, zl);
+                    const float xn = clampf(__fadd_rn(t1, t2), lo, hi);
+                    axj = fmaf(av, xn, axj);
+                    const float dx = xn - x;
+                    acc.f[kMaxRows] = fmaf(dx, dx, acc.f[kMaxRows]);
+                    acc.f[kMaxRows + 1] = fmaf(xn, xn, acc.f[kMaxRows + 1]);
+                    return xn;
+                };
+                for_chunk<VEC>(
+                    cb, ce,
+                    [&](int64_t v) {
+                        float4 x = LD4L2(a.x, v), zh = LD4(a.z, v), zl = LD4(a.zlo, v), av = LD4(a.A, v);
+                        float4 o;
+                        o.x = e(x.x, zh.x, zl.x, av.x);
+                        o.y = e(x.y, zh.y, zl.y, av.y);
+                        o.z = e(x.z, zh.z, zl.z, av.z);
+                        o.w = e(x.w, zh.w, zl.w, av.w);
+                        reinterpret_cast<float4*>(a.x)[v] = o;
+                        if (++cnt == kFoldEvery) {
+                            axd = df_add_f(axd, axj);
+                            axj = 0.0f;
+                            cnt = 0;
+                            acc.fold();
+                        }
+                    },
+                    [&](int64_t i) { a.x[i] = e(a.x[i], a.z[i], a.zlo[i], a.A[i]); });
+            }
+            axd = df_add_f(axd, axj);
+            acc.d[j] = df_add(acc.d[j], axd);
+        }
+        acc.fold();
+        const int nv = a.nrows + (a.proj ? 0 : 2);
+        if (a.nrows < kMaxRows) {
+            // pack the two norms right after the rows
+            acc.d[a.nrows] = acc.d[kMaxRows];
+            acc.d[a.nrows + 1] = acc.d[kMaxRows + 1];
+        }
+        block_reduce<kMaxRows + 2, 0>(acc.d, nullptr, sc);
+        grid_reduce_update(&ws->ctrl, &ws->part, sc, nv, 0, a.timeout_cycles,
+                           [&](BlockScratch& s) { update_final(a, s, ws); });
+    }
+}
+
+template <bool VEC>
+static cudaError_t launch_seg_t(const SegArgs& a, int blocks, cudaStream_t stream) {
+    void* args[] = {const_cast<SegArgs*>(&a)};
+    return cudaLaunchCooperativeKernel((void*)seg_kernel<VEC>, dim3(blocks), dim3(kThreads), args, 0, stream);
+}
+
+cudaError_t launch_seg(const SegArgs& a, int blocks, cudaStream_t stream) {
+    bool vec = true;
+    auto al = [](const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    vec = al(a.x) && al(a.g) && al(a.A) && al(a.x_prev) && al(a.g_prev) && al(a.d_prev) && al(a.d_new) &&
+          al(a.z) && al(a.zlo) && al(a.z_in) && al(a.x_out);
+    return vec ? launch_seg_t<true>(a, blocks, stream) : launch_seg_t<false>(a, blocks, stream);
+}
+
+int max_blocks_seg(int device) {
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, seg_kernel<true>, kThreads, 0);
+    int per2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, seg_kernel<false>, kThreads, 0);
+    per = per < per2 ? per : per2;
+    if (per < 1) per = 1;
+    int nb = sms * per;
+    return nb > kMaxBlocks ? kMaxBlocks : nb;
+}
+
+}  // namespace pgdto
