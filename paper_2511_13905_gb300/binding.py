@@ -85,6 +85,9 @@ def load(path=None):
         "pgdto_project": (ctypes.c_int, [H, P, P, D, P, D, ctypes.POINTER(Info)]),
         "pgdto_last_info": (ctypes.c_int, [H, ctypes.POINTER(Info), D]),
         "pgdto_kernel_launches": (ctypes.c_int64, [H]),
+        "pgdto_project_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                                 ctypes.c_float, ctypes.c_float, ctypes.c_double, P, P, D, P, D,
+                                                 ctypes.POINTER(Info), P]),
         "pgdto_version": (ctypes.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -208,3 +211,17 @@ class Handle:
 
     def kernel_launches(self):
         return int(self.lib.pgdto_kernel_launches(self.h))
+
+
+def project_noalloc(z, A, b, x_out, m=1, seg=None, lo=0.0, hi=1.0, C=1e12, stream=None, want_info=True):
+    """pgdto_project_noalloc: the projection without any device allocation (no handle).
+    Returns (status, lambda list or None, Info or None)."""
+    lib = load()
+    n = int(z.numel())
+    segarr = (ctypes.c_int64 * (m + 1))(*[int(s) for s in seg]) if seg is not None else None
+    info = Info() if want_info else None
+    lam = (ctypes.c_double * m)() if want_info else None
+    st = lib.pgdto_project_noalloc(n, int(m), segarr, float(lo), float(hi), float(C), _dptr(z), _dptr(A),
+                                   _darr(b, m), _dptr(x_out), lam, ctypes.byref(info) if info is not None else None,
+                                   _stream_ptr(stream))
+    return st, (list(lam) if lam is not None else None), info

@@ -18,6 +18,7 @@
 // Each phase ends in one grid-wide reduction (dev_common.cuh).
 #include <float.h>
 #include <math.h>
+#include <string.h>
 
 #include "dev_common.cuh"
 #include "kernels.h"
@@ -764,3 +765,105 @@ int max_blocks_seg(int device) {
 }
 
 }  // namespace pgdto
+
+// ------------------------------------------------------------------ allocation-free projection
+//
+// pgdto_project_noalloc serves callers that cannot allocate device memory: code that runs
+// while a CUDA graph it does not own is being captured (cudaMalloc is not allowed there),
+// processes whose device memory is handed out by another allocator or fixed at start-up,
+// and loops that must never wait on the driver's allocator.  It runs the projection kernel
+// above with its workspace in the file-scope array below instead of a handle's allocation.
+// Every GPU that loads this library holds the array until the process exits.
+
+#include <mutex>
+
+#include "../../include/pgdto.h"
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(pgdto::SegWork)];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoallocMaxDevices];
+
+// Device address of the array on `device`, looked up once per device with that device
+// current.  Host code only ever sees the array through this address: the symbol name
+// itself is a host-side stand-in, not a device pointer.
+cudaError_t noalloc_workspace(int device, void** out) {
+    if (device < 0 || device >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[device] = p;
+    }
+    *out = g_noalloc_addr[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" pgdto_status pgdto_project_noalloc(int64_t n, int m, const int64_t* seg_offsets, float lo, float hi,
+                                              double C, const float* z, const float* A, const double* b,
+                                              float* x_out, double* lambda_out, pgdto_info* info,
+                                              void* cuda_stream) {
+    using namespace pgdto;
+    if (n < 1 || m < 1 || m > kMaxRows || !z || !A || !b || !x_out) return PGDTO_ERR_ARG;
+    if (m > 1 && !seg_offsets) return PGDTO_ERR_ARG;
+    if (!(isfinite(lo) && isfinite(hi) && lo < hi) || !(C > 0.0 && isfinite(C))) return PGDTO_ERR_ARG;
+    SegArgs a;
+    memset(&a, 0, sizeof(a));
+    a.seg[0] = 0;
+    a.seg[m] = n;
+    if (seg_offsets) {
+        if (seg_offsets[0] != 0 || seg_offsets[m] != n) return PGDTO_ERR_ARG;
+        for (int j = 0; j < m; ++j) {
+            if (seg_offsets[j + 1] <= seg_offsets[j]) return PGDTO_ERR_ARG;
+            a.seg[j] = seg_offsets[j];
+        }
+    }
+    for (int j = 0; j < m; ++j) {
+        if (!isfinite(b[j])) return PGDTO_ERR_NONFINITE;
+        a.bconst[j] = b[j];
+    }
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return PGDTO_ERR_CUDA;
+    void* ws = nullptr;
+    if (noalloc_workspace(device, &ws) != cudaSuccess) return PGDTO_ERR_CUDA;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    pgdto_params p;
+    pgdto_params_default(&p);
+    int clock_khz = 0;
+    cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, device);
+    if (clock_khz <= 0) clock_khz = 2000000;
+    a.n = n;
+    a.nrows = m;
+    a.t = 0;
+    a.proj = 1;
+    a.lo = lo;
+    a.hi = hi;
+    a.A = A;
+    a.z_in = z;
+    a.x_out = x_out;
+    a.C = C;
+    a.tol_lambda = p.tol_lambda;
+    a.max_passes = p.max_passes;
+    a.timeout_cycles = (long long)clock_khz * (long long)p.barrier_timeout_ms;
+    a.ws = (SegWork*)ws;
+    // the barrier counters and the sticky status must start at zero; the rest of the array
+    // keeps whatever the last call left and is rewritten before it is read
+    if (cudaMemsetAsync(ws, 0, sizeof(GridCtrl), stream) != cudaSuccess) return PGDTO_ERR_CUDA;
+    if (launch_seg(a, max_blocks_seg(device), stream) != cudaSuccess) return PGDTO_ERR_CUDA;
+    if (!info && !lambda_out) return PGDTO_OK;
+    DeviceInfo di;
+    if (cudaMemcpyAsync(&di, seg_work_info((SegWork*)ws), sizeof(di), cudaMemcpyDeviceToHost, stream) !=
+        cudaSuccess)
+        return PGDTO_ERR_CUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return PGDTO_ERR_CUDA;
+    if (info) memcpy(info, &di, sizeof(di));
+    if (lambda_out)
+        for (int j = 0; j < m; ++j) lambda_out[j] = di.lambda[j];
+    return (pgdto_status)di.status;
+}
