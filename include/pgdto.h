@@ -175,6 +175,15 @@ pgdto_status pgdto_project(pgdto_handle* h, const float* z, const float* A, cons
 /* Wait for the handle's stream and report the last step or projection. */
 pgdto_status pgdto_last_info(pgdto_handle* h, pgdto_info* info, double* lambda_out);
 
+/*
+ * Phase timeline of the last step or projection (tracing): waits for the stream, writes
+ * up to max_marks times in microseconds since the kernel started, one per grid-wide
+ * reduction in order (step: step-size pass, trial-point pass, each root-search pass or
+ * Newton iteration, final pass), and returns how many marks there were (or -1 on error).
+ * Taken from the device's global timer; resolution is that timer's.
+ */
+int pgdto_trace(pgdto_handle* h, double* us_out, int max_marks);
+
 /* Number of the library's kernels launched by this handle so far (for accounting). */
 int64_t pgdto_kernel_launches(const pgdto_handle* h);
 

@@ -85,6 +85,7 @@ def load(path=None):
         "pgdto_project": (ctypes.c_int, [H, P, P, D, P, D, ctypes.POINTER(Info)]),
         "pgdto_last_info": (ctypes.c_int, [H, ctypes.POINTER(Info), D]),
         "pgdto_kernel_launches": (ctypes.c_int64, [H]),
+        "pgdto_trace": (ctypes.c_int, [H, D, ctypes.c_int]),
         "pgdto_project_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                                  ctypes.c_float, ctypes.c_float, ctypes.c_double, P, P, D, P, D,
                                                  ctypes.POINTER(Info), P]),
@@ -208,6 +209,12 @@ class Handle:
         lam = (ctypes.c_double * self.m)()
         st = self.lib.pgdto_last_info(self.h, ctypes.byref(info), lam)
         return st, list(lam), info
+
+    def trace(self, max_marks=62):
+        """Phase timeline of the last call: microseconds since kernel start, one per grid reduction."""
+        buf = (ctypes.c_double * max_marks)()
+        k = self.lib.pgdto_trace(self.h, buf, max_marks)
+        return list(buf)[:max(k, 0)]
 
     def kernel_launches(self):
         return int(self.lib.pgdto_kernel_launches(self.h))

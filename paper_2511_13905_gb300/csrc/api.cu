@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/pgdto.h"
+#include "dev_common.cuh"
 #include "kernels.h"
 
 using namespace pgdto;
@@ -396,4 +397,14 @@ extern "C" pgdto_status pgdto_project(pgdto_handle* h, const float* z, const flo
     h->last_was_project = 1;
     if (info || lambda_out) return read_info(h, info, lambda_out);
     return PGDTO_OK;
+}
+
+extern "C" int pgdto_trace(pgdto_handle* h, double* us_out, int max_marks) {
+    if (!h || max_marks < 0 || (max_marks > 0 && !us_out)) return -1;
+    GridCtrl c;
+    if (cudaMemcpyAsync(&c, h->work, sizeof(c), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return -1;
+    int k = c.ntrace < 0 ? 0 : (c.ntrace > 62 ? 62 : c.ntrace);
+    for (int i = 0; i < k && i < max_marks; ++i) us_out[i] = (double)(c.trace[i] - c.trace_start) * 1e-3;
+    return k;
 }

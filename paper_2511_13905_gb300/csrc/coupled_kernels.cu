@@ -1,19 +1,1119 @@
-// coupled_kernels.cu -- coupled rows (Alg. 2); filled in below the segmented path.
+// coupled_kernels.cu -- fused PGD-TO step / projection for m <= 4 coupled rows (Alg. 2).
+//
+// One cooperative launch; A is m dense rows of n floats.  Phases (each ends in one grid
+// reduction, dev_common.cuh):
+//   A  step size and PR+ coefficient (as for single rows)
+//   B  double-float trial point z, state copies; per row a_j^T x_t, r_j(0), the saturation
+//      bound and the free-set curvature at 0 (Alg. 1's inputs for each row)
+//   S1 Alg. 2 stage 1: the m single-row searches (row j alone, the others at zero) run
+//      side by side, K trial points per row per pass
+//   F  feasibility of each single-row candidate against every row (m x m sums); a
+//      candidate that satisfies all rows ends the projection (stage 1 accepted)
+//   E  evaluation at the dual iterate lam: h = A x(lam) - b - 2 lam / C, J_h = A D A^T + 2/C
+//      (eq. h, eq. reg_jacobian) and sum_i |a_ji x_i| for the row scales
+//   LS exact line search along the Newton direction d: phi'(g) = d^T h(lam + g d) is the
+//      residual of a single virtual row u = A^T d on w0 = z - A^T lam, so it reuses the
+//      root search of the single-row path; then back to E
+//   D  x = clip(z - A^T lam) in double-float, a_j^T x, ||x - x_t||, ||x||
+// Stage 2 solves J_h on the working set {lam_j > 0 or h_j > 0} (the semismooth Newton
+// system of App. A.3.3 restricted to the rows that can move) and, instead of backtracking
+// on the merit ||Phi||^2 / 2, maximises the concave dual exactly along the direction,
+// which keeps lam >= 0 by capping the step.
+#include <float.h>
+#include <math.h>
+#include <string.h>
+
 #include "dev_common.cuh"
 #include "kernels.h"
+#include "step_common.cuh"
 
 namespace pgdto {
 
+enum CoupledMode : int { kModeDone = 0, kModeStage1 = 1, kModeFeas = 2, kModeEval = 3, kModeLine = 4 };
+
+struct CoupledBcast {
+    // step scalars (field names shared with the single-row kernel's templates)
+    double alpha, beta, c;
+    float c_hi, c_lo, beta_hi, beta_lo;
+    int branch, status;
+    int any_active;  // root searches still running (stage 1 or line search)
+    int mode;        // what the next pass computes (CoupledMode)
+    float pts[kMaxRows][K];
+    int active[kMaxRows];
+    float lam_hi[kMaxRows], lam_lo[kMaxRows];  // stage-1 candidates, then the final lam
+    // dual iterate and Newton direction, split into float pairs for the element passes
+    float it_hi[kMaxRows], it_lo[kMaxRows];
+    float d_hi[kMaxRows], d_lo[kMaxRows];
+    int cand_row[kMaxRows];  // rows whose stage-1 candidate is tested in the F pass
+    int ncand;
+    int pad;
+};
+
+struct NewtonState {
+    double lam[kMaxRows];   // current dual iterate
+    double d[kMaxRows];     // current direction
+    double base[kMaxRows];  // iterate the direction was computed at (the full step is a trial)
+    double base_phi;        // scaled KKT residual at base
+    double base_slope, base_dtb, base_dd;  // line-search data at base along d
+    double cap;             // largest step keeping lam >= 0 along d
+    double tol;
+    double phi;             // largest scaled |h_j| seen at the last evaluation
+    int iters;
+    int passes;             // passes after the trial-point pass
+    int stage;              // 1 stage-1 candidate accepted, 2 Newton
+    int how;                // 3 if an iteration limit was hit
+    int ls_expand;          // 1: line-search bracket open on the right, 2: closed by the cap
+    int stall;              // evaluations in a row without progress at the rounding floor
+    int trial;              // lam is the full Newton step from base, not yet accepted
+    int pad;
+};
+
 struct CoupledWork {
     GridCtrl ctrl;
+    CoupledBcast bc;
+    RowState rows[kMaxRows];  // stage-1 searches
+    RowState ls;              // the line search
+    NewtonState nt;
     DeviceInfo info;
+    Partials part;
 };
 
 size_t coupled_work_bytes() { return sizeof(CoupledWork); }
 size_t coupled_work_ctrl_bytes() { return sizeof(GridCtrl); }
 DeviceInfo* coupled_work_info(CoupledWork* ws) { return &ws->info; }
 
-cudaError_t launch_coupled(const CoupledArgs&, int, cudaStream_t) { return cudaErrorNotSupported; }
-int max_blocks_coupled(int) { return 1; }
+// sc.tot layout of each pass
+//   B:   4 per row (a^T x_t, a^T clip(z), free curvature at 0, S_min), max per row
+//   S1:  2K per row
+//   F:   m per candidate row (sums of every row at that candidate)
+//   E:   [0, m) h sums a_j^T x, [m, 2m) sum |a_j x|, [2m, 2m + 10) J upper triangle
+//   LS:  2K
+//   D:   [0, m) a_j^T x, m: ||x - x_t||^2, m + 1: ||x||^2
+template <int M>
+__device__ __forceinline__ int jidx(int j, int k) {  // row-major upper-triangle index of (j, k), j <= k
+    return j * M - (j * (j - 1)) / 2 + (k - j);
+}
+
+// ----------------------------------------------------------------------- scalar updates
+
+// Phase B: inputs of the single-row searches (Alg. 2 stage 1), as for a single row.
+template <int M>
+__device__ void cupd_after_trial(const CoupledArgs& a, const BlockScratch& sc, CoupledWork* ws) {
+    const int lane = threadIdx.x, j = lane >> 3, k = lane & 7;
+    volatile CoupledBcast* bc = &ws->bc;
+    volatile RowState* rows = ws->rows;
+    const bool row = j < M;
+    const int jj = row ? j : 0;
+    const double two_c = 2.0 / a.C;
+    const double ax = a.proj ? 0.0 : df_to_double(sc.tot[4 * jj + 0]);
+    const double r0s = df_to_double(sc.tot[4 * jj + 1]);
+    const double sf = df_to_double(sc.tot[4 * jj + 2]);
+    const double smin = df_to_double(sc.tot[4 * jj + 3]);
+    const double lsat = (double)sc.totmax[jj];
+    const bool finite = isfinite(ax) && isfinite(r0s) && isfinite(sf) && isfinite(smin);
+    const double b = a.bconst[jj] + ax;
+    const double r0 = r0s - b;
+    float Hf = (float)(lsat * (1.0 + 1e-5) + 1e-30);
+    if (!((double)Hf > 0.0)) Hf = FLT_MIN;
+    const double H = (double)Hf;
+    const double rH = smin - b - two_c * H;
+    const bool inactive = !(r0 > 0.0);
+    const bool closed = !inactive && rH > 0.0;
+    const bool search = row && finite && !inactive && !closed;
+    const double SL = sf + two_c;
+    double q = 0.0;
+    if (k == 0) q = r0 / SL;
+    else if (k == 1) q = rH / two_c;
+    const double NL = __shfl_sync(kFull, q, lane & ~7);
+    const double NH = H + __shfl_sync(kFull, q, (lane & ~7) + 1);
+    const float p = next_point(lane, 0.0, r0, H, rH, NL, NH);
+    if (row && k == 0) {
+        ws->info.b[j] = b;
+        rows[j].reg = two_c;
+        if (search) {
+            store_row(&rows[j], b, 0.0, r0, SL, H, rH, two_c, 0.0, 0.0, 1, 0, 2);
+            bc->active[j] = 1;
+        } else if (closed) {
+            const double lam = 0.5 * a.C * (smin - b);
+            store_row(&rows[j], b, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, lam, 0.0, 0, 0, 1);
+            publish_lambda(bc, j, lam);
+        } else {
+            store_row(&rows[j], b, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, r0, 0, 0, 0);
+            publish_lambda(bc, j, 0.0);
+        }
+    }
+    if (search) bc->pts[j][k] = p;
+    const unsigned any = __ballot_sync(kFull, search);
+    const unsigned bad = __ballot_sync(kFull, row && !finite);
+    if (lane == 0) {
+        int status = a.proj ? kOk : bc->status;
+        if (bad) status = kErrNonfinite;
+        bc->status = status;
+        bc->any_active = (status == kOk && any) ? 1 : 0;
+        volatile NewtonState* nt = &ws->nt;
+        nt->iters = 0;
+        nt->how = 0;
+        nt->stage = 0;
+        nt->passes = 0;
+        nt->stall = 0;
+        nt->trial = 0;
+        nt->phi = INFINITY;
+        nt->tol = 1e-8;  // relative tolerance of the line search (the next Newton step corrects)
+    }
+}
+
+// Candidates of stage 1 are known: set up the feasibility pass (or finish at lam = 0).
+template <int M>
+__device__ void cupd_plan_feasibility(CoupledWork* ws) {
+    volatile CoupledBcast* bc = &ws->bc;
+    volatile RowState* rows = ws->rows;
+    if (threadIdx.x != 0) return;
+    int nc = 0;
+    for (int j = 0; j < M; ++j)
+        if (rows[j].lam > 0.0) bc->cand_row[nc++] = j;
+    bc->ncand = nc;
+    volatile NewtonState* nt = &ws->nt;
+    for (int j = 0; j < M; ++j) {
+        nt->lam[j] = 0.0;
+        bc->it_hi[j] = 0.0f;
+        bc->it_lo[j] = 0.0f;
+    }
+    if (nc == 0) {
+        // every row holds at lam = 0: that is the KKT point
+        nt->stage = 1;
+        bc->mode = kModeDone;
+    } else {
+        bc->mode = kModeFeas;
+    }
+}
+
+__device__ __forceinline__ void set_iterate(volatile CoupledBcast* bc, volatile NewtonState* nt, int m) {
+    for (int j = 0; j < m; ++j) {
+        float h, l;
+        split_double(nt->lam[j], h, l);
+        bc->it_hi[j] = h;
+        bc->it_lo[j] = l;
+    }
+}
+
+// Phase F: accept the first single-row candidate that every row admits (Alg. 2 stage 1);
+// otherwise start stage 2 from all candidates together.
+template <int M>
+__device__ void cupd_after_feasibility(const CoupledArgs& a, const BlockScratch& sc, CoupledWork* ws) {
+    if (threadIdx.x != 0) return;
+    volatile CoupledBcast* bc = &ws->bc;
+    volatile RowState* rows = ws->rows;
+    volatile NewtonState* nt = &ws->nt;
+    const double two_c = 2.0 / a.C;
+    const int nc = bc->ncand;
+    int accepted = -1;
+    for (int c = 0; c < nc && accepted < 0; ++c) {
+        const int j = bc->cand_row[c];
+        bool ok = true;
+        for (int k = 0; k < M; ++k) {
+            if (k == j) continue;  // row j holds at its own root by construction
+            const double r = df_to_double(sc.tot[c * M + k]) - rows[k].b;
+            // admitted when the row holds to 1e-9 of its magnitude (tighter than tol_N so the
+            // accepted point is the regularised optimum to the parity tolerance)
+            if (!(r <= 1e-9 * fmax(1.0, fabs(rows[k].b)))) ok = false;
+        }
+        if (ok) accepted = j;
+    }
+    if (accepted >= 0) {
+        for (int k = 0; k < M; ++k) nt->lam[k] = (k == accepted) ? rows[accepted].lam : 0.0;
+        nt->stage = 1;
+        bc->mode = kModeDone;
+    } else {
+        for (int k = 0; k < M; ++k) nt->lam[k] = rows[k].lam;
+        nt->stage = 2;
+        bc->mode = kModeEval;
+    }
+    set_iterate(bc, nt, M);
+}
+
+// Line search along nt->d from nt->base (nt->lam is reset to base): first points
+// around the Newton step g = 1; phi'(0) = d^T h(base) = d^T J d > 0.
+template <int M>
+__device__ void cstart_line_search(CoupledWork* ws) {
+    volatile CoupledBcast* bc = &ws->bc;
+    volatile NewtonState* nt = &ws->nt;
+    volatile RowState* ls = &ws->ls;
+    for (int j = 0; j < M; ++j) nt->lam[j] = nt->base[j];
+    set_iterate(bc, nt, M);
+    double cap = INFINITY;
+    for (int j = 0; j < M; ++j)
+        if (nt->d[j] < 0.0) cap = fmin(cap, nt->base[j] / (-nt->d[j]));
+    nt->cap = cap;
+    ls->b = nt->base_dtb;
+    ls->reg = nt->base_dd;
+    ls->L = 0.0;
+    ls->rL = nt->base_slope;
+    ls->SL = nt->base_slope;
+    ls->passes = 0;
+    ls->active = 1;
+    ls->how = 2;
+    const float base[K] = {0.125f, 0.25f, 0.5f, 0.75f, 1.0f, 1.25f, 2.0f, 8.0f};
+    if (isfinite(cap)) {
+        ls->H = cap;
+        ls->rH = 0.0;
+        ls->SH = 0.0;
+        for (int k = 0; k < K; ++k) {
+            double v = fmin((double)base[k], cap * (double)(k + 1) / (double)K);
+            if (k == K - 1) v = cap;
+            bc->pts[0][k] = (float)v;
+        }
+        nt->ls_expand = 2;  // bracket closed by the cap
+    } else {
+        ls->H = INFINITY;
+        for (int k = 0; k < K; ++k) bc->pts[0][k] = base[k];
+        nt->ls_expand = 1;
+    }
+    nt->trial = 0;
+    bc->any_active = 1;
+    bc->mode = kModeLine;
+}
+
+// Phase E: h and J_h at lam.  A full Newton step under test is accepted when the scaled
+// KKT residual fell; otherwise the step is replaced by an exact line search from its base.
+// At an accepted point: KKT test, then the Newton direction on the working set and the
+// next full step max(lam + d, 0) as the new trial.
+template <int M>
+__device__ void cupd_after_eval(const CoupledArgs& a, const BlockScratch& sc, CoupledWork* ws) {
+    if (threadIdx.x != 0) return;
+    volatile CoupledBcast* bc = &ws->bc;
+    volatile RowState* rows = ws->rows;
+    volatile NewtonState* nt = &ws->nt;
+    const double two_c = 2.0 / a.C;
+    double h[M], scale[M];
+    bool conv = true;
+    for (int j = 0; j < M; ++j) {
+        h[j] = df_to_double(sc.tot[j]) - rows[j].b - two_c * nt->lam[j];
+        scale[j] = fmax(1.0, fmax(fabs(rows[j].b), df_to_double(sc.tot[M + j])));
+        const double tol = 1e-9 * scale[j];
+        if (nt->lam[j] > 0.0) {
+            if (!(fabs(h[j]) <= tol)) conv = false;
+        } else if (!(h[j] <= tol)) {
+            conv = false;
+        }
+    }
+    if (!isfinite(h[0]) || !isfinite(h[M - 1])) {
+        bc->status = kErrNonfinite;
+        bc->mode = kModeDone;
+        return;
+    }
+    double phi = 0.0;
+    for (int j = 0; j < M; ++j) phi = fmax(phi, (nt->lam[j] > 0.0 ? fabs(h[j]) : fmax(h[j], 0.0)) / scale[j]);
+    if (nt->trial) {
+        if (!(phi < nt->base_phi * (1.0 - 1e-4) || phi <= 1e-8)) {
+            cstart_line_search<M>(ws);  // the full step did not reduce the residual
+            return;
+        }
+        nt->trial = 0;
+        nt->iters = nt->iters + 1;
+    }
+    // stop at the rounding floor of the FP32 sums: the scaled KKT residual is small and
+    // has stopped halving over the last iterations
+    const double prev = nt->phi;
+    const int stall = (nt->iters >= 2 && phi <= 1e-7 && phi >= 0.5 * prev) ? nt->stall + 1 : 0;
+    nt->stall = stall;
+    nt->phi = phi;
+    if (stall >= 2) conv = true;
+    int S[M], ns = 0;
+    for (int j = 0; j < M; ++j)
+        if (nt->lam[j] > 0.0 || h[j] > 0.0) S[ns++] = j;
+    if (conv || ns == 0) {
+        bc->mode = kModeDone;
+        return;
+    }
+    if (nt->iters >= a.maxiter_newton) {
+        nt->how = 3;
+        bc->mode = kModeDone;
+        return;
+    }
+    // J_SS d_S = h_S (eq. reg_jacobian restricted to the working set), Gaussian elimination;
+    // a row at lam_j = 0 whose direction would push it below zero leaves the set and the
+    // system is solved again (at most M times)
+    double d[M];
+    for (int round = 0; round < M; ++round) {
+        double Mx[M][M], rhs[M];
+        for (int p = 0; p < ns; ++p) {
+            for (int q = 0; q < ns; ++q) {
+                const int jp = S[p], jq = S[q];
+                const int lo = jp < jq ? jp : jq, hi = jp < jq ? jq : jp;
+                Mx[p][q] = df_to_double(sc.tot[2 * M + jidx<M>(lo, hi)]) + (jp == jq ? two_c : 0.0);
+            }
+            rhs[p] = h[S[p]];
+        }
+        for (int p = 0; p < ns; ++p) {
+            const double inv = 1.0 / Mx[p][p];
+            for (int r = p + 1; r < ns; ++r) {
+                const double f = Mx[r][p] * inv;
+                for (int q = p; q < ns; ++q) Mx[r][q] -= f * Mx[p][q];
+                rhs[r] -= f * rhs[p];
+            }
+        }
+        double dS[M];
+        for (int p = ns - 1; p >= 0; --p) {
+            double v = rhs[p];
+            for (int q = p + 1; q < ns; ++q) v -= Mx[p][q] * dS[q];
+            dS[p] = v / Mx[p][p];
+        }
+        for (int j = 0; j < M; ++j) d[j] = 0.0;
+        for (int p = 0; p < ns; ++p) d[S[p]] = dS[p];
+        int keep = 0;
+        bool dropped = false;
+        for (int p = 0; p < ns; ++p) {
+            const int j = S[p];
+            if (nt->lam[j] <= 0.0 && d[j] < 0.0) dropped = true;
+            else S[keep++] = j;
+        }
+        if (!dropped || keep == 0) break;
+        ns = keep;
+    }
+    double slope0 = 0.0, dtb = 0.0, dd = 0.0;
+    for (int j = 0; j < M; ++j) {
+        slope0 += d[j] * h[j];
+        dtb += d[j] * (rows[j].b + two_c * nt->lam[j]);
+        dd += d[j] * d[j];
+    }
+    if (!(slope0 > 0.0)) {
+        bc->mode = kModeDone;  // no ascent along d: the rounding floor is reached
+        return;
+    }
+    for (int j = 0; j < M; ++j) {
+        nt->d[j] = d[j];
+        nt->base[j] = nt->lam[j];
+        float dh, dl;
+        split_double(d[j], dh, dl);
+        bc->d_hi[j] = dh;
+        bc->d_lo[j] = dl;
+    }
+    nt->base_phi = phi;
+    nt->base_slope = slope0;
+    nt->base_dtb = dtb;
+    nt->base_dd = two_c * dd;
+    // the full Newton step, kept in lam >= 0, is evaluated by the next E pass
+    for (int j = 0; j < M; ++j) nt->lam[j] = fmax(nt->lam[j] + d[j], 0.0);
+    set_iterate(bc, nt, M);
+    nt->trial = 1;
+    bc->mode = kModeEval;
+}
+
+// Phase LS: one pass of the exact line search along d.  The first pass of a direction
+// either finds the sign change of phi' among its points or, if phi' > 0 at all of them,
+// takes the cap (closed bracket) or moves the bracket right (open bracket).  Later
+// passes are the shared root search.  When it ends, lam <- max(lam + g d, 0).
+template <int M>
+__device__ void cupd_after_line(const CoupledArgs& a, const BlockScratch& sc, CoupledWork* ws) {
+    const int lane = threadIdx.x;
+    volatile CoupledBcast* bc = &ws->bc;
+    volatile NewtonState* nt = &ws->nt;
+    volatile RowState* ls = &ws->ls;
+    const int expand = nt->ls_expand;
+    if (expand) {
+        const int k = lane & 7;
+        const double gk = (double)bc->pts[0][k];
+        const double rk = df_to_double(sc.tot[k]) - ls->b - ls->reg * gk;
+        const double Sk = df_to_double(sc.tot[K + k]) + ls->reg;
+        const unsigned nonpos = __ballot_sync(kFull, lane < K && !(rk > 0.0)) & 0xffu;
+        const int kH = nonpos ? __ffs(nonpos) - 1 : -1;
+        double L = ls->L, rL = ls->rL, SL = ls->SL;
+        const double gL = __shfl_sync(kFull, gk, kH > 0 ? kH - 1 : 0);
+        const double rLn = __shfl_sync(kFull, rk, kH > 0 ? kH - 1 : 0);
+        const double SLn = __shfl_sync(kFull, Sk, kH > 0 ? kH - 1 : 0);
+        const double gH = __shfl_sync(kFull, gk, kH >= 0 ? kH : K - 1);
+        const double rHn = __shfl_sync(kFull, rk, kH >= 0 ? kH : K - 1);
+        const double SHn = __shfl_sync(kFull, Sk, kH >= 0 ? kH : K - 1);
+        if (kH > 0) {
+            L = gL;
+            rL = rLn;
+            SL = SLn;
+        }
+        if (kH >= 0) {
+            // bracket [L, H] closed: next points from the shared rule
+            double q = 0.0;
+            if (k == 0) q = rL / SL;
+            else if (k == 1) q = rHn / SHn;
+            const double NL = L + __shfl_sync(kFull, q, 0);
+            const double NH = gH + __shfl_sync(kFull, q, 1);
+            const float p = next_point(lane, L, rL, gH, rHn, NL, NH);
+            if (lane < K) bc->pts[0][lane] = p;
+            if (lane == 0) {
+                store_row(ls, ls->b, L, rL, SL, gH, rHn, SHn, 0.0, 0.0, 1, ls->passes + 1, 2);
+                nt->ls_expand = 0;
+                bc->any_active = 1;
+            }
+        } else if (lane == 0) {
+            // phi' > 0 at every point
+            if (expand == 2 || ls->passes >= 4) {
+                store_row(ls, ls->b, gH, rHn, SHn, gH, rHn, SHn, expand == 2 ? nt->cap : gH, 0.0, 0, ls->passes + 1,
+                          2);
+                bc->any_active = 0;
+            } else {
+                store_row(ls, ls->b, gH, rHn, SHn, INFINITY, 0.0, 0.0, 0.0, 0.0, 1, ls->passes + 1, 2);
+                const float mult[K] = {2.0f, 3.0f, 4.0f, 6.0f, 8.0f, 16.0f, 64.0f, 1024.0f};
+                for (int q = 0; q < K; ++q) bc->pts[0][q] = (float)(gH * (double)mult[q]);
+                bc->any_active = 1;
+            }
+        }
+    } else {
+        search_pass_update(sc, 0, ls, bc, 1, nt->tol, a.max_passes);
+    }
+    __syncwarp();
+    if (lane != 0) return;
+    nt->passes = nt->passes + 1;
+    if (bc->any_active) return;
+    // line search finished: take the step
+    double g = ls->lam;
+    const double cap = nt->cap;
+    const bool at_cap = isfinite(cap) && g >= cap * (1.0 - 1e-12);
+    if (at_cap) g = cap;
+    for (int j = 0; j < M; ++j) {
+        const double dj = nt->d[j];
+        double v = nt->lam[j] + g * dj;
+        if (v < 0.0 || (at_cap && dj < 0.0 && nt->lam[j] / (-dj) <= cap * (1.0 + 1e-12))) v = fmax(v, 0.0);
+        if (at_cap && dj < 0.0 && nt->lam[j] / (-dj) <= cap * (1.0 + 1e-12)) v = 0.0;
+        nt->lam[j] = v;
+    }
+    nt->iters = nt->iters + 1;
+    nt->trial = 0;
+    set_iterate(bc, nt, M);
+    bc->mode = kModeEval;
+}
+
+// When the projection is decided, publish lam for the final pass (thread 0).
+template <int M>
+__device__ __forceinline__ void cfinish_if_done(CoupledWork* ws) {
+    volatile CoupledBcast* bc = &ws->bc;
+    volatile NewtonState* nt = &ws->nt;
+    if (bc->mode != kModeDone) return;
+    for (int j = 0; j < M; ++j) {
+        float h, l;
+        split_double(nt->lam[j], h, l);
+        bc->lam_hi[j] = h;
+        bc->lam_lo[j] = l;
+    }
+}
+
+// After phase D: the report.
+template <int M>
+__device__ void cupd_final(const CoupledArgs& a, const BlockScratch& sc, CoupledWork* ws) {
+    const int lane = threadIdx.x;
+    volatile DeviceInfo* inf = &ws->info;
+    volatile RowState* rows = ws->rows;
+    volatile CoupledBcast* bc = &ws->bc;
+    volatile NewtonState* nt = &ws->nt;
+    double rc = 0.0;
+    if (lane == 1 && !a.proj) {
+        const double dd = df_to_double(sc.tot[M]);
+        const double nn = df_to_double(sc.tot[M + 1]);
+        rc = nn > 0.0 ? sqrt(dd / nn) : INFINITY;
+    }
+    rc = __shfl_sync(kFull, rc, 1);
+    if (lane != 0) return;
+    int status = bc->status;
+    for (int j = 0; j < M; ++j) {
+        const double ax = df_to_double(sc.tot[j]);
+        inf->lambda[j] = nt->lam[j];
+        inf->viol[j] = ax - rows[j].b;
+        inf->b[j] = rows[j].b;
+        if (!isfinite(ax) && status == kOk) status = kErrNonfinite;
+    }
+    for (int j = M; j < kMaxRows; ++j) {
+        inf->lambda[j] = 0.0;
+        inf->viol[j] = 0.0;
+        inf->b[j] = 0.0;
+    }
+    if (nt->how == 3 && status == kOk) status = kNotConverged;
+    if (!a.proj) {
+        inf->rel_change = rc;
+    } else {
+        inf->rel_change = 0.0;
+        inf->alpha = 0.0;
+        inf->beta = 0.0;
+        inf->branch = -1;
+        inf->t = -1;
+    }
+    inf->phi_inf = nt->phi;
+    inf->passes = nt->passes;
+    inf->newton_iters = nt->iters;
+    inf->stage = nt->stage;
+    inf->status = status;
+    if (status != kOk) atomicCAS(&ws->ctrl.status, kOk, status);
+    ws->ctrl.launches += 1ull;
+}
+
+// ----------------------------------------------------------------------- element passes
+
+template <bool VEC, int M>
+__global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
+    __shared__ BlockScratch sc;
+    __shared__ CoupledBcast bc;
+    CoupledWork* ws = a.ws;
+    if (ld_volatile_i32(&ws->ctrl.abort)) return;
+    const int nb = gridDim.x, blk = blockIdx.x;
+    const float lo = a.lo, hi = a.hi;
+    const int64_t n = a.n;
+    if (blk == 0 && threadIdx.x == 0) {
+        volatile GridCtrl* vc = &ws->ctrl;
+        vc->trace_start = globaltimer_ns();
+        vc->ntrace = 0;
+    }
+    int64_t cb, ce;
+    block_chunk(0, n, blk, nb, cb, ce);
+    const float* zh_src = a.proj ? a.z_in : a.z;
+    const bool has_lo = !a.proj;
+
+    if (!a.proj) {
+        // ------------------------------------------------------------ phase A
+        Acc<6> acc;
+        acc.init();
+        float gmax = 0.0f;
+        if (a.t > 0) {
+            auto e = [&](float x, float xp, float g, float gp) {
+                const float s = x - xp, y = g - gp;
+                acc.f[0] = fmaf(s, s, acc.f[0]);
+                acc.f[1] = fmaf(s, y, acc.f[1]);
+                acc.f[2] = fmaf(y, y, acc.f[2]);
+                acc.f[3] = fmaf(g, y, acc.f[3]);
+                acc.f[4] = fmaf(gp, gp, acc.f[4]);
+                acc.f[5] = fmaf(g, g, acc.f[5]);
+                gmax = fmaxf(gmax, fabsf(g));
+            };
+            for_chunk<VEC>(
+                cb, ce,
+                [&](int64_t v) {
+                    float4 x = LD4L2(a.x, v), xp = LD4(a.x_prev, v), g = LD4L2(a.g, v), gp = LD4(a.g_prev, v);
+                    e(x.x, xp.x, g.x, gp.x);
+                    e(x.y, xp.y, g.y, gp.y);
+                    e(x.z, xp.z, g.z, gp.z);
+                    e(x.w, xp.w, g.w, gp.w);
+                    acc.tick();
+                },
+                [&](int64_t i) {
+                    e(a.x[i], a.x_prev[i], a.g[i], a.g_prev[i]);
+                    acc.tick();
+                });
+        } else {
+            auto e = [&](float g) {
+                acc.f[5] = fmaf(g, g, acc.f[5]);
+                gmax = fmaxf(gmax, fabsf(g));
+            };
+            for_chunk<VEC>(
+                cb, ce,
+                [&](int64_t v) {
+                    float4 g = LD4L2(a.g, v);
+                    e(g.x);
+                    e(g.y);
+                    e(g.z);
+                    e(g.w);
+                    acc.tick();
+                },
+                [&](int64_t i) {
+                    e(a.g[i]);
+                    acc.tick();
+                });
+        }
+        acc.fold();
+        {
+            float mx[1] = {gmax};
+            block_reduce<6, 1>(acc.d, mx, sc);
+        }
+        if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 6, 1, a.timeout_cycles,
+                                [&](BlockScratch& s) { update_step_scalars(a, s, &ws->bc, &ws->info); }))
+            return;
+        load_cg(bc, &ws->bc);
+        if (bc.status != kOk) {
+            if (blk == 0 && threadIdx.x == 0) {
+                ws->info.status = bc.status;
+                atomicCAS(&ws->ctrl.status, kOk, bc.status);
+            }
+            return;
+        }
+    }
+
+    // ---------------------------------------------------------------- phase B
+    {
+        const float ch = a.proj ? 0.0f : bc.c_hi, cl = a.proj ? 0.0f : bc.c_lo;
+        const float bh = a.proj ? 0.0f : bc.beta_hi, bl = a.proj ? 0.0f : bc.beta_lo;
+        const bool first = a.t == 0;
+        Acc<4 * M> acc;
+        acc.init();
+        float lsat[M];
+#pragma unroll
+        for (int j = 0; j < M; ++j) lsat[j] = 0.0f;
+        auto rowsum = [&](float z, const float (&av)[M], float x) {
+            const bool fr = z >= lo && z <= hi;
+            const float xc = clampf(z, lo, hi);
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                const float aj = av[j];
+                acc.f[4 * j + 0] = fmaf(aj, x, acc.f[4 * j + 0]);
+                acc.f[4 * j + 1] = fmaf(aj, xc, acc.f[4 * j + 1]);
+                acc.f[4 * j + 2] = fr ? fmaf(aj, aj, acc.f[4 * j + 2]) : acc.f[4 * j + 2];
+                acc.f[4 * j + 3] += aj > 0.0f ? aj * lo : (aj < 0.0f ? aj * hi : 0.0f);
+                if (aj != 0.0f) lsat[j] = fmaxf(lsat[j], (aj > 0.0f ? z - lo : z - hi) / aj);
+            }
+        };
+        // d_t and z = x + c d_t in double-float (as in the single-row kernel)
+        auto trial = [&](float x, float g, float dp, float& dout, float& zh, float& zl) {
+            float uh, ul;
+            if (first) {
+                uh = -g;
+                ul = 0.0f;
+            } else {
+                const float p = bh * dp;
+                const float pe = fmaf(bh, dp, -p);
+                const DF s = two_sum(p, -g);
+                uh = s.hi;
+                ul = __fadd_rn(s.lo, fmaf(bl, dp, pe));
+            }
+            const DF u = fast_two_sum(uh, ul);
+            const float vh = ch * u.hi;
+            const float ve = fmaf(ch, u.hi, -vh);
+            const float vl = __fadd_rn(ve, fmaf(ch, u.lo, cl * u.hi));
+            const DF s = two_sum(x, vh);
+            const DF z = fast_two_sum(s.hi, __fadd_rn(s.lo, vl));
+            dout = u.hi;
+            zh = z.hi;
+            zl = z.lo;
+        };
+        for_chunk<VEC>(
+            cb, ce,
+            [&](int64_t v) {
+                float4 A4[M];
+#pragma unroll
+                for (int j = 0; j < M; ++j) A4[j] = LD4L2(a.A + (int64_t)j * n, v);
+                if (a.proj) {
+                    float4 z = LD4L2(a.z_in, v);
+                    const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float av[M];
+#pragma unroll
+                        for (int j = 0; j < M; ++j) av[j] = reinterpret_cast<const float*>(&A4[j])[q];
+                        rowsum(zz[q], av, 0.0f);
+                    }
+                } else {
+                    float4 x = LD4L2(a.x, v), g = LD4L2(a.g, v);
+                    float4 dp = first ? make_float4(0.f, 0.f, 0.f, 0.f) : LD4(a.d_prev, v);
+                    float4 d, zh, zl;
+                    const float xx[4] = {x.x, x.y, x.z, x.w}, gg[4] = {g.x, g.y, g.z, g.w};
+                    const float pp[4] = {dp.x, dp.y, dp.z, dp.w};
+                    float dd[4], h4[4], l4[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        trial(xx[q], gg[q], pp[q], dd[q], h4[q], l4[q]);
+                        float av[M];
+#pragma unroll
+                        for (int j = 0; j < M; ++j) av[j] = reinterpret_cast<const float*>(&A4[j])[q];
+                        rowsum(h4[q], av, xx[q]);
+                    }
+                    d = make_float4(dd[0], dd[1], dd[2], dd[3]);
+                    zh = make_float4(h4[0], h4[1], h4[2], h4[3]);
+                    zl = make_float4(l4[0], l4[1], l4[2], l4[3]);
+                    __stcs(reinterpret_cast<float4*>(a.d_new) + v, d);
+                    reinterpret_cast<float4*>(a.z)[v] = zh;
+                    reinterpret_cast<float4*>(a.zlo)[v] = zl;
+                    __stcs(reinterpret_cast<float4*>(a.x_prev) + v, x);
+                    __stcs(reinterpret_cast<float4*>(a.g_prev) + v, g);
+                }
+                acc.tick();
+            },
+            [&](int64_t i) {
+                float av[M];
+#pragma unroll
+                for (int j = 0; j < M; ++j) av[j] = a.A[(int64_t)j * n + i];
+                if (a.proj) {
+                    rowsum(a.z_in[i], av, 0.0f);
+                } else {
+                    const float x = a.x[i], g = a.g[i];
+                    float d, zh, zl;
+                    trial(x, g, first ? 0.0f : a.d_prev[i], d, zh, zl);
+                    a.d_new[i] = d;
+                    a.z[i] = zh;
+                    a.zlo[i] = zl;
+                    a.x_prev[i] = x;
+                    a.g_prev[i] = g;
+                    rowsum(zh, av, x);
+                }
+                acc.tick();
+            });
+        acc.fold();
+        block_reduce<4 * M, M>(acc.d, lsat, sc);
+        if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 4 * M, M, a.timeout_cycles, [&](BlockScratch& s) {
+                cupd_after_trial<M>(a, s, ws);
+                __syncwarp();
+                if (threadIdx.x == 0) {
+                    volatile CoupledBcast* vb = &ws->bc;
+                    if (vb->status != kOk) vb->mode = kModeDone;
+                    else if (vb->any_active) vb->mode = kModeStage1;
+                    else cupd_plan_feasibility<M>(ws);
+                    cfinish_if_done<M>(ws);
+                }
+            }))
+            return;
+        load_cg(bc, &ws->bc);
+        if (bc.status != kOk) {
+            if (blk == 0 && threadIdx.x == 0) {
+                ws->info.status = bc.status;
+                atomicCAS(&ws->ctrl.status, kOk, bc.status);
+            }
+            return;
+        }
+    }
+
+    // ---------------------------------------------------------------- S1, F, E, LS
+    while (bc.mode != kModeDone) {
+        const int mode = bc.mode;
+        if (mode == kModeStage1) {
+            // Alg. 2 stage 1: row j alone (others at zero), K points per active row
+            for (int j = 0; j < M; ++j) {
+                if (!bc.active[j]) continue;
+                float p[K];
+#pragma unroll
+                for (int k = 0; k < K; ++k) p[k] = bc.pts[j][k];
+                Acc<2 * K> acc;
+                acc.init();
+                const float* Aj = a.A + (int64_t)j * n;
+                auto e = [&](float z, float zl, float av) {
+                    const float aa = av * av;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        const float w = __fadd_rn(fmaf(-p[k], av, z), zl);
+                        acc.f[k] = fmaf(av, clampf(w, lo, hi), acc.f[k]);
+                        acc.f[K + k] += (w >= lo && w <= hi) ? aa : 0.0f;
+                    }
+                };
+                for_chunk<VEC>(
+                    cb, ce,
+                    [&](int64_t v) {
+                        float4 z = LD4L2(zh_src, v), av = LD4L2(Aj, v);
+                        float4 zl = has_lo ? LD4L2(a.zlo, v) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        e(z.x, zl.x, av.x);
+                        e(z.y, zl.y, av.y);
+                        e(z.z, zl.z, av.z);
+                        e(z.w, zl.w, av.w);
+                        acc.tick();
+                    },
+                    [&](int64_t i) {
+                        e(zh_src[i], has_lo ? a.zlo[i] : 0.0f, Aj[i]);
+                        acc.tick();
+                    });
+                acc.fold();
+                block_reduce<2 * K, 0>(acc.d, nullptr, sc, 2 * K * j, 0);
+            }
+            if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 2 * K * M, 0, a.timeout_cycles,
+                                    [&](BlockScratch& s) {
+                                        search_pass_update(s, 0, ws->rows, &ws->bc, M, a.tol_lambda, a.max_passes);
+                                        __syncwarp();
+                                        if (threadIdx.x == 0) {
+                                            volatile NewtonState* nt = &ws->nt;
+                                            nt->passes = nt->passes + 1;
+                                            if (!ws->bc.any_active) cupd_plan_feasibility<M>(ws);
+                                            cfinish_if_done<M>(ws);
+                                        }
+                                    }))
+                return;
+        } else if (mode == kModeFeas) {
+            // every row's sum at each single-row candidate lam_j e_j
+            const int nc = bc.ncand;
+            int crow[M];
+            float clh[M], cll[M];
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                crow[c] = c < nc ? bc.cand_row[c] : 0;
+                clh[c] = bc.lam_hi[crow[c]];
+                cll[c] = bc.lam_lo[crow[c]];
+            }
+            Acc<M * M> acc;
+            acc.init();
+            auto e = [&](float z, float zl, const float (&av)[M]) {
+#pragma unroll
+                for (int c = 0; c < M; ++c) {
+                    if (c >= nc) break;
+                    float aj = av[0];
+#pragma unroll
+                    for (int q = 1; q < M; ++q) aj = crow[c] == q ? av[q] : aj;
+                    const float w = __fadd_rn(fmaf(-clh[c], aj, z), fmaf(-cll[c], aj, zl));
+                    const float x = clampf(w, lo, hi);
+#pragma unroll
+                    for (int k = 0; k < M; ++k) acc.f[c * M + k] = fmaf(av[k], x, acc.f[c * M + k]);
+                }
+            };
+            for_chunk<VEC>(
+                cb, ce,
+                [&](int64_t v) {
+                    float4 z = LD4L2(zh_src, v);
+                    float4 zl = has_lo ? LD4L2(a.zlo, v) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 A4[M];
+#pragma unroll
+                    for (int j = 0; j < M; ++j) A4[j] = LD4L2(a.A + (int64_t)j * n, v);
+                    const float zz[4] = {z.x, z.y, z.z, z.w}, ll[4] = {zl.x, zl.y, zl.z, zl.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float av[M];
+#pragma unroll
+                        for (int j = 0; j < M; ++j) av[j] = reinterpret_cast<const float*>(&A4[j])[q];
+                        e(zz[q], ll[q], av);
+                    }
+                    acc.tick();
+                },
+                [&](int64_t i) {
+                    float av[M];
+#pragma unroll
+                    for (int j = 0; j < M; ++j) av[j] = a.A[(int64_t)j * n + i];
+                    e(zh_src[i], has_lo ? a.zlo[i] : 0.0f, av);
+                    acc.tick();
+                });
+            acc.fold();
+            block_reduce<M * M, 0>(acc.d, nullptr, sc);
+            if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, M * M, 0, a.timeout_cycles, [&](BlockScratch& s) {
+                    cupd_after_feasibility<M>(a, s, ws);
+                    if (threadIdx.x == 0) {
+                        volatile NewtonState* nt = &ws->nt;
+                        nt->passes = nt->passes + 1;
+                        cfinish_if_done<M>(ws);
+                    }
+                }))
+                return;
+        } else if (mode == kModeEval) {
+            // h, row magnitudes and J_h at the iterate (eq. h, eq. reg_jacobian)
+            float lh[M], ll[M];
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                lh[j] = bc.it_hi[j];
+                ll[j] = bc.it_lo[j];
+            }
+            constexpr int NJ = M * (M + 1) / 2;
+            Acc<2 * M + NJ> acc;
+            acc.init();
+            auto e = [&](float z, float zl, const float (&av)[M]) {
+                float w = z, wl = zl;
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    w = fmaf(-lh[j], av[j], w);
+                    wl = fmaf(-ll[j], av[j], wl);
+                }
+                w = __fadd_rn(w, wl);
+                const float x = clampf(w, lo, hi);
+                const bool fr = w >= lo && w <= hi;
+                int t = 0;
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    const float ax = av[j] * x;
+                    acc.f[j] += ax;
+                    acc.f[M + j] += fabsf(ax);
+#pragma unroll
+                    for (int k = j; k < M; ++k) {
+                        acc.f[2 * M + t] = fr ? fmaf(av[j], av[k], acc.f[2 * M + t]) : acc.f[2 * M + t];
+                        ++t;
+                    }
+                }
+            };
+            for_chunk<VEC>(
+                cb, ce,
+                [&](int64_t v) {
+                    float4 z = LD4L2(zh_src, v);
+                    float4 zl = has_lo ? LD4L2(a.zlo, v) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 A4[M];
+#pragma unroll
+                    for (int j = 0; j < M; ++j) A4[j] = LD4L2(a.A + (int64_t)j * n, v);
+                    const float zz[4] = {z.x, z.y, z.z, z.w}, l4[4] = {zl.x, zl.y, zl.z, zl.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float av[M];
+#pragma unroll
+                        for (int j = 0; j < M; ++j) av[j] = reinterpret_cast<const float*>(&A4[j])[q];
+                        e(zz[q], l4[q], av);
+                    }
+                    acc.tick();
+                },
+                [&](int64_t i) {
+                    float av[M];
+#pragma unroll
+                    for (int j = 0; j < M; ++j) av[j] = a.A[(int64_t)j * n + i];
+                    e(zh_src[i], has_lo ? a.zlo[i] : 0.0f, av);
+                    acc.tick();
+                });
+            acc.fold();
+            block_reduce<2 * M + NJ, 0>(acc.d, nullptr, sc);
+            if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 2 * M + NJ, 0, a.timeout_cycles,
+                                    [&](BlockScratch& s) {
+                                        cupd_after_eval<M>(a, s, ws);
+                                        if (threadIdx.x == 0) {
+                                            volatile NewtonState* nt = &ws->nt;
+                                            nt->passes = nt->passes + 1;
+                                            cfinish_if_done<M>(ws);
+                                        }
+                                    }))
+                return;
+        } else {
+            // exact line search along d: virtual row u = A^T d on w0 = z - A^T lam
+            float lh[M], ll[M], dh[M], p[K];
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                lh[j] = bc.it_hi[j];
+                ll[j] = bc.it_lo[j];
+                dh[j] = bc.d_hi[j];
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) p[k] = bc.pts[0][k];
+            Acc<2 * K> acc;
+            acc.init();
+            auto e = [&](float z, float zl, const float (&av)[M]) {
+                float w = z, wl = zl, u = 0.0f;
+#pragma unroll
+                for (int j = 0; j < M; ++j) {
+                    w = fmaf(-lh[j], av[j], w);
+                    wl = fmaf(-ll[j], av[j], wl);
+                    u = fmaf(dh[j], av[j], u);
+                }
+                w = __fadd_rn(w, wl);
+                const float uu = u * u;
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const float wk = fmaf(-p[k], u, w);
+                    acc.f[k] = fmaf(u, clampf(wk, lo, hi), acc.f[k]);
+                    acc.f[K + k] += (wk >= lo && wk <= hi) ? uu : 0.0f;
+                }
+            };
+            for_chunk<VEC>(
+                cb, ce,
+                [&](int64_t v) {
+                    float4 z = LD4L2(zh_src, v);
+                    float4 zl = has_lo ? LD4L2(a.zlo, v) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 A4[M];
+#pragma unroll
+                    for (int j = 0; j < M; ++j) A4[j] = LD4L2(a.A + (int64_t)j * n, v);
+                    const float zz[4] = {z.x, z.y, z.z, z.w}, l4[4] = {zl.x, zl.y, zl.z, zl.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float av[M];
+#pragma unroll
+                        for (int j = 0; j < M; ++j) av[j] = reinterpret_cast<const float*>(&A4[j])[q];
+                        e(zz[q], l4[q], av);
+                    }
+                    acc.tick();
+                },
+                [&](int64_t i) {
+                    float av[M];
+#pragma unroll
+                    for (int j = 0; j < M; ++j) av[j] = a.A[(int64_t)j * n + i];
+                    e(zh_src[i], has_lo ? a.zlo[i] : 0.0f, av);
+                    acc.tick();
+                });
+            acc.fold();
+            block_reduce<2 * K, 0>(acc.d, nullptr, sc);
+            if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 2 * K, 0, a.timeout_cycles, [&](BlockScratch& s) {
+                    cupd_after_line<M>(a, s, ws);
+                    if (threadIdx.x == 0) cfinish_if_done<M>(ws);
+                }))
+                return;
+        }
+        load_cg(bc, &ws->bc);
+        if (bc.status != kOk) break;
+    }
+
+    // ---------------------------------------------------------------- phase D
+    {
+        float lh[M], ll[M];
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+            lh[j] = bc.lam_hi[j];
+            ll[j] = bc.lam_lo[j];
+        }
+        Acc<M + 2> acc;
+        acc.init();
+        // x = clip(z - sum_j lam_j a_j): hi parts with TwoSum, lo parts and product errors
+        // gathered separately, so x is exact to FP32 rounding of the result
+        auto e = [&](float x, float z, float zl, const float (&av)[M]) -> float {
+            float sh = z, comp = zl;
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                const float ph = lh[j] * av[j];
+                const float pe = fmaf(lh[j], av[j], -ph);
+                const DF t = two_sum(sh, -ph);
+                sh = t.hi;
+                comp = __fadd_rn(comp, __fsub_rn(t.lo, fmaf(ll[j], av[j], pe)));
+            }
+            const float xn = clampf(__fadd_rn(sh, comp), lo, hi);
+#pragma unroll
+            for (int j = 0; j < M; ++j) acc.f[j] = fmaf(av[j], xn, acc.f[j]);
+            const float dx = xn - x;
+            acc.f[M] = fmaf(dx, dx, acc.f[M]);
+            acc.f[M + 1] = fmaf(xn, xn, acc.f[M + 1]);
+            return xn;
+        };
+        float* out = a.proj ? a.x_out : a.x;
+        for_chunk<VEC>(
+            cb, ce,
+            [&](int64_t v) {
+                float4 z = LD4(zh_src, v);
+                float4 zl = has_lo ? LD4(a.zlo, v) : make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 x = a.proj ? make_float4(0.f, 0.f, 0.f, 0.f) : LD4L2(a.x, v);
+                float4 A4[M];
+#pragma unroll
+                for (int j = 0; j < M; ++j) A4[j] = LD4(a.A + (int64_t)j * n, v);
+                const float zz[4] = {z.x, z.y, z.z, z.w}, l4[4] = {zl.x, zl.y, zl.z, zl.w};
+                const float xx[4] = {x.x, x.y, x.z, x.w};
+                float o[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float av[M];
+#pragma unroll
+                    for (int j = 0; j < M; ++j) av[j] = reinterpret_cast<const float*>(&A4[j])[q];
+                    o[q] = e(xx[q], zz[q], l4[q], av);
+                }
+                reinterpret_cast<float4*>(out)[v] = make_float4(o[0], o[1], o[2], o[3]);
+                acc.tick();
+            },
+            [&](int64_t i) {
+                float av[M];
+#pragma unroll
+                for (int j = 0; j < M; ++j) av[j] = a.A[(int64_t)j * n + i];
+                out[i] = e(a.proj ? 0.0f : a.x[i], zh_src[i], has_lo ? a.zlo[i] : 0.0f, av);
+                acc.tick();
+            });
+        acc.fold();
+        block_reduce<M + 2, 0>(acc.d, nullptr, sc);
+        grid_reduce_update(&ws->ctrl, &ws->part, sc, M + 2, 0, a.timeout_cycles,
+                           [&](BlockScratch& s) { cupd_final<M>(a, s, ws); });
+    }
+}
+
+template <bool VEC, int M>
+static cudaError_t launch_coupled_t(const CoupledArgs& a, int blocks, cudaStream_t stream) {
+    void* args[] = {const_cast<CoupledArgs*>(&a)};
+    return cudaLaunchCooperativeKernel((void*)coupled_kernel<VEC, M>, dim3(blocks), dim3(kThreads), args, 0, stream);
+}
+
+cudaError_t launch_coupled(const CoupledArgs& a, int blocks, cudaStream_t stream) {
+    auto al = [](const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    const bool vec = al(a.x) && al(a.g) && al(a.A) && al(a.x_prev) && al(a.g_prev) && al(a.d_prev) &&
+                     al(a.d_new) && al(a.z) && al(a.zlo) && al(a.z_in) && al(a.x_out) && (a.n % 4 == 0);
+    switch (a.m) {
+        case 2: return vec ? launch_coupled_t<true, 2>(a, blocks, stream) : launch_coupled_t<false, 2>(a, blocks, stream);
+        case 3: return vec ? launch_coupled_t<true, 3>(a, blocks, stream) : launch_coupled_t<false, 3>(a, blocks, stream);
+        case 4: return vec ? launch_coupled_t<true, 4>(a, blocks, stream) : launch_coupled_t<false, 4>(a, blocks, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int max_blocks_coupled(int device) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    int per = 1 << 20;
+    int v = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, coupled_kernel<true, 2>, kThreads, 0);
+    per = v < per ? v : per;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, coupled_kernel<true, 4>, kThreads, 0);
+    per = v < per ? v : per;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, coupled_kernel<false, 4>, kThreads, 0);
+    per = v < per ? v : per;
+    if (per < 1) per = 1;
+    int nb = sms * per;
+    return nb > kMaxBlocks ? kMaxBlocks : nb;
+}
 
 }  // namespace pgdto

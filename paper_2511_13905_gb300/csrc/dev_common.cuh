@@ -103,12 +103,24 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
 
 struct GridCtrl {
     unsigned count;    // arrivals in the current round
-    unsigned gen;      // round counter, bumped by the last block
+    int pad0;
     int status;        // sticky pgdto_status of device work
     int abort;         // raised by a block that gave up; every wait then returns
     unsigned long long launches;  // kernels that ran to completion (diagnostics)
-    int pad[10];
+    int pad1[26];
+    unsigned gen;      // round counter, bumped by the last block (own 128-byte line: the
+    int pad2[31];      // waiting blocks poll it while the others still arrive on `count`)
+    unsigned long long trace_start;  // globaltimer at kernel entry (block 0)
+    unsigned long long trace[62];    // globaltimer after each grid reduction's update
+    int ntrace;
+    int pad3[3];
 };
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 // Partial sums of one grid reduction: DF values (SoA over blocks) and float maxima.
 struct Partials {
@@ -158,8 +170,8 @@ __device__ __forceinline__ void block_reduce(const DF (&v)[NV], const float* mx,
 
 // Grid-wide reduction of sc.tot[0..nv) / sc.totmax[0..nm) followed by a scalar update.
 // Every block calls it with its block totals in sc.  The last block to arrive reduces all
-// partials in block order (deterministic), calls update(sc) with the grid totals in
-// sc.tot / sc.totmax on thread 0, and releases the others.  Returns false if the wait
+// partials in block order (deterministic), calls update(sc) on its warp 0 with the grid
+// totals in sc.tot / sc.totmax, and releases the others.  Returns false if the wait
 // was abandoned (timeout or abort); the caller must then return.
 template <class Update>
 __device__ bool grid_reduce_update(GridCtrl* ctrl, Partials* part, BlockScratch& sc, int nv, int nm,
@@ -182,9 +194,16 @@ __device__ bool grid_reduce_update(GridCtrl* ctrl, Partials* part, BlockScratch&
         const int lane = tid & 31, warp = tid >> 5;
         for (int i = warp; i < nv; i += kWarps) {
             DF acc = df_zero();
-            for (int b = lane; b < nb; b += 32) {
-                float2 p = __ldcg(&part->v[i][b]);
-                acc = df_add(acc, DF{p.x, p.y});
+            // 8 independent loads in flight per lane before they are summed (fixed order)
+            for (int b0 = 0; b0 < nb; b0 += 256) {
+                float2 buf[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int b = b0 + lane + 32 * k;
+                    buf[k] = b < nb ? __ldcg(&part->v[i][b]) : make_float2(0.0f, 0.0f);
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) acc = df_add(acc, DF{buf[k].x, buf[k].y});
             }
             acc = warp_reduce_df(acc);
             if (lane == 0) sc.tot[i] = acc;
@@ -196,8 +215,17 @@ __device__ bool grid_reduce_update(GridCtrl* ctrl, Partials* part, BlockScratch&
             if (lane == 0) sc.totmax[i] = acc;
         }
         __syncthreads();
+        if (tid < 32) {
+            update(sc);  // warp 0: the scalar update spreads its work over the lanes
+            __syncwarp();
+        }
         if (tid == 0) {
-            update(sc);
+            volatile GridCtrl* vc = ctrl;
+            const int k = vc->ntrace;
+            if (k >= 0 && k < 62) {
+                vc->trace[k] = globaltimer_ns();
+                vc->ntrace = k + 1;
+            }
             __threadfence();
             ctrl->count = 0u;
             __threadfence();

@@ -22,16 +22,9 @@
 
 #include "dev_common.cuh"
 #include "kernels.h"
+#include "step_common.cuh"
 
 namespace pgdto {
-
-constexpr int K = 8;           // trial points per root-search pass
-constexpr int kFoldEvery = 8;  // float4 groups accumulated in FP32 before folding into DF
-
-struct RowState {
-    double b, L, rL, SL, H, rH, SH, lam, rlast;
-    int active, passes, how, pad;
-};
 
 struct SegBcast {
     double alpha, beta, c;
@@ -54,8 +47,6 @@ size_t seg_work_bytes() { return sizeof(SegWork); }
 size_t seg_work_ctrl_bytes() { return sizeof(GridCtrl); }
 DeviceInfo* seg_work_info(SegWork* ws) { return &ws->info; }
 
-__device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
-
 __device__ __forceinline__ bool all_finite(const BlockScratch& sc, int nv) {
     for (int i = 0; i < nv; ++i)
         if (!isfinite(sc.tot[i].hi)) return false;
@@ -63,99 +54,14 @@ __device__ __forceinline__ bool all_finite(const BlockScratch& sc, int nv) {
 }
 
 // ----------------------------------------------------------------------- scalar updates
+//
+// The updates run on warp 0 of the last block.  FP64 throughput is a small fraction of
+// FP32 on this part and a division is a long dependent sequence, so the work is spread
+// over lanes: lane 8j + k handles trial point k of row j (4 rows x 8 points = 32 lanes),
+// per-row quantities are computed redundantly by the 8 lanes of the row's group, and no
+// lane waits on more than one FP64 division per pass.
 
-// Step size and PR+ coefficient (Alg. 3; eq. final_alpha, eq. alpha, eq. CG).
-__device__ void update_step_scalars(const SegArgs& a, const BlockScratch& sc, SegWork* ws) {
-    volatile SegBcast* bc = &ws->bc;
-    const double ss = df_to_double(sc.tot[0]), sy = df_to_double(sc.tot[1]), yy = df_to_double(sc.tot[2]);
-    const double gy = df_to_double(sc.tot[3]), pp = df_to_double(sc.tot[4]), gg = df_to_double(sc.tot[5]);
-    const double gmax = (double)sc.totmax[0];
-    int status = kOk;
-    if (!(isfinite(ss) && isfinite(sy) && isfinite(yy) && isfinite(gy) && isfinite(pp) && isfinite(gg)))
-        status = kErrNonfinite;
-    const double fb = gmax > 0.0 ? fmin(a.alpha_max, a.alpha_fb / gmax) : a.alpha_max;
-    double alpha;
-    int branch;
-    if (a.force_fallback || a.t == 0 || ss == 0.0) {
-        alpha = fb;
-        branch = 0;
-    } else {
-        const double lip = yy == 0.0 ? INFINITY : sqrt(ss / yy);
-        if (sy > a.eps_alpha) {
-            alpha = fmin(fmin(ss / sy, 2.0 * lip), a.alpha_max);
-            branch = 1;
-        } else {
-            alpha = fmin(lip, a.alpha_max);
-            branch = 2;
-        }
-    }
-    const double beta = (a.t == 0 || pp == 0.0) ? 0.0 : fmax(gy / pp, 0.0);
-    const double c = a.omega * alpha;
-    float h, l;
-    bc->alpha = alpha;
-    bc->beta = beta;
-    bc->c = c;
-    split_double(c, h, l);
-    bc->c_hi = h;
-    bc->c_lo = l;
-    split_double(beta, h, l);
-    bc->beta_hi = h;
-    bc->beta_lo = l;
-    bc->branch = branch;
-    bc->status = status;
-    volatile DeviceInfo* inf = &ws->info;
-    inf->alpha = alpha;
-    inf->beta = beta;
-    inf->branch = branch;
-    inf->t = a.t;
-}
-
-__device__ __forceinline__ double float_ulp(double v) {
-    float f = (float)fabs(v);
-    return (double)nextafterf(f, INFINITY) - (double)f;
-}
-
-__device__ void sort8(float* p) {
-    for (int i = 1; i < K; ++i) {
-        float v = p[i];
-        int j = i - 1;
-        while (j >= 0 && p[j] > v) {
-            p[j + 1] = p[j];
-            --j;
-        }
-        p[j + 1] = v;
-    }
-}
-
-// Next K trial points inside (L, H): Newton from both ends of the bracket (exact when the
-// bracket is one linear piece), the secant point, and a uniform fill that guarantees the
-// bracket shrinks by at least a factor 6 per pass.
-__device__ void choose_points(const RowState& r, volatile float* out) {
-    const double L = r.L, H = r.H, w = H - L;
-    double c[K];
-    c[0] = L + r.rL / r.SL;
-    c[1] = H + r.rH / r.SH;
-    c[2] = L + r.rL * w / (r.rL - r.rH);
-    for (int q = 1; q <= 5; ++q) c[2 + q] = L + w * (double)q / 6.0;
-    float p[K];
-    for (int k = 0; k < K; ++k) {
-        double v = c[k];
-        if (!(v > L && v < H)) v = L + w * ((double)k + 0.5) / (double)K;
-        float f = (float)v;
-        if (!((double)f > L && (double)f < H)) {
-            f = (float)(0.5 * (L + H));
-            if (!((double)f > L && (double)f < H)) f = (float)H;
-        }
-        p[k] = f;
-    }
-    sort8(p);
-    for (int k = 0; k < K; ++k) out[k] = p[k];
-}
-
-__device__ void finish_row(RowState& r, double lam, int how, volatile SegBcast* bc, int j) {
-    r.lam = lam;
-    r.active = 0;
-    r.how = how;
+__device__ __forceinline__ void publish_lambda(volatile SegBcast* bc, int j, double lam) {
     float h, l;
     split_double(lam, h, l);
     bc->lam_hi[j] = h;
@@ -166,153 +72,75 @@ __device__ void finish_row(RowState& r, double lam, int how, volatile SegBcast* 
 // After phase B: feasibility at lam = 0, bracket [0, H] (Alg. 1), closed form when the row
 // is violated even with every variable at its row-minimising bound (regularised root).
 __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, SegWork* ws) {
+    const int lane = threadIdx.x, j = lane >> 3, k = lane & 7;
     volatile SegBcast* bc = &ws->bc;
     volatile RowState* rows = ws->rows;
-    const int nr = a.nrows;
-    int any = 0;
-    int status = a.proj ? kOk : bc->status;
-    for (int j = 0; j < nr; ++j) {
-        const double ax = a.proj ? 0.0 : df_to_double(sc.tot[4 * j + 0]);
-        const double r0s = df_to_double(sc.tot[4 * j + 1]);
-        const double sf = df_to_double(sc.tot[4 * j + 2]);
-        const double smin = df_to_double(sc.tot[4 * j + 3]);
-        const double lsat = (double)sc.totmax[j];
-        if (!(isfinite(ax) && isfinite(r0s) && isfinite(sf) && isfinite(smin))) status = kErrNonfinite;
-        RowState r = {};
-        r.b = a.bconst[j] + ax;
-        r.passes = 0;
-        r.rlast = 0.0;
-        const double r0 = r0s - r.b;
-        ws->info.b[j] = r.b;
-        if (!(r0 > 0.0)) {
-            r.rlast = r0;
-            finish_row(r, 0.0, 0, bc, j);
+    const bool row = j < a.nrows;
+    const int jj = row ? j : 0;
+    const double two_c = 2.0 / a.C;  // one division, shared by every lane
+    const double ax = a.proj ? 0.0 : df_to_double(sc.tot[4 * jj + 0]);
+    const double r0s = df_to_double(sc.tot[4 * jj + 1]);
+    const double sf = df_to_double(sc.tot[4 * jj + 2]);
+    const double smin = df_to_double(sc.tot[4 * jj + 3]);
+    const double lsat = (double)sc.totmax[jj];
+    const bool finite = isfinite(ax) && isfinite(r0s) && isfinite(sf) && isfinite(smin);
+    const double b = a.bconst[jj] + ax;
+    const double r0 = r0s - b;
+    float Hf = (float)(lsat * (1.0 + 1e-5) + 1e-30);
+    if (!((double)Hf > 0.0)) Hf = FLT_MIN;
+    const double H = (double)Hf;
+    const double rH = smin - b - two_c * H;
+    const bool inactive = !(r0 > 0.0);
+    const bool closed = !inactive && rH > 0.0;
+    const bool search = row && finite && !inactive && !closed;
+    const double SL = sf + two_c;
+    // every lane of the group computes the row's first Newton quotients
+    double q = 0.0;
+    if (k == 0) q = r0 / SL;
+    else if (k == 1) q = rH / two_c;
+    const double NL = __shfl_sync(kFull, q, lane & ~7);
+    const double NH = H + __shfl_sync(kFull, q, (lane & ~7) + 1);
+    const float p = next_point(lane, 0.0, r0, H, rH, NL, NH);
+    if (row && k == 0) {
+        ws->info.b[j] = b;
+        rows[j].reg = two_c;
+        if (search) {
+            store_row(&rows[j], b, 0.0, r0, SL, H, rH, two_c, 0.0, 0.0, 1, 0, 2);
+            bc->active[j] = 1;
+        } else if (closed) {
+            const double lam = 0.5 * a.C * (smin - b);
+            store_row(&rows[j], b, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, lam, 0.0, 0, 0, 1);
+            publish_lambda(bc, j, lam);
         } else {
-            // every variable with a != 0 sits at its row-minimising bound for lam >= H
-            float Hf = (float)(lsat * (1.0 + 1e-5) + 1e-30);
-            if (!((double)Hf > 0.0)) Hf = FLT_MIN;
-            const double H = (double)Hf;
-            const double rH = smin - r.b - 2.0 * H / a.C;
-            if (rH > 0.0) {
-                r.rlast = 0.0;
-                finish_row(r, 0.5 * a.C * (smin - r.b), 1, bc, j);
-            } else {
-                r.L = 0.0;
-                r.rL = r0;
-                r.SL = sf + 2.0 / a.C;
-                r.H = H;
-                r.rH = rH;
-                r.SH = 2.0 / a.C;
-                r.lam = 0.0;
-                r.active = 1;
-                r.how = 2;
-                bc->active[j] = 1;
-                choose_points(r, bc->pts[j]);
-                any = 1;
-            }
+            store_row(&rows[j], b, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, r0, 0, 0, 0);
+            publish_lambda(bc, j, 0.0);
         }
-        rows[j].b = r.b;
-        rows[j].L = r.L;
-        rows[j].rL = r.rL;
-        rows[j].SL = r.SL;
-        rows[j].H = r.H;
-        rows[j].rH = r.rH;
-        rows[j].SH = r.SH;
-        rows[j].lam = r.lam;
-        rows[j].rlast = r.rlast;
-        rows[j].active = r.active;
-        rows[j].passes = r.passes;
-        rows[j].how = r.how;
     }
-    if (status != kOk) any = 0;
-    bc->status = status;
-    bc->any_active = any;
-}
-
-// After a root-search pass: move the bracket, test convergence, choose the next points.
-__device__ void update_after_pass(const SegArgs& a, const BlockScratch& sc, SegWork* ws) {
-    volatile SegBcast* bc = &ws->bc;
-    volatile RowState* rows = ws->rows;
-    int any = 0;
-    for (int j = 0; j < a.nrows; ++j) {
-        if (!rows[j].active) continue;
-        RowState r;
-        r.b = rows[j].b;
-        r.L = rows[j].L;
-        r.rL = rows[j].rL;
-        r.SL = rows[j].SL;
-        r.H = rows[j].H;
-        r.rH = rows[j].rH;
-        r.SH = rows[j].SH;
-        r.passes = rows[j].passes + 1;
-        r.active = 1;
-        r.how = 2;
-        r.rlast = 0.0;
-        double exact = -1.0;
-        double rk[K], Sk[K], lk[K];
-        for (int k = 0; k < K; ++k) {
-            lk[k] = (double)bc->pts[j][k];
-            rk[k] = df_to_double(sc.tot[2 * K * j + k]) - r.b - 2.0 * lk[k] / a.C;
-            Sk[k] = df_to_double(sc.tot[2 * K * j + K + k]) + 2.0 / a.C;
-        }
-        // new lower end: the largest point with r > 0; new upper end: the smallest point
-        // above it with r <= 0 (points the rounding noise puts out of order are ignored)
-        for (int k = 0; k < K; ++k)
-            if (rk[k] > 0.0 && lk[k] > r.L && lk[k] < r.H) {
-                r.L = lk[k];
-                r.rL = rk[k];
-                r.SL = Sk[k];
-            }
-        for (int k = 0; k < K; ++k)
-            if (!(rk[k] > 0.0) && lk[k] > r.L && lk[k] < r.H) {
-                r.H = lk[k];
-                r.rH = rk[k];
-                r.SH = Sk[k];
-                if (rk[k] == 0.0) exact = lk[k];
-            }
-        const double NL = r.L + r.rL / r.SL;
-        const double NH = r.H + r.rH / r.SH;
-        const double w = r.H - r.L;
-        const double tol = a.tol_lambda * fmax(fabs(r.H), 1e-300);
-        double root = -1.0;
-        if (exact >= 0.0) {
-            root = exact;
-        } else if (fabs(NL - NH) <= tol) {
-            root = fmin(fmax(0.5 * (NL + NH), r.L), r.H);
-        } else if (w <= tol || w <= 4.0 * float_ulp(r.H)) {
-            root = fmin(fmax(0.5 * (NL + NH), r.L), r.H);
-        }
-        if (root < 0.0 && r.passes >= a.max_passes) {
-            root = fmin(fmax(r.L + r.rL * w / (r.rL - r.rH), r.L), r.H);
-            r.how = 3;  // not converged
-        }
-        if (root >= 0.0) {
-            r.rlast = fmax(fabs(r.rL), fabs(r.rH));
-            finish_row(r, root, r.how, bc, j);
-        } else {
-            choose_points(r, bc->pts[j]);
-            any = 1;
-        }
-        rows[j].L = r.L;
-        rows[j].rL = r.rL;
-        rows[j].SL = r.SL;
-        rows[j].H = r.H;
-        rows[j].rH = r.rH;
-        rows[j].SH = r.SH;
-        rows[j].lam = r.lam;
-        rows[j].rlast = r.rlast;
-        rows[j].active = r.active;
-        rows[j].passes = r.passes;
-        rows[j].how = r.how;
+    if (search) bc->pts[j][k] = p;
+    const unsigned any = __ballot_sync(kFull, search);
+    const unsigned bad = __ballot_sync(kFull, row && !finite);
+    if (lane == 0) {
+        int status = a.proj ? kOk : bc->status;
+        if (bad) status = kErrNonfinite;
+        bc->status = status;
+        bc->any_active = (status == kOk && any) ? 1 : 0;
     }
-    bc->any_active = any;
 }
 
 // After phase D: the report.
 __device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegWork* ws) {
+    const int lane = threadIdx.x;
     volatile DeviceInfo* inf = &ws->info;
     volatile RowState* rows = ws->rows;
     volatile SegBcast* bc = &ws->bc;
+    double rc = 0.0;
+    if (lane == 1 && !a.proj) {
+        const double dd = df_to_double(sc.tot[a.nrows]);
+        const double nn = df_to_double(sc.tot[a.nrows + 1]);
+        rc = nn > 0.0 ? sqrt(dd / nn) : INFINITY;
+    }
+    rc = __shfl_sync(kFull, rc, 1);
+    if (lane != 0) return;
     int status = bc->status;
     int passes = 0;
     double phi = 0.0;
@@ -332,9 +160,7 @@ __device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegWork* 
         inf->b[j] = 0.0;
     }
     if (!a.proj) {
-        const double dd = df_to_double(sc.tot[a.nrows]);
-        const double nn = df_to_double(sc.tot[a.nrows + 1]);
-        inf->rel_change = nn > 0.0 ? sqrt(dd / nn) : INFINITY;
+        inf->rel_change = rc;
     } else {
         inf->rel_change = 0.0;
         inf->alpha = 0.0;
@@ -362,52 +188,6 @@ __device__ void report_status_only(const SegArgs& a, SegWork* ws, int status) {
 
 // ----------------------------------------------------------------------- element passes
 
-template <int N>
-struct Acc {
-    float f[N];
-    DF d[N];
-    int cnt;
-    __device__ __forceinline__ void init() {
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            f[i] = 0.0f;
-            d[i] = df_zero();
-        }
-        cnt = 0;
-    }
-    __device__ __forceinline__ void fold() {
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-            d[i] = df_add_f(d[i], f[i]);
-            f[i] = 0.0f;
-        }
-        cnt = 0;
-    }
-    __device__ __forceinline__ void tick() {
-        if (++cnt == kFoldEvery) fold();
-    }
-};
-
-// Iterate the block's share [cb, ce): f4(v) for aligned float4 groups v (elements 4v..4v+3),
-// f1(i) for the unaligned head and tail, then tick() per group.
-template <bool VEC, class F4, class F1>
-__device__ __forceinline__ void for_chunk(int64_t cb, int64_t ce, F4&& f4, F1&& f1) {
-    if (VEC) {
-        int64_t vb = (cb + 3) & ~int64_t(3);
-        if (vb > ce) vb = ce;
-        int64_t ve = ce & ~int64_t(3);
-        if (ve < vb) ve = vb;
-        for (int64_t i = cb + threadIdx.x; i < vb; i += blockDim.x) f1(i);
-        for (int64_t v = (vb >> 2) + threadIdx.x; v < (ve >> 2); v += blockDim.x) f4(v);
-        for (int64_t i = ve + threadIdx.x; i < ce; i += blockDim.x) f1(i);
-    } else {
-        for (int64_t i = cb + threadIdx.x; i < ce; i += blockDim.x) f1(i);
-    }
-}
-
-#define LD4(p, v) (__ldcs(reinterpret_cast<const float4*>(p) + (v)))
-#define LD4L2(p, v) (__ldcg(reinterpret_cast<const float4*>(p) + (v)))
-
 template <bool VEC>
 __global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
     __shared__ BlockScratch sc;
@@ -415,6 +195,11 @@ __global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
     SegWork* ws = a.ws;
     if (ld_volatile_i32(&ws->ctrl.abort)) return;
     const int nb = gridDim.x, blk = blockIdx.x;
+    if (blk == 0 && threadIdx.x == 0) {
+        volatile GridCtrl* vc = &ws->ctrl;
+        vc->trace_start = globaltimer_ns();
+        vc->ntrace = 0;
+    }
     const float lo = a.lo, hi = a.hi;
 
     if (!a.proj) {
@@ -475,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
             block_reduce<6, 1>(acc.d, mx, sc);
         }
         if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 6, 1, a.timeout_cycles,
-                                [&](BlockScratch& s) { update_step_scalars(a, s, ws); }))
+                                [&](BlockScratch& s) { update_step_scalars(a, s, &ws->bc, &ws->info); }))
             return;
         load_cg(bc, &ws->bc);
         if (bc.status != kOk) {
@@ -647,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
             block_reduce<2 * K, 0>(acc.d, nullptr, sc, 2 * K * j, 0);
         }
         if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 2 * K * a.nrows, 0, a.timeout_cycles,
-                                [&](BlockScratch& s) { update_after_pass(a, s, ws); }))
+                                [&](BlockScratch& s) { search_pass_update(s, 0, ws->rows, &ws->bc, a.nrows, a.tol_lambda, a.max_passes); }))
             return;
         load_cg(bc, &ws->bc);
     }

@@ -1,0 +1,277 @@
+// step_common.cuh -- pieces shared by the single/independent-row and the coupled-row
+// kernels: per-thread accumulators, the block-share iterator, the step-size update of
+// Alg. 3, and the warp-parallel one-dimensional root search used for Alg. 1 rows and for
+// the exact line search of the coupled Newton iteration.
+#pragma once
+
+#include <float.h>
+#include <math.h>
+
+#include "dev_common.cuh"
+#include "kernels.h"
+
+namespace pgdto {
+
+constexpr int K = 8;           // trial points per root-search pass
+constexpr int kFoldEvery = 8;  // float4 groups accumulated in FP32 before folding into DF
+constexpr unsigned kFull = 0xffffffffu;
+
+// State of one monotone piecewise-linear root search r(t) = S(t) - b - reg t = 0 on [L, H]
+// with r(L) > 0 >= r(H); SL, SH are the slopes -dr/dt at the ends.
+struct RowState {
+    double b, L, rL, SL, H, rH, SH, lam, rlast, reg;
+    int active, passes, how, pad;
+};
+
+__device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
+
+// ----------------------------------------------------------------------- scalar updates
+//
+// The updates run on warp 0 of the last block.  FP64 throughput is a small fraction of
+// FP32 on this part and a division is a long dependent sequence, so the work is spread
+// over lanes: lane 8j + k handles trial point k of search j (4 searches x 8 points = 32
+// lanes), per-search quantities are computed redundantly by the 8 lanes of the group,
+// and no lane waits on more than one FP64 division per pass.
+
+// Step size and PR+ coefficient (Alg. 3; eq. final_alpha, eq. alpha, eq. CG).
+template <class Args, class Bcast>
+__device__ void update_step_scalars(const Args& a, const BlockScratch& sc, volatile Bcast* bc,
+                                    volatile DeviceInfo* inf) {
+    const int lane = threadIdx.x;
+    const double ss = df_to_double(sc.tot[0]), sy = df_to_double(sc.tot[1]), yy = df_to_double(sc.tot[2]);
+    const double gy = df_to_double(sc.tot[3]), pp = df_to_double(sc.tot[4]), gg = df_to_double(sc.tot[5]);
+    const double gmax = (double)sc.totmax[0];
+    double q = 0.0;
+    if (lane == 0) q = ss / sy;                                      // BB1 ratio s's / s'y
+    else if (lane == 1) q = yy > 0.0 ? sqrt(ss / yy) : INFINITY;     // ||s|| / ||y||
+    else if (lane == 2) q = pp > 0.0 ? gy / pp : 0.0;                // PR coefficient
+    else if (lane == 3) q = gmax > 0.0 ? a.alpha_fb / gmax : INFINITY;  // fallback alpha_fb / ||g||_inf
+    const double bb = __shfl_sync(kFull, q, 0), lip = __shfl_sync(kFull, q, 1);
+    const double pr = __shfl_sync(kFull, q, 2), fbq = __shfl_sync(kFull, q, 3);
+    if (lane != 0) return;
+    int status = kOk;
+    if (!(isfinite(ss) && isfinite(sy) && isfinite(yy) && isfinite(gy) && isfinite(pp) && isfinite(gg)))
+        status = kErrNonfinite;
+    const double fb = fmin(a.alpha_max, fbq);
+    double alpha;
+    int branch;
+    if (a.force_fallback || a.t == 0 || ss == 0.0) {
+        alpha = fb;
+        branch = 0;
+    } else if (sy > a.eps_alpha) {
+        alpha = fmin(fmin(bb, 2.0 * lip), a.alpha_max);
+        branch = 1;
+    } else {
+        alpha = fmin(lip, a.alpha_max);
+        branch = 2;
+    }
+    const double beta = a.t == 0 ? 0.0 : fmax(pr, 0.0);
+    const double c = a.omega * alpha;
+    float h, l;
+    bc->alpha = alpha;
+    bc->beta = beta;
+    bc->c = c;
+    split_double(c, h, l);
+    bc->c_hi = h;
+    bc->c_lo = l;
+    split_double(beta, h, l);
+    bc->beta_hi = h;
+    bc->beta_lo = l;
+    bc->branch = branch;
+    bc->status = status;
+    inf->alpha = alpha;
+    inf->beta = beta;
+    inf->branch = branch;
+    inf->t = a.t;
+}
+
+
+__device__ __forceinline__ double float_ulp(double v) {
+    float f = (float)fabs(v);
+    return (double)nextafterf(f, INFINITY) - (double)f;
+}
+
+// Ascending bitonic sort of one float per lane within aligned groups of 8 lanes.
+__device__ __forceinline__ float group8_sort(float v, int lane) {
+    const int i = lane & 7;
+#pragma unroll
+    for (int size = 2; size <= 8; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const float o = __shfl_xor_sync(kFull, v, stride);
+            const bool up = (i & size) == 0;
+            const bool lower = (i & stride) == 0;
+            v = (lower == up) ? fminf(v, o) : fmaxf(v, o);
+        }
+    }
+    return v;
+}
+
+// Trial point k of the next pass inside (L, H): Newton from the lower end (k = 0), from the
+// upper end (k = 1), the secant point (k = 2), and a uniform fill (k = 3..7) that
+// guarantees the bracket shrinks by at least a factor 6.  Returns the group-sorted value.
+__device__ __forceinline__ float next_point(int lane, double L, double rL, double H, double rH, double NL,
+                                            double NH) {
+    const int k = lane & 7;
+    const double w = H - L;
+    double v;
+    if (k == 0) v = NL;
+    else if (k == 1) v = NH;
+    else if (k == 2) v = L + rL * w / (rL - rH);
+    else v = L + w * (double)(k - 2) * (1.0 / 6.0);
+    if (!(v > L && v < H)) v = L + w * ((double)k + 0.5) * 0.125;
+    float f = (float)v;
+    if (!((double)f > L && (double)f < H)) {
+        f = (float)(0.5 * (L + H));
+        if (!((double)f > L && (double)f < H)) f = (float)H;
+    }
+    return group8_sort(f, lane);
+}
+
+__device__ __forceinline__ void store_row(volatile RowState* r, double b, double L, double rL, double SL, double H,
+                                          double rH, double SH, double lam, double rlast, int active, int passes,
+                                          int how) {
+    r->b = b;  // reg (the slope of the regulariser term) is set once when the search starts
+    r->L = L;
+    r->rL = rL;
+    r->SL = SL;
+    r->H = H;
+    r->rH = rH;
+    r->SH = SH;
+    r->lam = lam;
+    r->rlast = rlast;
+    r->active = active;
+    r->passes = passes;
+    r->how = how;
+}
+
+template <class Bcast>
+__device__ __forceinline__ void publish_lambda(volatile Bcast* bc, int j, double lam) {
+    float h, l;
+    split_double(lam, h, l);
+    bc->lam_hi[j] = h;
+    bc->lam_lo[j] = l;
+    bc->active[j] = 0;
+}
+
+// One pass of the root searches: the pass evaluated, for each active search j, the sums
+// S(t_k) (tot[base + 2K j + k]) and the free-set curvature (tot[base + 2K j + K + k]) at the
+// points bc->pts[j][k].  Moves each bracket, stops a search when Newton from both ends of
+// its bracket agrees (both ends on one linear piece), when the bracket is within tol or
+// a few float spacings, or at max_passes (flagged), and writes the next points.
+template <class Bcast>
+__device__ void search_pass_update(const BlockScratch& sc, int base, volatile RowState* rows, volatile Bcast* bc,
+                                   int nsearch, double tol_lambda, int max_passes) {
+    const int lane = threadIdx.x, j = lane >> 3, k = lane & 7, g0 = lane & ~7;
+    const int jj = j < nsearch ? j : 0;
+    const bool row = j < nsearch && rows[jj].active;
+    const double reg = rows[jj].reg;
+    const double b = rows[jj].b;
+    double L = rows[jj].L, rL = rows[jj].rL, SL = rows[jj].SL;
+    double H = rows[jj].H, rH = rows[jj].rH, SH = rows[jj].SH;
+    const int passes = rows[jj].passes + 1;
+    const double lk = (double)bc->pts[jj][k];
+    const double rk = df_to_double(sc.tot[base + 2 * K * jj + k]) - b - reg * lk;
+    const double Sk = df_to_double(sc.tot[base + 2 * K * jj + K + k]) + reg;
+    // new lower end: the largest point with r > 0; new upper end: the smallest point above
+    // it with r <= 0 (points the rounding noise puts out of order are ignored)
+    const unsigned pos = (__ballot_sync(kFull, row && rk > 0.0 && lk > L && lk < H) >> g0) & 0xffu;
+    const int kL = pos ? 31 - __clz(pos) : -1;
+    const double lL = __shfl_sync(kFull, lk, g0 + (kL < 0 ? 0 : kL));
+    const double rLn = __shfl_sync(kFull, rk, g0 + (kL < 0 ? 0 : kL));
+    const double SLn = __shfl_sync(kFull, Sk, g0 + (kL < 0 ? 0 : kL));
+    if (kL >= 0) {
+        L = lL;
+        rL = rLn;
+        SL = SLn;
+    }
+    const unsigned neg = (__ballot_sync(kFull, row && !(rk > 0.0) && lk > L && lk < H) >> g0) & 0xffu;
+    const int kH = neg ? __ffs(neg) - 1 : -1;
+    const double hH = __shfl_sync(kFull, lk, g0 + (kH < 0 ? 0 : kH));
+    const double rHn = __shfl_sync(kFull, rk, g0 + (kH < 0 ? 0 : kH));
+    const double SHn = __shfl_sync(kFull, Sk, g0 + (kH < 0 ? 0 : kH));
+    if (kH >= 0) {
+        H = hH;
+        rH = rHn;
+        SH = SHn;
+    }
+    double q = 0.0;
+    if (k == 0) q = rL / SL;
+    else if (k == 1) q = rH / SH;
+    const double NL = L + __shfl_sync(kFull, q, g0);
+    const double NH = H + __shfl_sync(kFull, q, g0 + 1);
+    const double w = H - L;
+    const double tol = tol_lambda * fmax(fabs(H), 1e-300);
+    double root = -1.0;
+    int how = 2;
+    if (kH >= 0 && rH == 0.0) root = H;
+    else if (fabs(NL - NH) <= tol || w <= tol || w <= 4.0 * float_ulp(H)) root = fmin(fmax(0.5 * (NL + NH), L), H);
+    if (root < 0.0 && passes >= max_passes) {
+        root = fmin(fmax(0.5 * (NL + NH), L), H);
+        how = 3;  // not converged
+    }
+    const bool done = row && root >= 0.0;
+    const float p = next_point(lane, L, rL, H, rH, NL, NH);
+    if (row && k == 0) {
+        if (done) {
+            store_row(&rows[j], b, L, rL, SL, H, rH, SH, root, fmax(fabs(rL), fabs(rH)), 0, passes, how);
+            publish_lambda(bc, j, root);
+        } else {
+            store_row(&rows[j], b, L, rL, SL, H, rH, SH, 0.0, 0.0, 1, passes, 2);
+        }
+    }
+    if (row && !done) bc->pts[j][k] = p;
+    const unsigned still = __ballot_sync(kFull, row && !done);
+    if (lane == 0) bc->any_active = still ? 1 : 0;
+}
+
+// ----------------------------------------------------------------------- element passes
+
+template <int N>
+struct Acc {
+    float f[N];
+    DF d[N];
+    int cnt;
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            f[i] = 0.0f;
+            d[i] = df_zero();
+        }
+        cnt = 0;
+    }
+    __device__ __forceinline__ void fold() {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            d[i] = df_add_f(d[i], f[i]);
+            f[i] = 0.0f;
+        }
+        cnt = 0;
+    }
+    __device__ __forceinline__ void tick() {
+        if (++cnt == kFoldEvery) fold();
+    }
+};
+
+// Iterate the block's share [cb, ce): f4(v) for aligned float4 groups v (elements 4v..4v+3),
+// f1(i) for the unaligned head and tail, then tick() per group.
+template <bool VEC, class F4, class F1>
+__device__ __forceinline__ void for_chunk(int64_t cb, int64_t ce, F4&& f4, F1&& f1) {
+    if (VEC) {
+        int64_t vb = (cb + 3) & ~int64_t(3);
+        if (vb > ce) vb = ce;
+        int64_t ve = ce & ~int64_t(3);
+        if (ve < vb) ve = vb;
+        for (int64_t i = cb + threadIdx.x; i < vb; i += blockDim.x) f1(i);
+        for (int64_t v = (vb >> 2) + threadIdx.x; v < (ve >> 2); v += blockDim.x) f4(v);
+        for (int64_t i = ve + threadIdx.x; i < ce; i += blockDim.x) f1(i);
+    } else {
+        for (int64_t i = cb + threadIdx.x; i < ce; i += blockDim.x) f1(i);
+    }
+}
+
+#define LD4(p, v) (__ldcs(reinterpret_cast<const float4*>(p) + (v)))
+#define LD4L2(p, v) (__ldcg(reinterpret_cast<const float4*>(p) + (v)))
+
+
+}  // namespace pgdto

@@ -1,0 +1,130 @@
+"""Parity of the coupled-row CUDA path (Alg. 2: single-row candidates, then Newton on the
+m x m Jacobian) with the FP64 oracle's exact optimum, through the C ABI."""
+
+import numpy as np
+import pytest
+
+from oracle import oracle_step
+from oracle import projection as P
+from oracle.checks import parity_errors
+from paper_2511_13905_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+C = 1e12
+TOL = {"lam_rel": 1e-6, "x_abs": 1e-6, "viol_rel": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def dev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch.device("cuda:0")
+
+
+def T(a, dev):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+def check(err, what=""):
+    bad = {k: err[k] for k in TOL if not err[k] <= TOL[k]}
+    assert not bad, "%s parity: %s (all: %s)" % (what, bad, {k: err[k] for k in TOL})
+
+
+def run_project(dev, z, A, b, lo=0.0, hi=1.0):
+    import torch
+    from paper_2511_13905_gb300 import binding
+    m, n = A.shape
+    h = binding.Handle(n, m, lo=lo, hi=hi, mode="coupled")
+    zt, At = T(z, dev), T(A, dev)
+    xt = torch.empty_like(zt)
+    st, lam, info = h.project(zt, At, b, xt)
+    torch.cuda.synchronize()
+    out = xt.cpu().numpy().astype(np.float64)
+    h.close()
+    return st, np.array(lam), out, info
+
+
+def coupled_problem(n, m, seed, feasible=True):
+    rng = np.random.default_rng(seed)
+    z = rng.uniform(-0.2, 1.2, n)
+    A = np.vstack([np.ones(n)] + [rng.uniform(-1, 1, n) for _ in range(m - 1)])
+    xin = rng.uniform(0.2, 0.6, n)
+    b = A @ xin
+    b[0] = 0.4 * n
+    if not feasible:
+        # the last row cannot hold for x >= 0; the other rows hold at x = 0 so only that row
+        # needs the regularisation (two rows infeasible together make the optimum hinge on
+        # cancellations of size C |b| that FP32 data cannot carry)
+        A[m - 1] = np.abs(A[m - 1]) + 0.05
+        b[m - 1] = -0.01 * n
+        b[1:m - 1] = np.abs(b[1:m - 1]) + 1.0
+    return z.astype(np.float32), A.astype(np.float32), b
+
+
+@pytest.mark.parametrize("n,m,seed,feasible", [
+    (1000, 2, 1, True), (4096, 3, 2, True), (65536, 4, 3, True), (100003, 4, 4, True),
+    (20000, 2, 5, False), (50000, 4, 6, False), (1 << 20, 4, 7, True)])
+def test_project_coupled(dev, n, m, seed, feasible):
+    z, A, b = coupled_problem(n, m, seed, feasible)
+    st, lam, x, info = run_project(dev, z, A, b)
+    assert st == 0, (st, info.as_dict(m))
+    z64, A64 = z.astype(np.float64), A.astype(np.float64)
+    lam_ref, rinfo = P.solve_coupled_exact(z64, A64, b, 0.0, 1.0, C)
+    assert rinfo["kkt"]["worst"] < 1e-9
+    x_ref = P.primal_from_dual(z64, A64, lam_ref, 0.0, 1.0)
+    check(parity_errors(x, lam, x_ref, lam_ref, A, b, C, 0.0, 1.0),
+          "n=%d m=%d ref=%s info=%s" % (n, m, lam_ref, info.as_dict(m)))
+
+
+def test_project_coupled_stage1_accepts_single_row(dev):
+    """Only the volume row binds: Alg. 2 stage 1 finds it without Newton."""
+    rng = np.random.default_rng(11)
+    n = 40000
+    z = rng.uniform(0.0, 1.0, n).astype(np.float32)
+    A = np.vstack([np.ones(n), rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)]).astype(np.float32)
+    b = np.array([0.3 * n, 1e6, 1e6])
+    st, lam, x, info = run_project(dev, z, A, b)
+    assert st == 0, info.as_dict(3)
+    assert info.stage == 1 and info.newton_iters == 0
+    lam_ref, _ = P.solve_coupled_exact(z.astype(np.float64), A.astype(np.float64), b, 0.0, 1.0, C)
+    x_ref = P.primal_from_dual(z.astype(np.float64), A.astype(np.float64), lam_ref, 0.0, 1.0)
+    check(parity_errors(x, lam, x_ref, lam_ref, A, b, C, 0.0, 1.0), "stage 1")
+
+
+def test_project_coupled_all_inactive(dev):
+    rng = np.random.default_rng(12)
+    n = 5000
+    z = rng.uniform(-0.5, 1.5, n).astype(np.float32)
+    A = rng.uniform(0.1, 1.0, (3, n)).astype(np.float32)
+    b = A.astype(np.float64) @ np.clip(z, 0, 1).astype(np.float64) + 10.0
+    st, lam, x, info = run_project(dev, z, A, b)
+    assert st == 0
+    assert np.all(lam == 0.0)
+    assert np.array_equal(x, np.clip(z, 0, 1).astype(np.float64))
+
+
+@pytest.mark.parametrize("dims,infeasible", [((32, 16, 16), False), ((64, 32, 32), False),
+                                             ((32, 16, 16), True), (None, False)])
+def test_step_config4(dev, dims, infeasible):
+    import torch
+    from paper_2511_13905_gb300 import binding
+    cfg = inputs.config4(dims=dims, infeasible=infeasible)
+    n, m = cfg["n"], cfg["m"]
+    h = binding.Handle(n, m, mode="coupled")
+    h.set_state(T(cfg["x_prev"], dev), T(cfg["g_prev"], dev), T(cfg["d_prev"], dev), cfg["t"])
+    x = T(cfg["x"], dev)
+    st, info = h.step(x, T(cfg["g"], dev), T(cfg["A"], dev), cfg["gval"], cfg["G"])
+    torch.cuda.synchronize()
+    assert st == 0, info.as_dict(m)
+    ref = oracle_step(cfg["x"], cfg["x_prev"], cfg["g"], cfg["g_prev"], cfg["d_prev"], cfg["A"], cfg["gval"],
+                      cfg["G"], cfg["t"], mode="coupled")
+    assert info.alpha == pytest.approx(ref["alpha"], rel=1e-6)
+    assert info.beta == pytest.approx(ref["beta"], rel=1e-6, abs=1e-12)
+    lam = np.array(list(info.lambda_)[:m])
+    check(parity_errors(x.cpu().numpy(), lam, ref["x_new"], ref["lam"], cfg["A"], ref["b"], C, 0.0, 1.0),
+          cfg["name"])
+    h.close()
