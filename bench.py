@@ -123,6 +123,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def combine_ranks(total_s, steps, world, device=None):
+    """Job value over ranks: every rank ran `steps` independent steps in `total_s` seconds;
+    the job's time is the slowest rank's (MAX all-reduce), its work the sum of all ranks'."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(total_s)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    return world * steps / total_s, total_s
+
+
 def algorithmic_bytes(n, m_eff, passes):
     """Streaming bytes of one step: 16 + (20 + 4 m_eff) + 4 (1 + m_eff) P + (12 + 4 m_eff) per element."""
     return n * (16 + (20 + 4 * m_eff) + 4 * (1 + m_eff) * passes + (12 + 4 * m_eff))
@@ -231,12 +243,7 @@ def run_ours(args, rank, world, local_rank):
     launches = h.kernel_launches() - launches0
     clk = clocks.stop()
     times_ms = [a.elapsed_time(b) for a, b in evs]
-    total_s = sum(times_ms) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_s = float(tt.item())
+    value, total_s = combine_ranks(sum(times_ms) / 1e3, args.steps, world, dev)
 
     # end to end through the host-buffer entry point (pinned memory, copies inside the timing)
     xh = torch.from_numpy(cfg["x"].copy()).pin_memory()
@@ -257,12 +264,7 @@ def run_ours(args, rank, world, local_rank):
         if not trajectory:
             xh.copy_(torch.from_numpy(cfg["x"]))
             reset()
-    e2e_total = sum(e2e_times)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_total = float(tt.item())
+    e2e_value, e2e_total = combine_ranks(sum(e2e_times), len(e2e_times), world, dev)
     a_bytes = 4 * (m * n if cfg["mode"] == "coupled" or wl in (1, 2) else n)
     h2d = 4 * n * 2 + a_bytes
     d2h = 4 * n
@@ -274,7 +276,7 @@ def run_ours(args, rank, world, local_rank):
     achieved = alg_bytes / step_s / 1e9
     result = {
         "metric": "PGD-TO optimizer steps/s",
-        "value": world * args.steps / total_s,
+        "value": value,
         "unit": "steps/s",
         "n_gpus": world,
         "steps": args.steps,
@@ -294,7 +296,7 @@ def run_ours(args, rank, world, local_rank):
                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback", "kernel": "pgdto::seg_kernel (fused step)",
                      "algorithmic_bytes_per_launch": alg_bytes},
-        "e2e": {"value": world * len(e2e_times) / e2e_total, "unit": "steps/s", "h2d_bytes_per_step": h2d,
+        "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "api": "pgdto_step_host (pinned host buffers)"},
         "gpu_launches": launches,
         "clocks": clk,

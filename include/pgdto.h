@@ -78,6 +78,9 @@ typedef struct {
     int max_passes;         /* cap on root-search passes per projection, 64 */
     int barrier_timeout_ms; /* budget of each device-side wait, 2000 */
     pgdto_mode mode;        /* PGDTO_AUTO */
+    int fault_inject;       /* tests only: 1 = block 0 leaves before the first grid reduction,
+                               so the others' waits run out and the call reports
+                               PGDTO_ERR_TIMEOUT (no fault, trap or hang); 0 = off */
 } pgdto_params;
 
 /* Per-call report. */

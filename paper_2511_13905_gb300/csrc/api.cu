@@ -72,6 +72,7 @@ extern "C" pgdto_status pgdto_params_default(pgdto_params* p) {
     p->max_passes = 64;
     p->barrier_timeout_ms = 2000;
     p->mode = PGDTO_AUTO;
+    p->fault_inject = 0;
     return PGDTO_OK;
 }
 
@@ -95,7 +96,8 @@ static void free_handle(pgdto_handle* h) {
 static bool params_ok(const pgdto_params& p) {
     return p.C > 0 && isfinite(p.C) && p.alpha_max > 0 && p.alpha_fallback > 0 && p.tol_N >= 0 && p.omega > 0 &&
            p.eps_alpha >= 0 && p.tol_lambda > 0 && p.tol_lambda < 1e-2 && p.t_warmup >= 0 &&
-           p.maxiter_newton >= 1 && p.max_passes >= 1 && p.max_passes <= 100000 && p.barrier_timeout_ms >= 1;
+           p.maxiter_newton >= 1 && p.max_passes >= 1 && p.max_passes <= 100000 && p.barrier_timeout_ms >= 1 &&
+           (p.fault_inject == 0 || p.fault_inject == 1);
 }
 
 extern "C" pgdto_status pgdto_create(pgdto_handle** out, int64_t n, int m, const int64_t* seg_offsets, float lo,
@@ -296,6 +298,7 @@ static pgdto_status launch(pgdto_handle* h, bool proj, float* x, const float* g,
         a.c1 = h->p.c1;
         a.max_passes = h->p.max_passes;
         a.maxiter_newton = h->p.maxiter_newton;
+        a.fault_inject = h->p.fault_inject;
         a.timeout_cycles = h->timeout_cycles;
         a.ws = (CoupledWork*)h->work;
         e = launch_coupled(a, h->blocks, h->stream);
@@ -329,6 +332,7 @@ static pgdto_status launch(pgdto_handle* h, bool proj, float* x, const float* g,
         a.omega = h->p.omega;
         a.tol_lambda = h->p.tol_lambda;
         a.max_passes = h->p.max_passes;
+        a.fault_inject = h->p.fault_inject;
         a.timeout_cycles = h->timeout_cycles;
         a.ws = (SegWork*)h->work;
         e = launch_seg(a, h->blocks, h->stream);

@@ -42,6 +42,7 @@ struct SegArgs {
     double bconst[kMaxRows];  // step: G_j - g_j(x_t); projection: b_j
     double C, alpha_max, alpha_fb, eps_alpha, omega, tol_lambda;
     int max_passes;
+    int fault_inject;
     long long timeout_cycles;
     SegWork* ws;
 };
@@ -68,6 +69,7 @@ struct CoupledArgs {
     double bconst[kMaxRows];
     double C, alpha_max, alpha_fb, eps_alpha, omega, tol_lambda, tol_N, c1;
     int max_passes, maxiter_newton;
+    int fault_inject;
     long long timeout_cycles;
     CoupledWork* ws;
 };
