@@ -81,6 +81,10 @@ typedef struct {
     int fault_inject;       /* tests only: 1 = block 0 leaves before the first grid reduction,
                                so the others' waits run out and the call reports
                                PGDTO_ERR_TIMEOUT (no fault, trap or hang); 0 = off */
+    int engine;             /* 0 auto, 1 grid (all SMs, grid-wide reductions), 2 cluster (one
+                               thread-block cluster, reductions in distributed shared memory;
+                               single and independent rows only).  Auto: cluster for n up to
+                               the handle's threshold, grid above it */
 } pgdto_params;
 
 /* Per-call report. */
@@ -174,6 +178,23 @@ pgdto_status pgdto_step_host(pgdto_handle* h, float* x, const float* grad_f, con
  */
 pgdto_status pgdto_project(pgdto_handle* h, const float* z, const float* A, const double* b,
                            float* x_out, double* lambda_out, pgdto_info* info);
+
+/*
+ * Batched form: `count` independent steps in ONE launch (the cluster engine runs one
+ * problem per thread-block cluster and takes the next from the list).  Handles must be in
+ * SINGLE or INDEPENDENT mode and share the first handle's stream.  Per handle k:
+ * x[k], grad_f[k], A[k] as for pgdto_step; g_val[4k + j], G[4k + j] its row scalars.
+ * Each handle's state advances as after pgdto_step.  infos: NULL for an asynchronous
+ * call, else `count` reports (waits for the stream).  The list of problems is uploaded
+ * to a device buffer owned by the first handle (grown on demand).
+ */
+pgdto_status pgdto_step_many(int count, pgdto_handle* const* hs, float* const* x, const float* const* grad_f,
+                             const float* const* A, const double* g_val, const double* G, pgdto_info* infos);
+
+/* Batched projections, same conventions: z[k], A[k], b[4k + j], x_out[k]; lambda_out[4k + j]. */
+pgdto_status pgdto_project_many(int count, pgdto_handle* const* hs, const float* const* z,
+                                const float* const* A, const double* b, float* const* x_out,
+                                double* lambda_out, pgdto_info* infos);
 
 /* Wait for the handle's stream and report the last step or projection. */
 pgdto_status pgdto_last_info(pgdto_handle* h, pgdto_info* info, double* lambda_out);

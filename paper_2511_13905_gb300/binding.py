@@ -34,7 +34,7 @@ class Params(ctypes.Structure):
                 ("eps_alpha", ctypes.c_double), ("c1", ctypes.c_double), ("c2", ctypes.c_double),
                 ("tol_lambda", ctypes.c_double), ("t_warmup", ctypes.c_int), ("maxiter_newton", ctypes.c_int),
                 ("max_passes", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int), ("mode", ctypes.c_int),
-                ("fault_inject", ctypes.c_int)]
+                ("fault_inject", ctypes.c_int), ("engine", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -87,6 +87,10 @@ def load(path=None):
         "pgdto_last_info": (ctypes.c_int, [H, ctypes.POINTER(Info), D]),
         "pgdto_kernel_launches": (ctypes.c_int64, [H]),
         "pgdto_trace": (ctypes.c_int, [H, D, ctypes.c_int]),
+        "pgdto_step_many": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(H), ctypes.POINTER(P), ctypes.POINTER(P),
+                                           ctypes.POINTER(P), D, D, ctypes.POINTER(Info)]),
+        "pgdto_project_many": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(H), ctypes.POINTER(P), ctypes.POINTER(P),
+                                              D, ctypes.POINTER(P), D, ctypes.POINTER(Info)]),
         "pgdto_project_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                                  ctypes.c_float, ctypes.c_float, ctypes.c_double, P, P, D, P, D,
                                                  ctypes.POINTER(Info), P]),
@@ -233,3 +237,40 @@ def project_noalloc(z, A, b, x_out, m=1, seg=None, lo=0.0, hi=1.0, C=1e12, strea
                                    _darr(b, m), _dptr(x_out), lam, ctypes.byref(info) if info is not None else None,
                                    _stream_ptr(stream))
     return st, (list(lam) if lam is not None else None), info
+
+
+def _ptrs(ts):
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = t.data_ptr()
+    return arr
+
+
+def _rows4(vals_per_item):
+    arr = (ctypes.c_double * (4 * len(vals_per_item)))()
+    for k, vals in enumerate(vals_per_item):
+        for j, v in enumerate(list(vals)[:4]):
+            arr[4 * k + j] = float(v)
+    return arr
+
+
+def step_many(handles, xs, grads, As, g_vals, Gs, want_info=True):
+    """pgdto_step_many: one launch, one step per handle.  Returns (status, [Info] or None)."""
+    lib = load()
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.h for h in handles])
+    infos = (Info * n)() if want_info else None
+    st = lib.pgdto_step_many(n, hs, _ptrs(xs), _ptrs(grads), _ptrs(As), _rows4(g_vals), _rows4(Gs), infos)
+    return st, (list(infos) if infos is not None else None)
+
+
+def project_many(handles, zs, As, bs, x_outs, want_info=True):
+    """pgdto_project_many: one launch, one projection per handle.  Returns (status, lambdas, infos)."""
+    lib = load()
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.h for h in handles])
+    infos = (Info * n)() if want_info else None
+    lam = (ctypes.c_double * (4 * n))() if want_info else None
+    st = lib.pgdto_project_many(n, hs, _ptrs(zs), _ptrs(As), _rows4(bs), _ptrs(x_outs), lam, infos)
+    lams = [[lam[4 * k + j] for j in range(handles[k].m)] for k in range(n)] if want_info else None
+    return st, lams, (list(infos) if infos is not None else None)

@@ -42,7 +42,16 @@ struct pgdto_handle {
     int64_t a_len;            // floats in A for this mode
     int64_t launches;
     int last_was_project;
+    int engine;               // 1 grid, 2 cluster
+    int cl_size, cl_max;      // cluster engine shape on this device
+    SegArgs* items;           // device list for the batched entries (grown on demand)
+    int items_cap;
 };
+
+// Problems up to this many variables run on one thread-block cluster by default: their
+// steps are bound by synchronisation latency, which the cluster barriers cut, while
+// larger ones need every SM's share of HBM bandwidth.
+static const int64_t kClusterMaxN = int64_t(1) << 21;
 
 static pgdto_status cuda_fail(cudaError_t e) {
     if (e == cudaErrorMemoryAllocation) return PGDTO_ERR_OOM;
@@ -73,6 +82,7 @@ extern "C" pgdto_status pgdto_params_default(pgdto_params* p) {
     p->barrier_timeout_ms = 2000;
     p->mode = PGDTO_AUTO;
     p->fault_inject = 0;
+    p->engine = 0;
     return PGDTO_OK;
 }
 
@@ -90,6 +100,7 @@ static void free_handle(pgdto_handle* h) {
     cudaFree(h->hx);
     cudaFree(h->hg);
     cudaFree(h->hA);
+    cudaFree(h->items);
     delete h;
 }
 
@@ -97,7 +108,7 @@ static bool params_ok(const pgdto_params& p) {
     return p.C > 0 && isfinite(p.C) && p.alpha_max > 0 && p.alpha_fallback > 0 && p.tol_N >= 0 && p.omega > 0 &&
            p.eps_alpha >= 0 && p.tol_lambda > 0 && p.tol_lambda < 1e-2 && p.t_warmup >= 0 &&
            p.maxiter_newton >= 1 && p.max_passes >= 1 && p.max_passes <= 100000 && p.barrier_timeout_ms >= 1 &&
-           (p.fault_inject == 0 || p.fault_inject == 1);
+           (p.fault_inject == 0 || p.fault_inject == 1) && p.engine >= 0 && p.engine <= 2;
 }
 
 extern "C" pgdto_status pgdto_create(pgdto_handle** out, int64_t n, int m, const int64_t* seg_offsets, float lo,
@@ -165,6 +176,14 @@ extern "C" pgdto_status pgdto_create(pgdto_handle** out, int64_t n, int m, const
         h->ctrl_bytes = seg_work_ctrl_bytes();
     }
     if (h->blocks < 1) {
+        delete h;
+        return PGDTO_ERR_UNSUPPORTED;
+    }
+    h->engine = 1;
+    if (mode != PGDTO_COUPLED) {
+        seg_cluster_shape(h->device, &h->cl_size, &h->cl_max);
+        if (p.engine == 2 || (p.engine == 0 && n <= kClusterMaxN)) h->engine = 2;
+    } else if (p.engine == 2) {
         delete h;
         return PGDTO_ERR_UNSUPPORTED;
     }
@@ -263,6 +282,42 @@ extern "C" pgdto_status pgdto_last_info(pgdto_handle* h, pgdto_info* info, doubl
     return read_info(h, info, lambda_out);
 }
 
+static void fill_seg_args(pgdto_handle* h, bool proj, float* x, const float* g, const float* A,
+                          const double* bconst, const float* z_in, float* x_out, bool force_fallback, SegArgs& a) {
+    memset(&a, 0, sizeof(a));
+    a.n = h->n;
+    a.nrows = h->m;
+    a.t = h->t;
+    a.proj = proj ? 1 : 0;
+    a.force_fallback = force_fallback ? 1 : 0;
+    for (int j = 0; j <= h->m; ++j) a.seg[j] = h->seg[j];
+    a.lo = h->lo;
+    a.hi = h->hi;
+    a.x = x;
+    a.g = g;
+    a.A = A;
+    a.x_prev = h->x_prev;
+    a.g_prev = h->g_prev;
+    a.d_prev = h->d[h->cur];
+    a.d_new = h->d[1 - h->cur];
+    a.z = h->z;
+    a.zlo = h->zlo;
+    a.z_in = z_in;
+    a.x_out = x_out;
+    for (int j = 0; j < h->m; ++j) a.bconst[j] = bconst[j];
+    a.C = h->p.C;
+    a.alpha_max = h->p.alpha_max;
+    a.alpha_fb = h->p.alpha_fallback;
+    a.eps_alpha = h->p.eps_alpha;
+    a.omega = h->p.omega;
+    a.tol_lambda = h->p.tol_lambda;
+    a.max_passes = h->p.max_passes;
+    a.fault_inject = h->p.fault_inject;
+    a.timeout_cycles = h->timeout_cycles;
+    a.ws = (SegWork*)h->work;
+    a.info_out = h->dev_info;
+}
+
 static pgdto_status launch(pgdto_handle* h, bool proj, float* x, const float* g, const float* A, const double* bconst,
                            const float* z_in, float* x_out, bool force_fallback) {
     cudaError_t e;
@@ -304,38 +359,11 @@ static pgdto_status launch(pgdto_handle* h, bool proj, float* x, const float* g,
         e = launch_coupled(a, h->blocks, h->stream);
     } else {
         SegArgs a;
-        memset(&a, 0, sizeof(a));
-        a.n = h->n;
-        a.nrows = h->m;
-        a.t = h->t;
-        a.proj = proj ? 1 : 0;
-        a.force_fallback = force_fallback ? 1 : 0;
-        for (int j = 0; j <= h->m; ++j) a.seg[j] = h->seg[j];
-        a.lo = h->lo;
-        a.hi = h->hi;
-        a.x = x;
-        a.g = g;
-        a.A = A;
-        a.x_prev = h->x_prev;
-        a.g_prev = h->g_prev;
-        a.d_prev = h->d[h->cur];
-        a.d_new = h->d[1 - h->cur];
-        a.z = h->z;
-        a.zlo = h->zlo;
-        a.z_in = z_in;
-        a.x_out = x_out;
-        for (int j = 0; j < h->m; ++j) a.bconst[j] = bconst[j];
-        a.C = h->p.C;
-        a.alpha_max = h->p.alpha_max;
-        a.alpha_fb = h->p.alpha_fallback;
-        a.eps_alpha = h->p.eps_alpha;
-        a.omega = h->p.omega;
-        a.tol_lambda = h->p.tol_lambda;
-        a.max_passes = h->p.max_passes;
-        a.fault_inject = h->p.fault_inject;
-        a.timeout_cycles = h->timeout_cycles;
-        a.ws = (SegWork*)h->work;
-        e = launch_seg(a, h->blocks, h->stream);
+        fill_seg_args(h, proj, x, g, A, bconst, z_in, x_out, force_fallback, a);
+        if (h->engine == 2 && !h->p.fault_inject)
+            e = launch_seg_clusters(a, nullptr, 1, 1, h->cl_size, seg_args_aligned(a), h->stream);
+        else
+            e = launch_seg(a, h->blocks, h->stream);
     }
     if (e != cudaSuccess) return cuda_fail(e);
     h->launches += 1;
@@ -411,4 +439,132 @@ extern "C" int pgdto_trace(pgdto_handle* h, double* us_out, int max_marks) {
     int k = c.ntrace < 0 ? 0 : (c.ntrace > 62 ? 62 : c.ntrace);
     for (int i = 0; i < k && i < max_marks; ++i) us_out[i] = (double)(c.trace[i] - c.trace_start) * 1e-3;
     return k;
+}
+
+// ------------------------------------------------------------------ batched entries
+
+static pgdto_status ensure_items(pgdto_handle* h, int count) {
+    if (h->items_cap >= count) return PGDTO_OK;
+    cudaFree(h->items);
+    h->items = nullptr;
+    h->items_cap = 0;
+    int cap = count < 64 ? 64 : count;
+    cudaError_t e = cudaMalloc(&h->items, sizeof(SegArgs) * (size_t)cap);
+    if (e != cudaSuccess) return cuda_fail(e);
+    h->items_cap = cap;
+    return PGDTO_OK;
+}
+
+static pgdto_status launch_many(int count, pgdto_handle* const* hs, SegArgs* args, bool vec) {
+    pgdto_handle* h0 = hs[0];
+    if (count > 1) {
+        pgdto_status s = ensure_items(h0, count);
+        if (s != PGDTO_OK) return s;
+        // pageable source: the copy is staged before the call returns, args may be reused
+        cudaError_t e = cudaMemcpyAsync(h0->items, args, sizeof(SegArgs) * (size_t)count, cudaMemcpyHostToDevice,
+                                        h0->stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    int ncl = count < h0->cl_max ? count : h0->cl_max;
+    cudaError_t e = launch_seg_clusters(args[0], h0->items, count, ncl, h0->cl_size, vec, h0->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int k = 0; k < count; ++k) hs[k]->launches += (k == 0);
+    return PGDTO_OK;
+}
+
+static pgdto_status check_many(int count, pgdto_handle* const* hs) {
+    if (count < 1 || !hs) return PGDTO_ERR_ARG;
+    for (int k = 0; k < count; ++k) {
+        if (!hs[k] || hs[k]->mode == PGDTO_COUPLED || hs[k]->p.fault_inject) return PGDTO_ERR_ARG;
+        if (hs[k]->stream != hs[0]->stream || hs[k]->device != hs[0]->device) return PGDTO_ERR_ARG;
+        for (int q = 0; q < k; ++q)
+            if (hs[q] == hs[k]) return PGDTO_ERR_ARG;  // one step per handle per launch
+    }
+    if (hs[0]->cl_size < 1) return PGDTO_ERR_UNSUPPORTED;
+    return PGDTO_OK;
+}
+
+extern "C" pgdto_status pgdto_step_many(int count, pgdto_handle* const* hs, float* const* x,
+                                        const float* const* grad_f, const float* const* A, const double* g_val,
+                                        const double* G, pgdto_info* infos) {
+    pgdto_status s = check_many(count, hs);
+    if (s != PGDTO_OK) return s;
+    if (!x || !grad_f || !A || !g_val || !G) return PGDTO_ERR_ARG;
+    SegArgs* args = new SegArgs[count];
+    bool vec = true;
+    for (int k = 0; k < count; ++k) {
+        pgdto_handle* h = hs[k];
+        if (!x[k] || !grad_f[k] || !A[k]) {
+            delete[] args;
+            return PGDTO_ERR_ARG;
+        }
+        double bconst[kMaxRows] = {0, 0, 0, 0};
+        double viol = 0.0;
+        for (int j = 0; j < h->m; ++j) {
+            const double gv = g_val[4 * k + j], gg = G[4 * k + j];
+            if (!(isfinite(gv) && isfinite(gg))) {
+                delete[] args;
+                return PGDTO_ERR_NONFINITE;
+            }
+            bconst[j] = gg - gv;
+            viol = fmax(viol, gv - gg);
+        }
+        const bool fallback = h->t == 0 || (h->t >= h->p.t_warmup && viol > h->p.tol_N);
+        fill_seg_args(h, false, x[k], grad_f[k], A[k], bconst, nullptr, nullptr, fallback, args[k]);
+        vec = vec && seg_args_aligned(args[k]);
+    }
+    s = launch_many(count, hs, args, vec);
+    delete[] args;
+    if (s != PGDTO_OK) return s;
+    for (int k = 0; k < count; ++k) {
+        hs[k]->cur = 1 - hs[k]->cur;
+        hs[k]->t += 1;
+        hs[k]->last_was_project = 0;
+    }
+    if (!infos) return PGDTO_OK;
+    pgdto_status worst = PGDTO_OK;
+    for (int k = 0; k < count; ++k) {
+        pgdto_status r = read_info(hs[k], &infos[k], nullptr);
+        if (r != PGDTO_OK && worst == PGDTO_OK) worst = r;
+    }
+    return worst;
+}
+
+extern "C" pgdto_status pgdto_project_many(int count, pgdto_handle* const* hs, const float* const* z,
+                                           const float* const* A, const double* b, float* const* x_out,
+                                           double* lambda_out, pgdto_info* infos) {
+    pgdto_status s = check_many(count, hs);
+    if (s != PGDTO_OK) return s;
+    if (!z || !A || !b || !x_out) return PGDTO_ERR_ARG;
+    SegArgs* args = new SegArgs[count];
+    bool vec = true;
+    for (int k = 0; k < count; ++k) {
+        pgdto_handle* h = hs[k];
+        if (!z[k] || !A[k] || !x_out[k]) {
+            delete[] args;
+            return PGDTO_ERR_ARG;
+        }
+        double bb[kMaxRows] = {0, 0, 0, 0};
+        for (int j = 0; j < h->m; ++j) {
+            if (!isfinite(b[4 * k + j])) {
+                delete[] args;
+                return PGDTO_ERR_NONFINITE;
+            }
+            bb[j] = b[4 * k + j];
+        }
+        fill_seg_args(h, true, nullptr, nullptr, A[k], bb, z[k], x_out[k], false, args[k]);
+        vec = vec && seg_args_aligned(args[k]);
+    }
+    s = launch_many(count, hs, args, vec);
+    delete[] args;
+    if (s != PGDTO_OK) return s;
+    for (int k = 0; k < count; ++k) hs[k]->last_was_project = 1;
+    if (!infos && !lambda_out) return PGDTO_OK;
+    pgdto_status worst = PGDTO_OK;
+    for (int k = 0; k < count; ++k) {
+        pgdto_info tmp;
+        pgdto_status r = read_info(hs[k], infos ? &infos[k] : &tmp, lambda_out ? lambda_out + 4 * k : nullptr);
+        if (r != PGDTO_OK && worst == PGDTO_OK) worst = r;
+    }
+    return worst;
 }

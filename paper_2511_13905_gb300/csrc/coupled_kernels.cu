@@ -559,6 +559,7 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
         vc->trace_start = globaltimer_ns();
         vc->ntrace = 0;
     }
+    grid_sync_init(&ws->ctrl, sc);
     // test hook: block 0 never arrives, so every other block's first wait runs out its budget
     if (a.fault_inject == 1 && blk == 0) return;
     int64_t cb, ce;

@@ -12,6 +12,7 @@
 //    returns, so a fault elsewhere never hangs the GPU.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -93,6 +94,14 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 
 __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ unsigned atom_add_relaxed_u32(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.relaxed.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
 }
 
 __device__ __forceinline__ int ld_volatile_i32(const int* p) {
@@ -182,15 +191,15 @@ __device__ bool grid_reduce_update(GridCtrl* ctrl, Partials* part, BlockScratch&
     for (int i = tid; i < nm; i += blockDim.x) part->mx[i][blockIdx.x] = sc.totmax[i];
     __syncthreads();
     if (tid == 0) {
-        unsigned g = ld_acquire_u32(&ctrl->gen);
-        __threadfence();
-        unsigned old = atomicAdd(&ctrl->count, 1u);
-        sc.gen = g;
+        // release: the block's partials (ordered before by the barrier above) are visible to
+        // whoever observes this arrival; sc.gen is tracked by the block itself (grid_sync_init)
+        fence_acq_rel_gpu();
+        const unsigned old = atom_add_relaxed_u32(&ctrl->count, 1u);
         sc.flag = (old == (unsigned)(nb - 1)) ? 1 : 0;
+        if (sc.flag) fence_acq_rel_gpu();  // acquire: every other block's partials
     }
     __syncthreads();
     if (sc.flag) {
-        __threadfence();
         const int lane = tid & 31, warp = tid >> 5;
         for (int i = warp; i < nv; i += kWarps) {
             DF acc = df_zero();
@@ -226,34 +235,82 @@ __device__ bool grid_reduce_update(GridCtrl* ctrl, Partials* part, BlockScratch&
                 vc->trace[k] = globaltimer_ns();
                 vc->ntrace = k + 1;
             }
-            __threadfence();
             ctrl->count = 0u;
-            __threadfence();
-            st_release_u32(&ctrl->gen, sc.gen + 1u);
+            st_release_u32(&ctrl->gen, sc.gen + 1u);  // orders the reset, the update and the trace
+            sc.gen = sc.gen + 1u;
         }
         __syncthreads();
         return true;
     }
     if (tid == 0) {
+        const unsigned target = sc.gen + 1u;
         long long t0 = clock64();
         int ok = 1;
         unsigned spins = 0;
-        while (ld_acquire_u32(&ctrl->gen) == sc.gen) {
-            if (ld_volatile_i32(&ctrl->abort)) {
-                ok = 0;
-                break;
-            }
-            if (((++spins) & 63u) == 0u && clock64() - t0 > timeout_cycles) {
-                atomicExch(&ctrl->status, kErrTimeout);
-                atomicExch(&ctrl->abort, 1);
-                ok = 0;
-                break;
+        while (ld_acquire_u32(&ctrl->gen) != target) {
+            if (((++spins) & 63u) == 0u) {
+                if (ld_volatile_i32(&ctrl->abort)) {
+                    ok = 0;
+                    break;
+                }
+                if (clock64() - t0 > timeout_cycles) {
+                    atomicExch(&ctrl->status, kErrTimeout);
+                    atomicExch(&ctrl->abort, 1);
+                    ok = 0;
+                    break;
+                }
             }
         }
+        sc.gen = target;
         sc.flag = ok;
     }
     __syncthreads();
     return sc.flag != 0;
+}
+
+// Cluster-wide reduction of sc.tot / sc.totmax followed by the scalar update, for the CTAs
+// of one thread-block cluster.  After a cluster barrier the first CTA reads every CTA's
+// block totals through distributed shared memory (lane r of a warp reads rank r, fixed
+// order: deterministic), runs update(sc) on its warp 0, and a second barrier publishes
+// the result.  The barriers are the hardware's: they complete when every CTA of the
+// cluster arrives, as every CTA runs the same sequence of phases.
+template <class Update>
+__device__ void cluster_reduce_update(BlockScratch& sc, int nv, int nm, Update&& update) {
+    namespace cgn = cooperative_groups;
+    cgn::cluster_group cl = cgn::this_cluster();
+    cl.sync();
+    if (cl.block_rank() == 0) {
+        const int S = (int)cl.num_blocks();
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int i = warp; i < nv; i += kWarps) {
+            DF v = df_zero();
+            if (lane < S) v = cl.map_shared_rank(&sc, lane)->tot[i];
+            v = warp_reduce_df(v);
+            __syncwarp();
+            if (lane == 0) sc.tot[i] = v;
+        }
+        for (int i = warp; i < nm; i += kWarps) {
+            float v = -INFINITY;
+            if (lane < S) v = cl.map_shared_rank(&sc, lane)->totmax[i];
+            v = warp_reduce_max(v);
+            __syncwarp();
+            if (lane == 0) sc.totmax[i] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            update(sc);
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+    cl.sync();
+}
+
+// Every block calls this once at kernel start, before its first grid_reduce_update: the
+// round counter is read while no round can have completed (this block has not arrived).
+__device__ __forceinline__ void grid_sync_init(GridCtrl* ctrl, BlockScratch& sc) {
+    if (threadIdx.x == 0) sc.gen = ld_acquire_u32(&ctrl->gen);
+    __syncthreads();
 }
 
 // Copy a small struct written by the last block (global) into shared memory through L2.

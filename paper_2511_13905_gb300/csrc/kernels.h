@@ -44,7 +44,8 @@ struct SegArgs {
     int max_passes;
     int fault_inject;
     long long timeout_cycles;
-    SegWork* ws;
+    SegWork* ws;          // grid engine workspace
+    DeviceInfo* info_out; // cluster engine: where this problem's report goes
 };
 
 // Arguments of the coupled-rows (Alg. 2) step / projection kernel.
@@ -84,6 +85,13 @@ size_t coupled_work_ctrl_bytes();
 
 // Launch helpers: cooperative launch on `stream` with `blocks` CTAs of kThreads threads.
 cudaError_t launch_seg(const SegArgs& a, int blocks, cudaStream_t stream);
+// Cluster engine: `items` (device array of `nitems` problems) on `nclusters` clusters of
+// `cluster` CTAs each.  vec: every pointer of every item is 16-byte aligned.
+cudaError_t launch_seg_clusters(const SegArgs& first, const SegArgs* items, int nitems, int nclusters, int cluster,
+                                bool vec, cudaStream_t stream);
+bool seg_args_aligned(const SegArgs& a);
+// Largest cluster size (<= 16) the cluster engine can use, and how many such clusters fit.
+int seg_cluster_shape(int device, int* cluster, int* max_clusters);
 cudaError_t launch_coupled(const CoupledArgs& a, int blocks, cudaStream_t stream);
 // Largest co-resident grid for each kernel on the current device.
 int max_blocks_seg(int device);

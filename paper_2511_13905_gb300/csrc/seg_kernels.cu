@@ -20,9 +20,13 @@
 #include <math.h>
 #include <string.h>
 
+#include <cooperative_groups.h>
+
 #include "dev_common.cuh"
 #include "kernels.h"
 #include "step_common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace pgdto {
 
@@ -35,17 +39,23 @@ struct SegBcast {
     float lam_hi[kMaxRows], lam_lo[kMaxRows];
 };
 
-struct SegWork {
-    GridCtrl ctrl;
+// Search state of one problem: in global memory for the grid engine, in the shared memory
+// of the cluster's first CTA for the cluster engine.
+struct SegState {
     SegBcast bc;
     RowState rows[kMaxRows];
     DeviceInfo info;
+};
+
+struct SegWork {
+    GridCtrl ctrl;
+    SegState st;
     Partials part;
 };
 
 size_t seg_work_bytes() { return sizeof(SegWork); }
 size_t seg_work_ctrl_bytes() { return sizeof(GridCtrl); }
-DeviceInfo* seg_work_info(SegWork* ws) { return &ws->info; }
+DeviceInfo* seg_work_info(SegWork* ws) { return &ws->st.info; }
 
 __device__ __forceinline__ bool all_finite(const BlockScratch& sc, int nv) {
     for (int i = 0; i < nv; ++i)
@@ -71,7 +81,7 @@ __device__ __forceinline__ void publish_lambda(volatile SegBcast* bc, int j, dou
 
 // After phase B: feasibility at lam = 0, bracket [0, H] (Alg. 1), closed form when the row
 // is violated even with every variable at its row-minimising bound (regularised root).
-__device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, SegWork* ws) {
+__device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, SegState* ws) {
     const int lane = threadIdx.x, j = lane >> 3, k = lane & 7;
     volatile SegBcast* bc = &ws->bc;
     volatile RowState* rows = ws->rows;
@@ -128,7 +138,8 @@ __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, Seg
 }
 
 // After phase D: the report.
-__device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegWork* ws) {
+__device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegState* ws, int* sticky,
+                             unsigned long long* launches) {
     const int lane = threadIdx.x;
     volatile DeviceInfo* inf = &ws->info;
     volatile RowState* rows = ws->rows;
@@ -173,35 +184,68 @@ __device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegWork* 
     inf->newton_iters = 0;
     inf->stage = 0;
     inf->status = status;
-    if (status != kOk) atomicCAS(&ws->ctrl.status, kOk, status);
-    ws->ctrl.launches += 1ull;
+    if (status != kOk && sticky) atomicCAS(sticky, kOk, status);
+    if (launches) *launches += 1ull;
 }
 
 // Early exit after a non-finite reduction: report and stop.
-__device__ void report_status_only(const SegArgs& a, SegWork* ws, int status) {
+__device__ void report_status_only(SegState* ws, int* sticky, unsigned long long* launches, int status) {
     volatile DeviceInfo* inf = &ws->info;
     inf->status = status;
     inf->passes = 0;
-    atomicCAS(&ws->ctrl.status, kOk, status);
-    ws->ctrl.launches += 1ull;
+    if (sticky) atomicCAS(sticky, kOk, status);
+    if (launches) *launches += 1ull;
 }
 
 // ----------------------------------------------------------------------- element passes
 
-template <bool VEC>
-__global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
-    __shared__ BlockScratch sc;
-    __shared__ SegBcast bc;
-    SegWork* ws = a.ws;
-    if (ld_volatile_i32(&ws->ctrl.abort)) return;
-    const int nb = gridDim.x, blk = blockIdx.x;
-    if (blk == 0 && threadIdx.x == 0) {
-        volatile GridCtrl* vc = &ws->ctrl;
-        vc->trace_start = globaltimer_ns();
-        vc->ntrace = 0;
+// Grid engine: the CTAs of one cooperative launch share one problem; phases end in a
+// grid-wide reduction through global memory (dev_common.cuh).
+struct GridSyncSeg {
+    SegWork* ws;
+    long long timeout;
+    __device__ int rank() const { return blockIdx.x; }
+    __device__ int size() const { return gridDim.x; }
+    __device__ SegState* state() const { return &ws->st; }
+    __device__ int* sticky() const { return &ws->ctrl.status; }
+    __device__ unsigned long long* launches() const { return &ws->ctrl.launches; }
+    template <class F>
+    __device__ bool reduce(BlockScratch& sc, int nv, int nm, F&& f) const {
+        SegState* st = &ws->st;
+        return grid_reduce_update(&ws->ctrl, &ws->part, sc, nv, nm, timeout, [&](BlockScratch& s) { f(s, st); });
     }
-    // test hook: block 0 never arrives, so every other block's first wait runs out its budget
-    if (a.fault_inject == 1 && blk == 0) return;
+    __device__ void fetch(SegBcast& bc) const { load_cg(bc, &ws->st.bc); }
+};
+
+// Cluster engine: the CTAs of one thread-block cluster share one problem; phases end in a
+// reduction through distributed shared memory and hardware cluster barriers, with the
+// search state in the first CTA's shared memory.
+struct ClusterSyncSeg {
+    SegState* st;  // this CTA's copy; the first CTA's is the live one
+    __device__ int rank() const { return (int)cg::this_cluster().block_rank(); }
+    __device__ int size() const { return (int)cg::this_cluster().num_blocks(); }
+    __device__ SegState* state() const { return st; }
+    __device__ int* sticky() const { return nullptr; }
+    __device__ unsigned long long* launches() const { return nullptr; }
+    template <class F>
+    __device__ bool reduce(BlockScratch& sc, int nv, int nm, F&& f) const {
+        SegState* s0 = st;
+        cluster_reduce_update(sc, nv, nm, [&](BlockScratch& s) { f(s, s0); });
+        return true;
+    }
+    __device__ void fetch(SegBcast& bc) const {
+        const SegBcast* src = cg::this_cluster().map_shared_rank(&st->bc, 0);
+        const unsigned* sw = reinterpret_cast<const unsigned*>(src);
+        unsigned* d = reinterpret_cast<unsigned*>(&bc);
+        for (int i = threadIdx.x; i < (int)(sizeof(SegBcast) / 4); i += blockDim.x) d[i] = sw[i];
+        __syncthreads();
+    }
+};
+
+// One PGD-TO step (or projection) on the problem `a`, executed by the CTAs of `sy`.
+template <bool VEC, class Sync>
+__device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, SegBcast& bc) {
+    const int nb = sy.size(), blk = sy.rank();
     const float lo = a.lo, hi = a.hi;
 
     if (!a.proj) {
@@ -261,12 +305,11 @@ __global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
             float mx[1] = {gmax};
             block_reduce<6, 1>(acc.d, mx, sc);
         }
-        if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 6, 1, a.timeout_cycles,
-                                [&](BlockScratch& s) { update_step_scalars(a, s, &ws->bc, &ws->info); }))
+        if (!sy.reduce(sc, 6, 1, [&](BlockScratch& s, SegState* st) { update_step_scalars(a, s, &st->bc, &st->info); }))
             return;
-        load_cg(bc, &ws->bc);
+        sy.fetch(bc);
         if (bc.status != kOk) {
-            if (blk == 0 && threadIdx.x == 0) report_status_only(a, ws, bc.status);
+            if (blk == 0 && threadIdx.x == 0) report_status_only(sy.state(), sy.sticky(), sy.launches(), bc.status);
             return;
         }
     }
@@ -367,12 +410,11 @@ __global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
             float mx[1] = {lsat};
             block_reduce<4, 1>(acc.d, mx, sc, 4 * j, j);
         }
-        if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 4 * a.nrows, a.nrows, a.timeout_cycles,
-                                [&](BlockScratch& s) { update_after_trial(a, s, ws); }))
+        if (!sy.reduce(sc, 4 * a.nrows, a.nrows, [&](BlockScratch& s, SegState* st) { update_after_trial(a, s, st); }))
             return;
-        load_cg(bc, &ws->bc);
+        sy.fetch(bc);
         if (bc.status != kOk) {
-            if (blk == 0 && threadIdx.x == 0) report_status_only(a, ws, bc.status);
+            if (blk == 0 && threadIdx.x == 0) report_status_only(sy.state(), sy.sticky(), sy.launches(), bc.status);
             return;
         }
     }
@@ -433,10 +475,11 @@ __global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
             acc.fold();
             block_reduce<2 * K, 0>(acc.d, nullptr, sc, 2 * K * j, 0);
         }
-        if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 2 * K * a.nrows, 0, a.timeout_cycles,
-                                [&](BlockScratch& s) { search_pass_update(s, 0, ws->rows, &ws->bc, a.nrows, a.tol_lambda, a.max_passes); }))
+        if (!sy.reduce(sc, 2 * K * a.nrows, 0, [&](BlockScratch& s, SegState* st) {
+                search_pass_update(s, 0, st->rows, &st->bc, a.nrows, a.tol_lambda, a.max_passes);
+            }))
             return;
-        load_cg(bc, &ws->bc);
+        sy.fetch(bc);
     }
 
     // ---------------------------------------------------------------- phase D
@@ -520,8 +563,50 @@ __global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
             acc.d[a.nrows + 1] = acc.d[kMaxRows + 1];
         }
         block_reduce<kMaxRows + 2, 0>(acc.d, nullptr, sc);
-        grid_reduce_update(&ws->ctrl, &ws->part, sc, nv, 0, a.timeout_cycles,
-                           [&](BlockScratch& s) { update_final(a, s, ws); });
+        sy.reduce(sc, nv, 0, [&](BlockScratch& s, SegState* st) { update_final(a, s, st, sy.sticky(), sy.launches()); });
+    }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
+    __shared__ BlockScratch sc;
+    __shared__ SegBcast bc;
+    SegWork* ws = a.ws;
+    if (ld_volatile_i32(&ws->ctrl.abort)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        volatile GridCtrl* vc = &ws->ctrl;
+        vc->trace_start = globaltimer_ns();
+        vc->ntrace = 0;
+    }
+    grid_sync_init(&ws->ctrl, sc);
+    // test hook: block 0 never arrives, so every other block's first wait runs out its budget
+    if (a.fault_inject == 1 && blockIdx.x == 0) return;
+    GridSyncSeg sy{ws, a.timeout_cycles};
+    seg_body<VEC>(a, sy, sc, bc);
+}
+
+// Cluster engine over a list of problems: cluster c takes problems c, c + nclusters, ...
+// Problem 0 travels in the launch parameters (a single problem needs no upload), the rest
+// in `items`.  Each problem's report goes to its info_out.
+template <bool VEC>
+__global__ void __launch_bounds__(kThreads, 1) seg_cluster_kernel(SegArgs first, const SegArgs* __restrict__ items,
+                                                                  int nitems) {
+    __shared__ BlockScratch sc;
+    __shared__ SegBcast bc;
+    __shared__ SegState st;
+    cg::cluster_group cl = cg::this_cluster();
+    const int S = (int)cl.num_blocks();
+    const int cid = blockIdx.x / S, ncl = gridDim.x / S;
+    for (int it = cid; it < nitems; it += ncl) {
+        const SegArgs& a = it == 0 ? first : items[it];
+        ClusterSyncSeg sy{&st};
+        seg_body<VEC>(a, sy, sc, bc);
+        if (cl.block_rank() == 0 && threadIdx.x == 0 && a.info_out) {
+            const unsigned* src = reinterpret_cast<const unsigned*>(&st.info);
+            unsigned* dst = reinterpret_cast<unsigned*>(a.info_out);
+            for (int i = 0; i < (int)(sizeof(DeviceInfo) / 4); ++i) dst[i] = src[i];
+        }
+        cl.sync();  // shared state is reused by the next problem
     }
 }
 
@@ -537,6 +622,75 @@ cudaError_t launch_seg(const SegArgs& a, int blocks, cudaStream_t stream) {
     vec = al(a.x) && al(a.g) && al(a.A) && al(a.x_prev) && al(a.g_prev) && al(a.d_prev) && al(a.d_new) &&
           al(a.z) && al(a.zlo) && al(a.z_in) && al(a.x_out);
     return vec ? launch_seg_t<true>(a, blocks, stream) : launch_seg_t<false>(a, blocks, stream);
+}
+
+template <bool VEC>
+static cudaError_t launch_clusters_t(const SegArgs& first, const SegArgs* items, int nitems, int ncl, int S,
+                                     cudaStream_t stream) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(seg_cluster_kernel<VEC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ncl * S);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = S;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, seg_cluster_kernel<VEC>, first, items, nitems);
+}
+
+cudaError_t launch_seg_clusters(const SegArgs& first, const SegArgs* items, int nitems, int nclusters, int cluster,
+                                bool vec, cudaStream_t stream) {
+    if (nitems < 1 || nclusters < 1 || cluster < 1 || cluster > 16) return cudaErrorInvalidValue;
+    return vec ? launch_clusters_t<true>(first, items, nitems, nclusters, cluster, stream)
+               : launch_clusters_t<false>(first, items, nitems, nclusters, cluster, stream);
+}
+
+bool seg_args_aligned(const SegArgs& a) {
+    auto al = [](const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    return al(a.x) && al(a.g) && al(a.A) && al(a.x_prev) && al(a.g_prev) && al(a.d_prev) && al(a.d_new) &&
+           al(a.z) && al(a.zlo) && al(a.z_in) && al(a.x_out);
+}
+
+int seg_cluster_shape(int device, int* cluster, int* max_clusters) {
+    static int cached_dev = -1, cached_s = 0, cached_n = 0;
+    if (cached_dev == device) {
+        *cluster = cached_s;
+        *max_clusters = cached_n;
+        return 0;
+    }
+    cudaFuncSetAttribute(seg_cluster_kernel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(seg_cluster_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(kThreads);
+    int s = 0;
+    if (cudaOccupancyMaxPotentialClusterSize(&s, seg_cluster_kernel<true>, &cfg) != cudaSuccess || s < 1) s = 8;
+    if (s > 16) s = 16;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = s;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(s);
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, seg_cluster_kernel<true>, &cfg) != cudaSuccess || nc < 1) nc = 1;
+    cached_dev = device;
+    cached_s = s;
+    cached_n = nc;
+    *cluster = s;
+    *max_clusters = nc;
+    return 0;
 }
 
 int max_blocks_seg(int device) {

@@ -13,7 +13,7 @@
 namespace pgdto {
 
 constexpr int K = 8;           // trial points per root-search pass
-constexpr int kFoldEvery = 8;  // float4 groups accumulated in FP32 before folding into DF
+constexpr int kFoldEvery = 2;  // float4 groups accumulated in FP32 before folding into DF
 constexpr unsigned kFull = 0xffffffffu;
 
 // State of one monotone piecewise-linear root search r(t) = S(t) - b - reg t = 0 on [L, H]
