@@ -51,7 +51,7 @@ struct pgdto_handle {
 // Problems up to this many variables run on one thread-block cluster by default: their
 // steps are bound by synchronisation latency, which the cluster barriers cut, while
 // larger ones need every SM's share of HBM bandwidth.
-static const int64_t kClusterMaxN = int64_t(1) << 21;
+static const int64_t kClusterMaxN = int64_t(1) << 17;
 
 static pgdto_status cuda_fail(cudaError_t e) {
     if (e == cudaErrorMemoryAllocation) return PGDTO_ERR_OOM;

@@ -268,6 +268,7 @@ __device__ void cstart_line_search(CoupledWork* ws) {
         for (int k = 0; k < K; ++k) bc->pts[0][k] = base[k];
         nt->ls_expand = 1;
     }
+    row_refresh_floats(ls);
     nt->trial = 0;
     bc->any_active = 1;
     bc->mode = kModeLine;

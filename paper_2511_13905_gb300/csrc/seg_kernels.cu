@@ -222,6 +222,7 @@ struct GridSyncSeg {
 // search state in the first CTA's shared memory.
 struct ClusterSyncSeg {
     SegState* st;  // this CTA's copy; the first CTA's is the live one
+    GridCtrl* trace;  // phase timeline of a single-problem launch (the handle's), or null
     __device__ int rank() const { return (int)cg::this_cluster().block_rank(); }
     __device__ int size() const { return (int)cg::this_cluster().num_blocks(); }
     __device__ SegState* state() const { return st; }
@@ -230,7 +231,19 @@ struct ClusterSyncSeg {
     template <class F>
     __device__ bool reduce(BlockScratch& sc, int nv, int nm, F&& f) const {
         SegState* s0 = st;
-        cluster_reduce_update(sc, nv, nm, [&](BlockScratch& s) { f(s, s0); });
+        GridCtrl* tr = trace;
+        cluster_reduce_update(sc, nv, nm, [&](BlockScratch& s) {
+            f(s, s0);
+            if (tr && threadIdx.x == 0) {
+                __syncwarp(1u);
+                volatile GridCtrl* vc = tr;
+                const int k = vc->ntrace;
+                if (k >= 0 && k < 62) {
+                    vc->trace[k] = globaltimer_ns();
+                    vc->ntrace = k + 1;
+                }
+            }
+        });
         return true;
     }
     __device__ void fetch(SegBcast& bc) const {
@@ -599,7 +612,13 @@ __global__ void __launch_bounds__(kThreads, 1) seg_cluster_kernel(SegArgs first,
     const int cid = blockIdx.x / S, ncl = gridDim.x / S;
     for (int it = cid; it < nitems; it += ncl) {
         const SegArgs& a = it == 0 ? first : items[it];
-        ClusterSyncSeg sy{&st};
+        GridCtrl* tr = (nitems == 1 && a.ws) ? &a.ws->ctrl : nullptr;
+        if (tr && cl.block_rank() == 0 && threadIdx.x == 0) {
+            volatile GridCtrl* vc = tr;
+            vc->trace_start = globaltimer_ns();
+            vc->ntrace = 0;
+        }
+        ClusterSyncSeg sy{&st, tr};
         seg_body<VEC>(a, sy, sc, bc);
         if (cl.block_rank() == 0 && threadIdx.x == 0 && a.info_out) {
             const unsigned* src = reinterpret_cast<const unsigned*>(&st.info);

@@ -21,6 +21,9 @@ constexpr unsigned kFull = 0xffffffffu;
 struct RowState {
     double b, L, rL, SL, H, rH, SH, lam, rlast, reg;
     int active, passes, how, pad;
+    // the same bracket in float / double-float form: the per-pass update works on these
+    // (FP64 issues at a small fraction of the FP32 rate here and sits on the critical path)
+    float b_hi, b_lo, fL, fH, rL_hi, rL_lo, rH_hi, rH_lo, fSL, fSH, freg, fpad;
 };
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
@@ -143,6 +146,40 @@ __device__ __forceinline__ void store_row(volatile RowState* r, double b, double
     r->active = active;
     r->passes = passes;
     r->how = how;
+    float h, l;
+    split_double(b, h, l);
+    r->b_hi = h;
+    r->b_lo = l;
+    split_double(rL, h, l);
+    r->rL_hi = h;
+    r->rL_lo = l;
+    split_double(rH, h, l);
+    r->rH_hi = h;
+    r->rH_lo = l;
+    r->fL = (float)L;  // bracket ends are float trial points (or 0 / the float saturation bound)
+    r->fH = (float)H;
+    r->fSL = (float)SL;
+    r->fSH = (float)SH;
+    r->freg = (float)r->reg;
+}
+
+// Refresh the float / double-float copy of a bracket whose FP64 fields were set directly.
+__device__ __forceinline__ void row_refresh_floats(volatile RowState* r) {
+    float h, l;
+    split_double(r->b, h, l);
+    r->b_hi = h;
+    r->b_lo = l;
+    split_double(r->rL, h, l);
+    r->rL_hi = h;
+    r->rL_lo = l;
+    split_double(r->rH, h, l);
+    r->rH_hi = h;
+    r->rH_lo = l;
+    r->fL = (float)r->L;
+    r->fH = (float)r->H;
+    r->fSL = (float)r->SL;
+    r->fSH = (float)r->SH;
+    r->freg = (float)r->reg;
 }
 
 template <class Bcast>
@@ -154,70 +191,129 @@ __device__ __forceinline__ void publish_lambda(volatile Bcast* bc, int j, double
     bc->active[j] = 0;
 }
 
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+
+// a / b for a double-float a and a float b, to double-float accuracy.
+__device__ __forceinline__ DF df_div_f(DF a, float b) {
+    const float q1 = __fdiv_rn(a.hi, b);
+    const float r = __fadd_rn(fmaf(-q1, b, a.hi), a.lo);
+    return fast_two_sum(q1, __fdiv_rn(r, b));
+}
+
+__device__ __forceinline__ bool df_pos(DF a) { return a.hi > 0.0f || (a.hi == 0.0f && a.lo > 0.0f); }
+
+__device__ __forceinline__ float float_ulp_f(float v) {
+    const float f = fabsf(v);
+    return nextafterf(f, INFINITY) - f;
+}
+
+// Trial point k of the next pass inside (L, H), float version of next_point.
+__device__ __forceinline__ float next_point_f(int lane, float L, float rL, float H, float rH, float NL, float NH) {
+    const int k = lane & 7;
+    const float w = H - L;
+    float v;
+    if (k == 0) v = NL;
+    else if (k == 1) v = NH;
+    else if (k == 2) v = L + rL * __fdiv_rn(w, rL - rH);
+    else v = fmaf(w, (float)(k - 2) * (1.0f / 6.0f), L);
+    if (!(v > L && v < H)) v = fmaf(w, ((float)k + 0.5f) * 0.125f, L);
+    if (!(v > L && v < H)) {
+        v = L + 0.5f * w;
+        if (!(v > L && v < H)) v = H;
+    }
+    return group8_sort(v, lane);
+}
+
 // One pass of the root searches: the pass evaluated, for each active search j, the sums
-// S(t_k) (tot[base + 2K j + k]) and the free-set curvature (tot[base + 2K j + K + k]) at the
-// points bc->pts[j][k].  Moves each bracket, stops a search when Newton from both ends of
-// its bracket agrees (both ends on one linear piece), when the bracket is within tol or
-// a few float spacings, or at max_passes (flagged), and writes the next points.
+// S(t_k) (tot[base + 2K j + k], double-float) and the free-set curvature (tot[base + 2K j +
+// K + k], float) at the points bc->pts[j][k].  Moves each bracket, stops a search when
+// Newton from both ends of its bracket agrees (both ends on one linear piece), when the
+// bracket is within tol or a few float spacings, or at max_passes (flagged), and writes
+// the next points.  Works in float and double-float; FP64 only for a finished root.
 template <class Bcast>
 __device__ void search_pass_update(const BlockScratch& sc, int base, volatile RowState* rows, volatile Bcast* bc,
                                    int nsearch, double tol_lambda, int max_passes) {
     const int lane = threadIdx.x, j = lane >> 3, k = lane & 7, g0 = lane & ~7;
     const int jj = j < nsearch ? j : 0;
     const bool row = j < nsearch && rows[jj].active;
-    const double reg = rows[jj].reg;
-    const double b = rows[jj].b;
-    double L = rows[jj].L, rL = rows[jj].rL, SL = rows[jj].SL;
-    double H = rows[jj].H, rH = rows[jj].rH, SH = rows[jj].SH;
+    const float reg = rows[jj].freg;
+    const DF b = DF{rows[jj].b_hi, rows[jj].b_lo};
+    float L = rows[jj].fL, H = rows[jj].fH, SL = rows[jj].fSL, SH = rows[jj].fSH;
+    DF rL = DF{rows[jj].rL_hi, rows[jj].rL_lo}, rH = DF{rows[jj].rH_hi, rows[jj].rH_lo};
     const int passes = rows[jj].passes + 1;
-    const double lk = (double)bc->pts[jj][k];
-    const double rk = df_to_double(sc.tot[base + 2 * K * jj + k]) - b - reg * lk;
-    const double Sk = df_to_double(sc.tot[base + 2 * K * jj + K + k]) + reg;
+    const float lk = bc->pts[jj][k];
+    // r_k = S_k - b - reg t_k
+    const float pr = reg * lk;
+    DF rk = df_add(sc.tot[base + 2 * K * jj + k], df_neg(b));
+    rk = df_add(rk, DF{-pr, -fmaf(reg, lk, -pr)});
+    const float Sk = sc.tot[base + 2 * K * jj + K + k].hi + reg;
     // new lower end: the largest point with r > 0; new upper end: the smallest point above
     // it with r <= 0 (points the rounding noise puts out of order are ignored)
-    const unsigned pos = (__ballot_sync(kFull, row && rk > 0.0 && lk > L && lk < H) >> g0) & 0xffu;
+    const unsigned pos = (__ballot_sync(kFull, row && df_pos(rk) && lk > L && lk < H) >> g0) & 0xffu;
     const int kL = pos ? 31 - __clz(pos) : -1;
-    const double lL = __shfl_sync(kFull, lk, g0 + (kL < 0 ? 0 : kL));
-    const double rLn = __shfl_sync(kFull, rk, g0 + (kL < 0 ? 0 : kL));
-    const double SLn = __shfl_sync(kFull, Sk, g0 + (kL < 0 ? 0 : kL));
+    const int sL = g0 + (kL < 0 ? 0 : kL);
+    const float lL = __shfl_sync(kFull, lk, sL);
+    const float rLh = __shfl_sync(kFull, rk.hi, sL), rLl = __shfl_sync(kFull, rk.lo, sL);
+    const float SLn = __shfl_sync(kFull, Sk, sL);
     if (kL >= 0) {
         L = lL;
-        rL = rLn;
+        rL = DF{rLh, rLl};
         SL = SLn;
     }
-    const unsigned neg = (__ballot_sync(kFull, row && !(rk > 0.0) && lk > L && lk < H) >> g0) & 0xffu;
+    const unsigned neg = (__ballot_sync(kFull, row && !df_pos(rk) && lk > L && lk < H) >> g0) & 0xffu;
     const int kH = neg ? __ffs(neg) - 1 : -1;
-    const double hH = __shfl_sync(kFull, lk, g0 + (kH < 0 ? 0 : kH));
-    const double rHn = __shfl_sync(kFull, rk, g0 + (kH < 0 ? 0 : kH));
-    const double SHn = __shfl_sync(kFull, Sk, g0 + (kH < 0 ? 0 : kH));
+    const int sH = g0 + (kH < 0 ? 0 : kH);
+    const float hH = __shfl_sync(kFull, lk, sH);
+    const float rHh = __shfl_sync(kFull, rk.hi, sH), rHl = __shfl_sync(kFull, rk.lo, sH);
+    const float SHn = __shfl_sync(kFull, Sk, sH);
     if (kH >= 0) {
         H = hH;
-        rH = rHn;
+        rH = DF{rHh, rHl};
         SH = SHn;
     }
-    double q = 0.0;
-    if (k == 0) q = rL / SL;
-    else if (k == 1) q = rH / SH;
-    const double NL = L + __shfl_sync(kFull, q, g0);
-    const double NH = H + __shfl_sync(kFull, q, g0 + 1);
-    const double w = H - L;
-    const double tol = tol_lambda * fmax(fabs(H), 1e-300);
-    double root = -1.0;
+    // Newton from both ends, NL = L + rL / SL and NH = H + rH / SH, in double-float
+    DF q = df_zero();
+    if (k == 0) q = df_div_f(rL, SL);
+    else if (k == 1) q = df_div_f(rH, SH);
+    const DF qL = DF{__shfl_sync(kFull, q.hi, g0), __shfl_sync(kFull, q.lo, g0)};
+    const DF qH = DF{__shfl_sync(kFull, q.hi, g0 + 1), __shfl_sync(kFull, q.lo, g0 + 1)};
+    const DF NL = df_add_f(qL, L), NH = df_add_f(qH, H);
+    const DF gap = df_add(NL, df_neg(NH));
+    const DF wd = two_sum(H, -L);
+    const float w = wd.hi;
+    const float tol = (float)tol_lambda * fabsf(H);
+    bool done = false;
     int how = 2;
-    if (kH >= 0 && rH == 0.0) root = H;
-    else if (fabs(NL - NH) <= tol || w <= tol || w <= 4.0 * float_ulp(H)) root = fmin(fmax(0.5 * (NL + NH), L), H);
-    if (root < 0.0 && passes >= max_passes) {
-        root = fmin(fmax(0.5 * (NL + NH), L), H);
+    if (kH >= 0 && rH.hi == 0.0f && rH.lo == 0.0f) done = true;
+    else if (fabsf(gap.hi) <= tol || w <= tol || w <= 4.0f * float_ulp_f(H)) done = true;
+    if (!done && passes >= max_passes) {
+        done = true;
         how = 3;  // not converged
     }
-    const bool done = row && root >= 0.0;
-    const float p = next_point(lane, L, rL, H, rH, NL, NH);
+    done = done && row;
+    const float p = next_point_f(lane, L, rL.hi, H, rH.hi, NL.hi, NH.hi);
     if (row && k == 0) {
+        volatile RowState* r = &rows[j];
+        r->fL = L;
+        r->fH = H;
+        r->fSL = SL;
+        r->fSH = SH;
+        r->rL_hi = rL.hi;
+        r->rL_lo = rL.lo;
+        r->rH_hi = rH.hi;
+        r->rH_lo = rH.lo;
+        r->passes = passes;
         if (done) {
-            store_row(&rows[j], b, L, rL, SL, H, rH, SH, root, fmax(fabs(rL), fabs(rH)), 0, passes, how);
+            // the root, once, in FP64: the midpoint of the two Newton predictions, in [L, H]
+            double root = (kH >= 0 && rH.hi == 0.0f && rH.lo == 0.0f)
+                              ? (double)H
+                              : 0.5 * (((double)NL.hi + (double)NL.lo) + ((double)NH.hi + (double)NH.lo));
+            root = fmin(fmax(root, (double)L), (double)H);
+            r->lam = root;
+            r->rlast = fmax(fabs((double)rL.hi), fabs((double)rH.hi));
+            r->active = 0;
+            r->how = how;
             publish_lambda(bc, j, root);
-        } else {
-            store_row(&rows[j], b, L, rL, SL, H, rH, SH, 0.0, 0.0, 1, passes, 2);
         }
     }
     if (row && !done) bc->pts[j][k] = p;
