@@ -196,6 +196,53 @@ pgdto_status pgdto_project_many(int count, pgdto_handle* const* hs, const float*
                                 const float* const* A, const double* b, float* const* x_out,
                                 double* lambda_out, pgdto_info* infos);
 
+/* ------------------------------------------------------------------ serving
+ * A server runs optimizer steps for many concurrent design sessions with continuous
+ * batching: every session keeps its design x and optimizer state on the device between
+ * its steps; submitted steps are uploaded asynchronously and, while one batch runs on the
+ * GPU, newly arrived steps queue and join the next launch (pgdto_step_many).  Sessions
+ * are admitted while their device memory fits the HBM budget; otherwise submit returns
+ * PGDTO_ERR_BUSY and the caller retries after sessions close.  Coupled-row sessions run
+ * one launch each inside the same cycle.  The paper has no serving layer; the step each
+ * request runs is Alg. 3 as above.
+ */
+typedef struct pgdto_server pgdto_server;
+
+typedef struct {
+    uint64_t session;            /* design id; its first request creates the session */
+    int64_t n;                   /* size of the design (fixed per session) */
+    int m;                       /* rows (fixed per session) */
+    const int64_t* seg_offsets;  /* as pgdto_create (NULL = dense rows); read on the first request */
+    float lo, hi;                /* box (fixed per session) */
+    const float* x0;             /* host, n floats: the starting design; first request only */
+    const float* grad_f;         /* host, n floats: grad f(rho_t), copied during submit */
+    const float* A;              /* host, constraint gradients (mode layout), copied during submit */
+    double g_val[4], G[4];       /* row scalars of this step */
+    float* x_out;                /* host, n floats: receives rho_{t+1} when the step completes */
+    int close_session;           /* 1: release the session's device memory after this step */
+} pgdto_request;
+
+/* budget_bytes: device memory the sessions may hold; max_sessions: open sessions at most;
+ * params: for every session (NULL = defaults); cuda_stream: stream of the launches. */
+pgdto_status pgdto_server_create(pgdto_server** srv, uint64_t budget_bytes, int max_sessions,
+                                 const pgdto_params* params, void* cuda_stream);
+
+/* Non-blocking: queue one step; *ticket identifies it.  PGDTO_ERR_BUSY: budget or session
+ * limit reached, or this session already has a step queued or running. */
+pgdto_status pgdto_submit(pgdto_server* srv, const pgdto_request* req, uint64_t* ticket);
+
+/* Non-blocking: *done = PGDTO_ERR_BUSY while the step is queued or running, else its final
+ * status (x_out written, info filled when non-NULL).  A finished ticket is forgotten after
+ * the first poll that reports it. */
+pgdto_status pgdto_poll(pgdto_server* srv, uint64_t ticket, pgdto_status* done, pgdto_info* info);
+
+/* Counters: launches (batches), steps completed, sessions open, bytes in use. */
+pgdto_status pgdto_server_stats(pgdto_server* srv, int64_t* batches, int64_t* steps, int* sessions,
+                                uint64_t* bytes_in_use);
+
+/* Wait for queued steps, stop the service thread, free every session. */
+void pgdto_server_destroy(pgdto_server* srv);
+
 /* Wait for the handle's stream and report the last step or projection. */
 pgdto_status pgdto_last_info(pgdto_handle* h, pgdto_info* info, double* lambda_out);
 

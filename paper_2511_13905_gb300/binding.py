@@ -50,6 +50,14 @@ class Info(ctypes.Structure):
                 "branch": self.branch, "status": self.status, "t": self.t}
 
 
+class Request(ctypes.Structure):
+    _fields_ = [("session", ctypes.c_uint64), ("n", ctypes.c_int64), ("m", ctypes.c_int),
+                ("seg_offsets", ctypes.POINTER(ctypes.c_int64)), ("lo", ctypes.c_float), ("hi", ctypes.c_float),
+                ("x0", ctypes.c_void_p), ("grad_f", ctypes.c_void_p), ("A", ctypes.c_void_p),
+                ("g_val", ctypes.c_double * 4), ("G", ctypes.c_double * 4), ("x_out", ctypes.c_void_p),
+                ("close_session", ctypes.c_int)]
+
+
 class PgdtoError(RuntimeError):
     def __init__(self, status, where):
         super().__init__("%s returned %s" % (where, STATUS_NAMES.get(status, status)))
@@ -95,6 +103,13 @@ def load(path=None):
                                                  ctypes.c_float, ctypes.c_float, ctypes.c_double, P, P, D, P, D,
                                                  ctypes.POINTER(Info), P]),
         "pgdto_version": (ctypes.c_char_p, []),
+        "pgdto_server_create": (ctypes.c_int, [ctypes.POINTER(H), ctypes.c_uint64, ctypes.c_int,
+                                               ctypes.POINTER(Params), P]),
+        "pgdto_submit": (ctypes.c_int, [H, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+        "pgdto_poll": (ctypes.c_int, [H, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Info)]),
+        "pgdto_server_stats": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint64)]),
+        "pgdto_server_destroy": (None, [H]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -274,3 +289,69 @@ def project_many(handles, zs, As, bs, x_outs, want_info=True):
     st = lib.pgdto_project_many(n, hs, _ptrs(zs), _ptrs(As), _rows4(bs), _ptrs(x_outs), lam, infos)
     lams = [[lam[4 * k + j] for j in range(handles[k].m)] for k in range(n)] if want_info else None
     return st, lams, (list(infos) if infos is not None else None)
+
+
+class Server:
+    """pgdto_server: continuous batching of optimizer steps over device-resident design sessions.
+
+    Host arrays are NumPy float32 (C-contiguous); the server copies grad_f and A during
+    submit, and writes rho_{t+1} into the x_out array when the step completes (keep it
+    alive until then)."""
+
+    def __init__(self, budget_bytes, max_sessions=1024, params=None, stream=None, **param_overrides):
+        self.lib = load()
+        p = params if params is not None else params_default(**param_overrides)
+        h = ctypes.c_void_p()
+        st = self.lib.pgdto_server_create(ctypes.byref(h), int(budget_bytes), int(max_sessions), ctypes.byref(p),
+                                          _stream_ptr(stream))
+        if st != PGDTO_OK:
+            raise PgdtoError(st, "pgdto_server_create")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, session, n, m, grad_f, A, g_val, G, x_out, x0=None, seg=None, lo=0.0, hi=1.0, close=False):
+        r = Request()
+        r.session, r.n, r.m, r.lo, r.hi = int(session), int(n), int(m), float(lo), float(hi)
+        segarr = None
+        if seg is not None:
+            segarr = (ctypes.c_int64 * (m + 1))(*[int(v) for v in seg])
+            r.seg_offsets = segarr
+        r.x0 = x0.ctypes.data if x0 is not None else None
+        r.grad_f = grad_f.ctypes.data
+        r.A = A.ctypes.data
+        for j in range(m):
+            r.g_val[j] = float(g_val[j])
+            r.G[j] = float(G[j])
+        r.x_out = x_out.ctypes.data
+        r.close_session = 1 if close else 0
+        t = ctypes.c_uint64()
+        st = self.lib.pgdto_submit(self.h, ctypes.byref(r), ctypes.byref(t))
+        if st == PGDTO_OK:
+            self._keep[t.value] = x_out
+        return st, t.value
+
+    def poll(self, ticket):
+        """(call status, done status or PGDTO_ERR_BUSY, Info)."""
+        d = ctypes.c_int()
+        info = Info()
+        st = self.lib.pgdto_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(d), ctypes.byref(info))
+        if st == PGDTO_OK and d.value != PGDTO_ERR_BUSY:
+            self._keep.pop(ticket, None)
+        return st, d.value, info
+
+    def stats(self):
+        b, s_, n = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        u = ctypes.c_uint64()
+        self.lib.pgdto_server_stats(self.h, ctypes.byref(b), ctypes.byref(s_), ctypes.byref(n), ctypes.byref(u))
+        return {"batches": b.value, "steps": s_.value, "sessions": n.value, "bytes_in_use": u.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pgdto_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

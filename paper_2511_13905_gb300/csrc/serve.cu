@@ -1,0 +1,312 @@
+// serve.cu -- the serving loop of include/pgdto.h: design sessions with device-resident
+// state, HBM-budget admission, asynchronous input upload, and continuous batching (a
+// service thread launches everything that is ready as one batched step while newer
+// requests queue for the next launch).  Host code only; the steps run in the kernels of
+// seg_kernels.cu / coupled_kernels.cu through the public entry points.
+#include <string.h>
+
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pgdto.h"
+
+namespace {
+
+struct Session {
+    uint64_t id = 0;
+    int64_t n = 0;
+    int m = 0;
+    int64_t a_len = 0;
+    bool coupled = false;
+    pgdto_handle* h = nullptr;
+    float* x = nullptr;       // device design (persists across steps)
+    float* g = nullptr;       // device staging of grad f
+    float* A = nullptr;       // device staging of the constraint gradients
+    float* in_pin = nullptr;  // pinned staging: [grad f | A | x0]
+    float* out_pin = nullptr; // pinned: rho_{t+1}
+    cudaEvent_t uploaded = nullptr;
+    uint64_t bytes = 0;
+    bool busy = false;        // a step is queued or running
+    bool closing = false;
+};
+
+struct Request {
+    uint64_t ticket = 0;
+    Session* s = nullptr;
+    double g_val[4] = {0, 0, 0, 0};
+    double G[4] = {0, 0, 0, 0};
+    float* x_out = nullptr;
+    bool close = false;
+};
+
+struct Done {
+    pgdto_status status = PGDTO_OK;
+    pgdto_info info;
+};
+
+}  // namespace
+
+struct pgdto_server {
+    uint64_t budget = 0, in_use = 0;
+    int max_sessions = 0;
+    pgdto_params params;
+    cudaStream_t stream = nullptr;  // launches and result copies
+    cudaStream_t copy = nullptr;    // input uploads
+    cudaEvent_t batch_done = nullptr;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::thread worker;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    std::map<uint64_t, Session*> sessions;
+    std::deque<Request> pending;
+    std::vector<Request> running;
+    std::map<uint64_t, Done> done;
+    int64_t batches = 0, steps = 0;
+};
+
+namespace {
+
+uint64_t session_bytes(int64_t n, int64_t a_len) {
+    // handle: x_prev, g_prev, d[2], z, z_lo (6 n floats) + workspace; session: x, g, A
+    return (uint64_t)(6 * n + 2 * n + a_len) * sizeof(float) + (uint64_t)(2u << 20);
+}
+
+void free_session(Session* s) {
+    if (!s) return;
+    pgdto_destroy(s->h);
+    cudaFree(s->x);
+    cudaFree(s->g);
+    cudaFree(s->A);
+    cudaFreeHost(s->in_pin);
+    cudaFreeHost(s->out_pin);
+    if (s->uploaded) cudaEventDestroy(s->uploaded);
+    delete s;
+}
+
+// Finish the batch in flight: results to the callers' buffers, reports, session cleanup.
+void finish_batch(pgdto_server* srv, std::vector<Request>& batch) {
+    cudaEventSynchronize(srv->batch_done);
+    std::vector<std::pair<uint64_t, Done>> results;
+    results.reserve(batch.size());
+    for (Request& r : batch) {
+        Done d;
+        memset(&d.info, 0, sizeof(d.info));
+        d.status = pgdto_last_info(r.s->h, &d.info, nullptr);
+        if (r.x_out) memcpy(r.x_out, r.s->out_pin, (size_t)r.s->n * sizeof(float));
+        results.emplace_back(r.ticket, d);
+    }
+    std::lock_guard<std::mutex> lock(srv->mu);
+    for (size_t i = 0; i < batch.size(); ++i) {
+        Request& r = batch[i];
+        srv->done[results[i].first] = results[i].second;
+        r.s->busy = false;
+        if (r.close) {
+            srv->in_use -= r.s->bytes;
+            srv->sessions.erase(r.s->id);
+            free_session(r.s);
+        }
+        srv->steps += 1;
+    }
+    batch.clear();
+}
+
+void launch_batch(pgdto_server* srv, std::vector<Request>& batch) {
+    std::vector<pgdto_handle*> hs;
+    std::vector<float*> xs;
+    std::vector<const float*> gs, As;
+    std::vector<double> gv, GG;
+    for (Request& r : batch) cudaStreamWaitEvent(srv->stream, r.s->uploaded, 0);
+    for (Request& r : batch) {
+        if (r.s->coupled) {
+            pgdto_step(r.s->h, r.s->x, r.s->g, r.s->A, r.g_val, r.G, nullptr);
+            continue;
+        }
+        hs.push_back(r.s->h);
+        xs.push_back(r.s->x);
+        gs.push_back(r.s->g);
+        As.push_back(r.s->A);
+        for (int j = 0; j < 4; ++j) {
+            gv.push_back(r.g_val[j]);
+            GG.push_back(r.G[j]);
+        }
+    }
+    if (!hs.empty())
+        pgdto_step_many((int)hs.size(), hs.data(), xs.data(), gs.data(), As.data(), gv.data(), GG.data(), nullptr);
+    for (Request& r : batch)
+        cudaMemcpyAsync(r.s->out_pin, r.s->x, (size_t)r.s->n * sizeof(float), cudaMemcpyDeviceToHost, srv->stream);
+    cudaEventRecord(srv->batch_done, srv->stream);
+    srv->batches += 1;
+}
+
+void service(pgdto_server* srv) {
+    std::vector<Request> batch;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lock(srv->mu);
+            srv->cv.wait(lock, [&] { return srv->stop || !srv->pending.empty(); });
+            if (srv->pending.empty() && srv->stop) return;
+            // everything queued now joins this launch (one step per session: submit enforces it)
+            while (!srv->pending.empty()) {
+                batch.push_back(srv->pending.front());
+                srv->pending.pop_front();
+            }
+            srv->running = batch;
+        }
+        launch_batch(srv, batch);
+        finish_batch(srv, batch);
+        {
+            std::lock_guard<std::mutex> lock(srv->mu);
+            srv->running.clear();
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" pgdto_status pgdto_server_create(pgdto_server** out, uint64_t budget_bytes, int max_sessions,
+                                            const pgdto_params* params, void* cuda_stream) {
+    if (!out || max_sessions < 1) return PGDTO_ERR_ARG;
+    *out = nullptr;
+    pgdto_server* srv = new pgdto_server();
+    srv->budget = budget_bytes;
+    srv->max_sessions = max_sessions;
+    if (params) srv->params = *params;
+    else pgdto_params_default(&srv->params);
+    srv->stream = (cudaStream_t)cuda_stream;
+    if (cudaStreamCreateWithFlags(&srv->copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&srv->batch_done, cudaEventDisableTiming) != cudaSuccess) {
+        if (srv->copy) cudaStreamDestroy(srv->copy);
+        delete srv;
+        return PGDTO_ERR_CUDA;
+    }
+    srv->worker = std::thread(service, srv);
+    *out = srv;
+    return PGDTO_OK;
+}
+
+extern "C" pgdto_status pgdto_submit(pgdto_server* srv, const pgdto_request* req, uint64_t* ticket) {
+    if (!srv || !req || !ticket || !req->grad_f || !req->A || req->n < 1 || req->m < 1 || req->m > 4)
+        return PGDTO_ERR_ARG;
+    std::unique_lock<std::mutex> lock(srv->mu);
+    Session* s = nullptr;
+    auto it = srv->sessions.find(req->session);
+    if (it != srv->sessions.end()) {
+        s = it->second;
+        if (s->n != req->n || s->m != req->m) return PGDTO_ERR_ARG;
+        if (s->busy) return PGDTO_ERR_BUSY;
+    } else {
+        if (!req->x0) return PGDTO_ERR_ARG;
+        const bool coupled = req->m > 1 && !req->seg_offsets;
+        const int64_t a_len = coupled || (req->m == 1) ? req->n * (int64_t)req->m : req->n;
+        const uint64_t bytes = session_bytes(req->n, a_len);
+        if ((int)srv->sessions.size() >= srv->max_sessions || srv->in_use + bytes > srv->budget)
+            return PGDTO_ERR_BUSY;
+        s = new Session();
+        s->id = req->session;
+        s->n = req->n;
+        s->m = req->m;
+        s->a_len = a_len;
+        s->coupled = coupled;
+        s->bytes = bytes;
+        pgdto_params p = srv->params;
+        p.mode = PGDTO_AUTO;
+        if (coupled) p.engine = 0;  // coupled rows run on the grid engine (one launch each)
+        pgdto_status st = pgdto_create(&s->h, req->n, req->m, req->seg_offsets, req->lo, req->hi, &p, srv->stream);
+        const size_t nb = (size_t)req->n * sizeof(float);
+        if (st == PGDTO_OK && (cudaMalloc(&s->x, nb) != cudaSuccess || cudaMalloc(&s->g, nb) != cudaSuccess ||
+                               cudaMalloc(&s->A, (size_t)a_len * sizeof(float)) != cudaSuccess ||
+                               cudaMallocHost(&s->in_pin, nb * 2 + (size_t)a_len * sizeof(float)) != cudaSuccess ||
+                               cudaMallocHost(&s->out_pin, nb) != cudaSuccess ||
+                               cudaEventCreateWithFlags(&s->uploaded, cudaEventDisableTiming) != cudaSuccess))
+            st = PGDTO_ERR_OOM;
+        if (st == PGDTO_OK) st = pgdto_set_state(s->h, nullptr, nullptr, nullptr, 0);
+        if (st != PGDTO_OK) {
+            free_session(s);
+            return st == PGDTO_ERR_OOM ? PGDTO_ERR_BUSY : st;
+        }
+        // the first design travels with the first request
+        memcpy(s->in_pin + req->n + a_len, req->x0, nb);
+        cudaMemcpyAsync(s->x, s->in_pin + req->n + a_len, nb, cudaMemcpyHostToDevice, srv->copy);
+        srv->sessions[s->id] = s;
+        srv->in_use += bytes;
+    }
+    // this step's inputs: host -> pinned staging (the caller's buffers are free on return),
+    // then an asynchronous upload the batch launch waits for
+    memcpy(s->in_pin, req->grad_f, (size_t)s->n * sizeof(float));
+    memcpy(s->in_pin + s->n, req->A, (size_t)s->a_len * sizeof(float));
+    cudaMemcpyAsync(s->g, s->in_pin, (size_t)s->n * sizeof(float), cudaMemcpyHostToDevice, srv->copy);
+    cudaMemcpyAsync(s->A, s->in_pin + s->n, (size_t)s->a_len * sizeof(float), cudaMemcpyHostToDevice, srv->copy);
+    cudaEventRecord(s->uploaded, srv->copy);
+    Request r;
+    r.ticket = srv->next_ticket++;
+    r.s = s;
+    for (int j = 0; j < req->m; ++j) {
+        r.g_val[j] = req->g_val[j];
+        r.G[j] = req->G[j];
+    }
+    r.x_out = req->x_out;
+    r.close = req->close_session != 0;
+    s->busy = true;
+    srv->pending.push_back(r);
+    *ticket = r.ticket;
+    lock.unlock();
+    srv->cv.notify_one();
+    return PGDTO_OK;
+}
+
+extern "C" pgdto_status pgdto_poll(pgdto_server* srv, uint64_t ticket, pgdto_status* done, pgdto_info* info) {
+    if (!srv || !done) return PGDTO_ERR_ARG;
+    std::lock_guard<std::mutex> lock(srv->mu);
+    auto it = srv->done.find(ticket);
+    if (it != srv->done.end()) {
+        *done = it->second.status;
+        if (info) *info = it->second.info;
+        srv->done.erase(it);
+        return PGDTO_OK;
+    }
+    for (const Request& r : srv->pending)
+        if (r.ticket == ticket) {
+            *done = PGDTO_ERR_BUSY;
+            return PGDTO_OK;
+        }
+    for (const Request& r : srv->running)
+        if (r.ticket == ticket) {
+            *done = PGDTO_ERR_BUSY;
+            return PGDTO_OK;
+        }
+    return PGDTO_ERR_ARG;  // unknown or already reported
+}
+
+extern "C" pgdto_status pgdto_server_stats(pgdto_server* srv, int64_t* batches, int64_t* steps, int* sessions,
+                                           uint64_t* bytes_in_use) {
+    if (!srv) return PGDTO_ERR_ARG;
+    std::lock_guard<std::mutex> lock(srv->mu);
+    if (batches) *batches = srv->batches;
+    if (steps) *steps = srv->steps;
+    if (sessions) *sessions = (int)srv->sessions.size();
+    if (bytes_in_use) *bytes_in_use = srv->in_use;
+    return PGDTO_OK;
+}
+
+extern "C" void pgdto_server_destroy(pgdto_server* srv) {
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        srv->stop = true;
+    }
+    srv->cv.notify_all();
+    if (srv->worker.joinable()) srv->worker.join();
+    cudaStreamSynchronize(srv->stream);
+    for (auto& kv : srv->sessions) free_session(kv.second);
+    srv->sessions.clear();
+    cudaEventDestroy(srv->batch_done);
+    cudaStreamDestroy(srv->copy);
+    delete srv;
+}
