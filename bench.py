@@ -305,6 +305,127 @@ def run_ours(args, rank, world, local_rank):
     return result
 
 
+# --------------------------------------------------------------------------- serving
+
+def run_serving(args, local_rank=0):
+    """Served (continuous batching) vs plain (one launch per request) on the same offered load.
+
+    `sessions` design sessions from the serving workload recipe (n log-uniform in
+    [4096, n_max], m in {1, 2, 4}, half of the m > 1 sessions independent, half coupled).
+    In each of `waves` waves every session submits its next step at once; a request's
+    latency runs from the wave's start to the moment its rho_{t+1} is in host memory.
+    Plain: the same requests one after another, each its own launch (H2D of grad f and A,
+    pgdto_step, D2H of x).  Both move the same bytes per request."""
+    import numpy as np
+    import torch
+
+    from paper_2511_13905_gb300 import binding, inputs
+    dev = torch.device("cuda", local_rank)
+    reqs = inputs.serving_requests(count=args.serve_sessions, n_max=args.serve_nmax)
+    probs = [inputs.request_problem(r) for r in reqs]
+    rng = np.random.default_rng(inputs.SEED_BASE + 77)
+    grads = [[(p["g"] * np.float32(1.0 + 0.05 * k)).astype(np.float32) for k in range(2)] for p in probs]
+    waves = args.serve_waves
+
+    def constraint_values(p, x):
+        # g_j(x_t) at the session's current design (all rows are linear here), computed by
+        # the client between waves, outside the timed region
+        x = x.astype(np.float64)
+        if p["mode"] == "independent":
+            return np.add.reduceat(x, p["seg"][:-1])
+        return np.atleast_2d(p["A"]).astype(np.float64) @ x
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
+
+    # served
+    srv = binding.Server(budget_bytes=64 << 30, max_sessions=len(probs) + 1)
+    outs = [np.empty(p["n"], np.float32) for p in probs]
+    gvals = [np.asarray(p["gval"], np.float64) for p in probs]
+    nc_served = 0
+    lat = []
+    warm = True
+    t_total = 0.0
+    for w in range(waves + 1):
+        t0 = time.perf_counter()
+        tickets = []
+        for i, p in enumerate(probs):
+            st, t = srv.submit(i, p["n"], p["m"], grads[i][w % 2], np.ascontiguousarray(p["A"]), gvals[i], p["G"],
+                               outs[i], x0=p["x"] if w == 0 else None, seg=p.get("seg"))
+            if st != binding.PGDTO_OK:
+                raise RuntimeError("submit failed: %s" % st)
+            tickets.append(t)
+        pending = set(range(len(tickets)))
+        done_at = {}
+        while pending:
+            for i in list(pending):
+                st, d, _ = srv.poll(tickets[i])
+                if d != binding.PGDTO_ERR_BUSY:
+                    if d not in (binding.PGDTO_OK, binding.PGDTO_NOT_CONVERGED):
+                        raise RuntimeError("served step failed: %s" % d)
+                    nc_served += int(d == binding.PGDTO_NOT_CONVERGED)
+                    done_at[i] = time.perf_counter()
+                    pending.discard(i)
+        t1 = time.perf_counter()
+        if not warm:
+            lat += [done_at[i] - t0 for i in range(len(probs))]
+            t_total += t1 - t0
+        warm = False
+        gvals = [constraint_values(p, outs[i]) for i, p in enumerate(probs)]
+    stats = srv.stats()
+    srv.close()
+    served_final = [o.copy() for o in outs]
+    served = {"p50_ms": 1e3 * pct(lat, 0.5), "p99_ms": 1e3 * pct(lat, 0.99),
+              "steps_per_s": len(lat) / t_total, "launches": stats["batches"], "not_converged": nc_served}
+
+    # plain: one launch per request
+    handles = [binding.Handle(p["n"], p["m"], seg=p.get("seg")) for p in probs]
+    xd = [torch.from_numpy(p["x"].copy()).to(dev) for p in probs]
+    gd = [torch.empty(p["n"], device=dev) for p in probs]
+    Ad = [torch.empty(np.asarray(p["A"]).size, device=dev) for p in probs]
+    # the same host arrays the served arm submits (pageable NumPy memory), copied by DMA
+    # straight to and from the device as the server does
+    ghost = [[torch.from_numpy(g) for g in gg] for gg in grads]
+    Ahost = [torch.from_numpy(np.ascontiguousarray(p["A"]).ravel()) for p in probs]
+    for h in handles:
+        h.set_state(None, None, None, 0)
+    gvals = [np.asarray(p["gval"], np.float64) for p in probs]
+    nc_plain = 0
+    lat_p = []
+    t_total_p = 0.0
+    warm = True
+    for w in range(waves + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, p in enumerate(probs):
+            gd[i].copy_(ghost[i][w % 2])
+            Ad[i].copy_(Ahost[i])
+            st, _ = handles[i].step(xd[i], gd[i], Ad[i], gvals[i], p["G"], want_info=True)
+            if st not in (binding.PGDTO_OK, binding.PGDTO_NOT_CONVERGED):
+                raise RuntimeError("plain step failed: %s" % st)
+            nc_plain += int(st == binding.PGDTO_NOT_CONVERGED)
+            torch.from_numpy(outs[i]).copy_(xd[i])
+            if not warm:
+                lat_p.append(time.perf_counter() - t0)
+        t1 = time.perf_counter()
+        if not warm:
+            t_total_p += t1 - t0
+        warm = False
+        gvals = [constraint_values(p, outs[i]) for i, p in enumerate(probs)]
+    for h in handles:
+        h.close()
+    plain = {"p50_ms": 1e3 * pct(lat_p, 0.5), "p99_ms": 1e3 * pct(lat_p, 0.99),
+             "steps_per_s": len(lat_p) / t_total_p, "not_converged": nc_plain}
+    # equal accuracy: both arms ran the same trajectories; the designs they end on
+    diff = max(float(np.max(np.abs(a.astype(np.float64) - b.astype(np.float64)))) for a, b in zip(served_final, outs))
+    return {"sessions": len(probs), "waves": waves, "requests_timed": len(lat),
+            "n_range": [min(p["n"] for p in probs), max(p["n"] for p in probs)],
+            "modes": {m: sum(1 for p in probs if p["mode"] == m) for m in ("single", "independent", "coupled")},
+            "served": served, "plain": plain, "max_abs_diff_final_x": diff,
+            "latency": "wave start to rho_{t+1} in host memory; every session submits one step per wave"}
+
+
 # --------------------------------------------------------------------------- oracle
 
 def oracle_workload(wl):
@@ -387,6 +508,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-sessions", type=int, default=48)
+    ap.add_argument("--serve-waves", type=int, default=6)
+    ap.add_argument("--serve-nmax", type=int, default=1 << 20)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -404,6 +529,8 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     res = run_ours(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_serving:
+        res["serving"] = run_serving(args, local_rank)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             res["cpu_baseline"] = cpu_baseline_subprocess(args.workload, 1000, 20.0)

@@ -199,12 +199,14 @@ pgdto_status pgdto_project_many(int count, pgdto_handle* const* hs, const float*
 /* ------------------------------------------------------------------ serving
  * A server runs optimizer steps for many concurrent design sessions with continuous
  * batching: every session keeps its design x and optimizer state on the device between
- * its steps; submitted steps are uploaded asynchronously and, while one batch runs on the
- * GPU, newly arrived steps queue and join the next launch (pgdto_step_many).  Sessions
- * are admitted while their device memory fits the HBM budget; otherwise submit returns
- * PGDTO_ERR_BUSY and the caller retries after sessions close.  Coupled-row sessions run
- * one launch each inside the same cycle.  The paper has no serving layer; the step each
- * request runs is Alg. 3 as above.
+ * its steps; a submitted step's inputs are copied by DMA from the caller's buffers on a
+ * copy stream and, while one cycle runs on the GPU, newly arrived steps queue for the
+ * next.  A cycle launches every queued single/independent session up to 131072 variables
+ * as one batched step (pgdto_step_many), then each larger or coupled-row session in a
+ * launch of its own, smallest first; each launch's results are delivered as soon as that
+ * launch completes.  Sessions are admitted while their device memory fits the HBM budget;
+ * otherwise submit returns PGDTO_ERR_BUSY and the caller retries after sessions close.
+ * The paper has no serving layer; the step each request runs is Alg. 3 as above.
  */
 typedef struct pgdto_server pgdto_server;
 
@@ -227,8 +229,11 @@ typedef struct {
 pgdto_status pgdto_server_create(pgdto_server** srv, uint64_t budget_bytes, int max_sessions,
                                  const pgdto_params* params, void* cuda_stream);
 
-/* Non-blocking: queue one step; *ticket identifies it.  PGDTO_ERR_BUSY: budget or session
- * limit reached, or this session already has a step queued or running. */
+/* Queue one step; *ticket identifies it.  Returns once the inputs (grad_f, A, and x0 on a
+ * session's first request) have been copied to the device, so those buffers are free on
+ * return; x_out must stay valid until the step is reported.  PGDTO_ERR_BUSY: budget or
+ * session limit reached, or this session already has a step queued or running.
+ * PGDTO_ERR_CUDA: an upload failed (a new session is not kept). */
 pgdto_status pgdto_submit(pgdto_server* srv, const pgdto_request* req, uint64_t* ticket);
 
 /* Non-blocking: *done = PGDTO_ERR_BUSY while the step is queued or running, else its final

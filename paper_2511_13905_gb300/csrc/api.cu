@@ -8,6 +8,7 @@
 
 #include "../../include/pgdto.h"
 #include "dev_common.cuh"
+#include "handle_internal.h"
 #include "kernels.h"
 
 using namespace pgdto;
@@ -248,6 +249,27 @@ extern "C" pgdto_status pgdto_get_state(pgdto_handle* h, float* x_prev, float* g
 }
 
 // Read the device report; clear the sticky device error once it has been reported.
+// The step status from a copied report and control block; an error is reported once, after
+// which the control block is cleared on the stream so the next launch starts clean.
+static pgdto_status interpret_info(pgdto_handle* h, const DeviceInfo& di, const int* ctrl, pgdto_info* info,
+                                   bool wait_reset) {
+    int status = di.status;
+    const int sticky = ctrl[2];
+    const int aborted = ctrl[3];
+    if (aborted && status == PGDTO_OK) status = sticky ? sticky : PGDTO_ERR_TIMEOUT;
+    if (sticky != 0 || aborted) {
+        cudaMemsetAsync(h->work, 0, h->ctrl_bytes, h->stream);
+        if (wait_reset) cudaStreamSynchronize(h->stream);
+        if (status == PGDTO_OK) status = sticky;
+    }
+    if (info) {
+        static_assert(sizeof(DeviceInfo) == sizeof(pgdto_info), "report layouts differ");
+        memcpy(info, &di, sizeof(di));
+        info->status = status;
+    }
+    return (pgdto_status)status;
+}
+
 static pgdto_status read_info(pgdto_handle* h, pgdto_info* info, double* lambda_out) {
     DeviceInfo di;
     cudaError_t e = cudaMemcpyAsync(&di, h->dev_info, sizeof(di), cudaMemcpyDeviceToHost, h->stream);
@@ -257,24 +279,23 @@ static pgdto_status read_info(pgdto_handle* h, pgdto_info* info, double* lambda_
     if (e != cudaSuccess) return cuda_fail(e);
     e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e);
-    int status = di.status;
-    const int sticky = ctrl[2];
-    const int aborted = ctrl[3];
-    if (aborted && status == PGDTO_OK) status = sticky ? sticky : PGDTO_ERR_TIMEOUT;
-    if (sticky != 0 || aborted) {
-        // errors are reported once; the next call starts from a clean control block
-        cudaMemsetAsync(h->work, 0, h->ctrl_bytes, h->stream);
-        cudaStreamSynchronize(h->stream);
-        if (status == PGDTO_OK) status = sticky;
-    }
-    if (info) {
-        static_assert(sizeof(DeviceInfo) == sizeof(pgdto_info), "report layouts differ");
-        memcpy(info, &di, sizeof(di));
-        info->status = status;
-    }
     if (lambda_out)
         for (int j = 0; j < h->m; ++j) lambda_out[j] = di.lambda[j];
-    return (pgdto_status)status;
+    return interpret_info(h, di, ctrl, info, true);
+}
+
+pgdto_status pgdto_info_enqueue(pgdto_handle* h, pgdto_info_slot* slot) {
+    if (!h || !slot) return PGDTO_ERR_ARG;
+    cudaError_t e = cudaMemcpyAsync(&slot->info, h->dev_info, sizeof(DeviceInfo), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(slot->ctrl, h->work, sizeof(slot->ctrl), cudaMemcpyDeviceToHost, h->stream);
+    return e == cudaSuccess ? PGDTO_OK : cuda_fail(e);
+}
+
+pgdto_status pgdto_info_collect(pgdto_handle* h, const pgdto_info_slot* slot, pgdto_info* info) {
+    if (!h || !slot) return PGDTO_ERR_ARG;
+    DeviceInfo di;
+    memcpy(&di, &slot->info, sizeof(di));
+    return interpret_info(h, di, slot->ctrl, info, false);
 }
 
 extern "C" pgdto_status pgdto_last_info(pgdto_handle* h, pgdto_info* info, double* lambda_out) {

@@ -1,0 +1,21 @@
+// handle_internal.h -- entry points shared by api.cu and serve.cu that are not part of the
+// public C ABI: a step report read without synchronising the handle's stream.
+#pragma once
+
+#include "../../include/pgdto.h"
+
+// The report of a handle's last launch as the device wrote it: pgdto_info plus the four
+// words of the grid control block that carry a sticky error and the abort flag.
+struct pgdto_info_slot {
+    pgdto_info info;
+    int ctrl[4];
+};
+
+// Enqueue the copy of the handle's report into `slot` (pinned host memory) on the handle's
+// stream, behind the launch it reports on.  Returns without waiting.
+pgdto_status pgdto_info_enqueue(pgdto_handle* h, pgdto_info_slot* slot);
+
+// Interpret a slot whose copy has completed (the caller waited on an event recorded after
+// pgdto_info_enqueue): the step's status, and `info` when non-null.  An error clears the
+// control block with an asynchronous memset on the handle's stream, as pgdto_last_info does.
+pgdto_status pgdto_info_collect(pgdto_handle* h, const pgdto_info_slot* slot, pgdto_info* info);

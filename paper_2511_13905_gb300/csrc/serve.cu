@@ -1,10 +1,14 @@
 // serve.cu -- the serving loop of include/pgdto.h: design sessions with device-resident
-// state, HBM-budget admission, asynchronous input upload, and continuous batching (a
-// service thread launches everything that is ready as one batched step while newer
-// requests queue for the next launch).  Host code only; the steps run in the kernels of
+// state, HBM-budget admission, input upload on a copy stream, and continuous batching (a
+// service thread launches everything that is ready while newer requests queue for the
+// next cycle).  Inputs are copied by DMA straight from the caller's memory (the copy
+// engine reads pageable memory at full speed on a coherent CPU-GPU link, so there is no
+// host-side staging copy); each launch unit's reports and results are read as soon as
+// that unit's event completes.  Host code only; the steps run in the kernels of
 // seg_kernels.cu / coupled_kernels.cu through the public entry points.
 #include <string.h>
 
+#include <algorithm>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -15,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/pgdto.h"
+#include "handle_internal.h"
 
 namespace {
 
@@ -24,12 +29,12 @@ struct Session {
     int m = 0;
     int64_t a_len = 0;
     bool coupled = false;
+    bool own_launch = false;  // coupled rows, or too large for the batched cluster launch
     pgdto_handle* h = nullptr;
     float* x = nullptr;       // device design (persists across steps)
     float* g = nullptr;       // device staging of grad f
     float* A = nullptr;       // device staging of the constraint gradients
-    float* in_pin = nullptr;  // pinned staging: [grad f | A | x0]
-    float* out_pin = nullptr; // pinned: rho_{t+1}
+    pgdto_info_slot* slot = nullptr;  // pinned: the last step's report
     cudaEvent_t uploaded = nullptr;
     uint64_t bytes = 0;
     bool busy = false;        // a step is queued or running
@@ -52,13 +57,18 @@ struct Done {
 
 }  // namespace
 
+// Single/independent sessions up to this size share one batched cluster launch; larger
+// ones (and coupled rows) get a grid launch of their own, shortest first.
+static const int64_t kServeBatchMaxN = int64_t(1) << 17;
+
 struct pgdto_server {
     uint64_t budget = 0, in_use = 0;
     int max_sessions = 0;
     pgdto_params params;
     cudaStream_t stream = nullptr;  // launches and result copies
     cudaStream_t copy = nullptr;    // input uploads
-    cudaEvent_t batch_done = nullptr;
+    cudaStream_t dtoh = nullptr;    // result downloads
+    std::vector<cudaEvent_t> unit_done;  // one per launch unit of a cycle (batched group, own launches)
     std::mutex mu;
     std::condition_variable cv;
     std::thread worker;
@@ -84,29 +94,38 @@ void free_session(Session* s) {
     cudaFree(s->x);
     cudaFree(s->g);
     cudaFree(s->A);
-    cudaFreeHost(s->in_pin);
-    cudaFreeHost(s->out_pin);
+    cudaFreeHost(s->slot);
     if (s->uploaded) cudaEventDestroy(s->uploaded);
     delete s;
 }
 
-// Finish the batch in flight: results to the callers' buffers, reports, session cleanup.
-void finish_batch(pgdto_server* srv, std::vector<Request>& batch) {
-    cudaEventSynchronize(srv->batch_done);
-    std::vector<std::pair<uint64_t, Done>> results;
-    results.reserve(batch.size());
-    for (Request& r : batch) {
-        Done d;
-        memset(&d.info, 0, sizeof(d.info));
-        d.status = pgdto_last_info(r.s->h, &d.info, nullptr);
-        if (r.x_out) memcpy(r.x_out, r.s->out_pin, (size_t)r.s->n * sizeof(float));
-        results.emplace_back(r.ticket, d);
+// Complete one launch unit: wait for its event, copy the designs to the callers' buffers,
+// publish the reports (poll sees them at once), release closing sessions.
+void finish_unit(pgdto_server* srv, cudaEvent_t ev, std::vector<Request>& unit) {
+    cudaEventSynchronize(ev);
+    std::vector<Done> results(unit.size());
+    cudaStreamWaitEvent(srv->dtoh, ev, 0);
+    for (size_t i = 0; i < unit.size(); ++i) {
+        Request& r = unit[i];
+        memset(&results[i].info, 0, sizeof(results[i].info));
+        results[i].status = pgdto_info_collect(r.s->h, r.s->slot, &results[i].info);
+        if (r.x_out &&
+            cudaMemcpyAsync(r.x_out, r.s->x, (size_t)r.s->n * sizeof(float), cudaMemcpyDeviceToHost, srv->dtoh) !=
+                cudaSuccess)
+            results[i].status = PGDTO_ERR_CUDA;
     }
+    if (cudaStreamSynchronize(srv->dtoh) != cudaSuccess)
+        for (Done& d : results) d.status = PGDTO_ERR_CUDA;
     std::lock_guard<std::mutex> lock(srv->mu);
-    for (size_t i = 0; i < batch.size(); ++i) {
-        Request& r = batch[i];
-        srv->done[results[i].first] = results[i].second;
+    for (size_t i = 0; i < unit.size(); ++i) {
+        Request& r = unit[i];
+        srv->done[r.ticket] = results[i];
         r.s->busy = false;
+        for (size_t q = 0; q < srv->running.size(); ++q)
+            if (srv->running[q].ticket == r.ticket) {
+                srv->running.erase(srv->running.begin() + q);
+                break;
+            }
         if (r.close) {
             srv->in_use -= r.s->bytes;
             srv->sessions.erase(r.s->id);
@@ -114,35 +133,54 @@ void finish_batch(pgdto_server* srv, std::vector<Request>& batch) {
         }
         srv->steps += 1;
     }
-    batch.clear();
 }
 
-void launch_batch(pgdto_server* srv, std::vector<Request>& batch) {
-    std::vector<pgdto_handle*> hs;
-    std::vector<float*> xs;
-    std::vector<const float*> gs, As;
-    std::vector<double> gv, GG;
-    for (Request& r : batch) cudaStreamWaitEvent(srv->stream, r.s->uploaded, 0);
-    for (Request& r : batch) {
-        if (r.s->coupled) {
-            pgdto_step(r.s->h, r.s->x, r.s->g, r.s->A, r.g_val, r.G, nullptr);
-            continue;
-        }
-        hs.push_back(r.s->h);
-        xs.push_back(r.s->x);
-        gs.push_back(r.s->g);
-        As.push_back(r.s->A);
-        for (int j = 0; j < 4; ++j) {
-            gv.push_back(r.g_val[j]);
-            GG.push_back(r.G[j]);
-        }
+// One cycle: the batched group (one cluster launch for every small single/independent
+// session), then each large or coupled session in its own launch, shortest first; each
+// unit's results are reported as soon as its own event completes.
+void run_cycle(pgdto_server* srv, std::vector<Request>& batch) {
+    std::vector<Request> group;
+    std::vector<Request> own;
+    for (Request& r : batch) (r.s->own_launch ? own : group).push_back(r);
+    std::sort(own.begin(), own.end(), [](const Request& a, const Request& b) { return a.s->n < b.s->n; });
+    while (srv->unit_done.size() < own.size() + 1) {
+        cudaEvent_t e;
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        srv->unit_done.push_back(e);
     }
-    if (!hs.empty())
+    for (Request& r : batch) cudaStreamWaitEvent(srv->stream, r.s->uploaded, 0);
+    if (!group.empty()) {
+        std::vector<pgdto_handle*> hs;
+        std::vector<float*> xs;
+        std::vector<const float*> gs, As;
+        std::vector<double> gv, GG;
+        for (Request& r : group) {
+            hs.push_back(r.s->h);
+            xs.push_back(r.s->x);
+            gs.push_back(r.s->g);
+            As.push_back(r.s->A);
+            for (int j = 0; j < 4; ++j) {
+                gv.push_back(r.g_val[j]);
+                GG.push_back(r.G[j]);
+            }
+        }
         pgdto_step_many((int)hs.size(), hs.data(), xs.data(), gs.data(), As.data(), gv.data(), GG.data(), nullptr);
-    for (Request& r : batch)
-        cudaMemcpyAsync(r.s->out_pin, r.s->x, (size_t)r.s->n * sizeof(float), cudaMemcpyDeviceToHost, srv->stream);
-    cudaEventRecord(srv->batch_done, srv->stream);
-    srv->batches += 1;
+        for (Request& r : group) pgdto_info_enqueue(r.s->h, r.s->slot);
+        cudaEventRecord(srv->unit_done[0], srv->stream);
+    }
+    for (size_t q = 0; q < own.size(); ++q) {
+        Request& r = own[q];
+        pgdto_step(r.s->h, r.s->x, r.s->g, r.s->A, r.g_val, r.G, nullptr);
+        pgdto_info_enqueue(r.s->h, r.s->slot);
+        cudaEventRecord(srv->unit_done[q + 1], srv->stream);
+    }
+    srv->batches += (group.empty() ? 0 : 1) + (int64_t)own.size();
+    if (!group.empty()) finish_unit(srv, srv->unit_done[0], group);
+    for (size_t q = 0; q < own.size(); ++q) {
+        std::vector<Request> one(1, own[q]);
+        finish_unit(srv, srv->unit_done[q + 1], one);
+    }
+    batch.clear();
 }
 
 void service(pgdto_server* srv) {
@@ -159,12 +197,7 @@ void service(pgdto_server* srv) {
             }
             srv->running = batch;
         }
-        launch_batch(srv, batch);
-        finish_batch(srv, batch);
-        {
-            std::lock_guard<std::mutex> lock(srv->mu);
-            srv->running.clear();
-        }
+        run_cycle(srv, batch);
     }
 }
 
@@ -181,8 +214,9 @@ extern "C" pgdto_status pgdto_server_create(pgdto_server** out, uint64_t budget_
     else pgdto_params_default(&srv->params);
     srv->stream = (cudaStream_t)cuda_stream;
     if (cudaStreamCreateWithFlags(&srv->copy, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&srv->batch_done, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&srv->dtoh, cudaStreamNonBlocking) != cudaSuccess) {
         if (srv->copy) cudaStreamDestroy(srv->copy);
+        if (srv->dtoh) cudaStreamDestroy(srv->dtoh);
         delete srv;
         return PGDTO_ERR_CUDA;
     }
@@ -196,6 +230,7 @@ extern "C" pgdto_status pgdto_submit(pgdto_server* srv, const pgdto_request* req
         return PGDTO_ERR_ARG;
     std::unique_lock<std::mutex> lock(srv->mu);
     Session* s = nullptr;
+    bool fresh = false;
     auto it = srv->sessions.find(req->session);
     if (it != srv->sessions.end()) {
         s = it->second;
@@ -214,6 +249,7 @@ extern "C" pgdto_status pgdto_submit(pgdto_server* srv, const pgdto_request* req
         s->m = req->m;
         s->a_len = a_len;
         s->coupled = coupled;
+        s->own_launch = coupled || req->n > kServeBatchMaxN;
         s->bytes = bytes;
         pgdto_params p = srv->params;
         p.mode = PGDTO_AUTO;
@@ -222,8 +258,7 @@ extern "C" pgdto_status pgdto_submit(pgdto_server* srv, const pgdto_request* req
         const size_t nb = (size_t)req->n * sizeof(float);
         if (st == PGDTO_OK && (cudaMalloc(&s->x, nb) != cudaSuccess || cudaMalloc(&s->g, nb) != cudaSuccess ||
                                cudaMalloc(&s->A, (size_t)a_len * sizeof(float)) != cudaSuccess ||
-                               cudaMallocHost(&s->in_pin, nb * 2 + (size_t)a_len * sizeof(float)) != cudaSuccess ||
-                               cudaMallocHost(&s->out_pin, nb) != cudaSuccess ||
+                               cudaMallocHost(&s->slot, sizeof(pgdto_info_slot)) != cudaSuccess ||
                                cudaEventCreateWithFlags(&s->uploaded, cudaEventDisableTiming) != cudaSuccess))
             st = PGDTO_ERR_OOM;
         if (st == PGDTO_OK) st = pgdto_set_state(s->h, nullptr, nullptr, nullptr, 0);
@@ -231,19 +266,34 @@ extern "C" pgdto_status pgdto_submit(pgdto_server* srv, const pgdto_request* req
             free_session(s);
             return st == PGDTO_ERR_OOM ? PGDTO_ERR_BUSY : st;
         }
-        // the first design travels with the first request
-        memcpy(s->in_pin + req->n + a_len, req->x0, nb);
-        cudaMemcpyAsync(s->x, s->in_pin + req->n + a_len, nb, cudaMemcpyHostToDevice, srv->copy);
         srv->sessions[s->id] = s;
         srv->in_use += bytes;
+        fresh = true;
     }
-    // this step's inputs: host -> pinned staging (the caller's buffers are free on return),
-    // then an asynchronous upload the batch launch waits for
-    memcpy(s->in_pin, req->grad_f, (size_t)s->n * sizeof(float));
-    memcpy(s->in_pin + s->n, req->A, (size_t)s->a_len * sizeof(float));
-    cudaMemcpyAsync(s->g, s->in_pin, (size_t)s->n * sizeof(float), cudaMemcpyHostToDevice, srv->copy);
-    cudaMemcpyAsync(s->A, s->in_pin + s->n, (size_t)s->a_len * sizeof(float), cudaMemcpyHostToDevice, srv->copy);
-    cudaEventRecord(s->uploaded, srv->copy);
+    // the session is reserved (busy) while its inputs upload outside the lock, so other
+    // submits, polls and the service thread carry on meanwhile
+    s->busy = true;
+    lock.unlock();
+    // DMA from the caller's buffers on the copy stream, waited for before returning, so the
+    // buffers are free on return whether they are pageable or pinned
+    const size_t nb = (size_t)s->n * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    if (fresh) e = cudaMemcpyAsync(s->x, req->x0, nb, cudaMemcpyHostToDevice, srv->copy);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->g, req->grad_f, nb, cudaMemcpyHostToDevice, srv->copy);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->A, req->A, (size_t)s->a_len * sizeof(float), cudaMemcpyHostToDevice, srv->copy);
+    if (e == cudaSuccess) e = cudaEventRecord(s->uploaded, srv->copy);
+    if (e == cudaSuccess) e = cudaEventSynchronize(s->uploaded);
+    lock.lock();
+    if (e != cudaSuccess) {
+        s->busy = false;
+        if (fresh) {
+            srv->in_use -= s->bytes;
+            srv->sessions.erase(s->id);
+            free_session(s);
+        }
+        return PGDTO_ERR_CUDA;
+    }
     Request r;
     r.ticket = srv->next_ticket++;
     r.s = s;
@@ -253,7 +303,6 @@ extern "C" pgdto_status pgdto_submit(pgdto_server* srv, const pgdto_request* req
     }
     r.x_out = req->x_out;
     r.close = req->close_session != 0;
-    s->busy = true;
     srv->pending.push_back(r);
     *ticket = r.ticket;
     lock.unlock();
@@ -306,7 +355,8 @@ extern "C" void pgdto_server_destroy(pgdto_server* srv) {
     cudaStreamSynchronize(srv->stream);
     for (auto& kv : srv->sessions) free_session(kv.second);
     srv->sessions.clear();
-    cudaEventDestroy(srv->batch_done);
+    for (cudaEvent_t e : srv->unit_done) cudaEventDestroy(e);
     cudaStreamDestroy(srv->copy);
+    cudaStreamDestroy(srv->dtoh);
     delete srv;
 }
