@@ -305,6 +305,94 @@ def run_ours(args, rank, world, local_rank):
     return result
 
 
+# --------------------------------------------------------------------------- batched
+
+def run_batched(args, local_rank=0):
+    """B instances of the 256x128 single-row workload (n = 32,768 each, seeds 0..B-1), one
+    step each from the seeded state: one pgdto_step_many launch (batched) against B
+    pgdto_step launches back to back on the same stream (plain).  Device time by CUDA
+    events around each form; state reset and an L2 flush between timed repetitions."""
+    import numpy as np
+    import torch
+
+    from paper_2511_13905_gb300 import binding, inputs
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    B = args.batch_instances
+    cfgs = [inputs.config1(seed_offset=k) for k in range(B)]
+    n = cfgs[0]["n"]
+
+    def T(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    hs = [binding.Handle(c["n"], 1) for c in cfgs]
+    x0 = [T(c["x"]) for c in cfgs]
+    xs = [t.clone() for t in x0]
+    gs = [T(c["g"]) for c in cfgs]
+    As = [T(c["A"]) for c in cfgs]
+    prev = [(T(c["x_prev"]), T(c["g_prev"]), T(c["d_prev"])) for c in cfgs]
+    gvals = [c["gval"] for c in cfgs]
+    Gs = [c["G"] for c in cfgs]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def reset():
+        for k in range(B):
+            xs[k].copy_(x0[k])
+            hs[k].set_state(prev[k][0], prev[k][1], prev[k][2], cfgs[k]["t"])
+
+    def batched():
+        st, _ = binding.step_many(hs, xs, gs, As, gvals, Gs, want_info=False)
+        if st != binding.PGDTO_OK:
+            raise RuntimeError("pgdto_step_many failed: %s" % st)
+
+    def plain():
+        for k in range(B):
+            st, _ = hs[k].step(xs[k], gs[k], As[k], gvals[k], Gs[k], want_info=False)
+            if st != binding.PGDTO_OK:
+                raise RuntimeError("pgdto_step failed: %s" % st)
+
+    def timed(fn, reps):
+        out, passes = [], []
+        for r in range(args.warmup + reps):
+            reset()
+            flush.fill_(float(r))
+            l0 = sum(h.kernel_launches() for h in hs)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            launches = sum(h.kernel_launches() for h in hs) - l0
+            infos = [h.last_info()[2] for h in hs]
+            bad = [i.status for i in infos if i.status not in (0, binding.PGDTO_NOT_CONVERGED)]
+            if bad:
+                raise RuntimeError("batched workload step failed: %s" % bad[:4])
+            if r >= args.warmup:
+                out.append(e0.elapsed_time(e1))
+                passes.append(sum(i.passes for i in infos))
+        return float(np.median(out)), float(np.mean(passes)), launches, [h.last_info()[2] for h in hs]
+
+    t_b, passes_b, launches_b, info_b = timed(batched, args.steps)
+    x_b = [x.cpu().numpy() for x in xs]
+    t_p, passes_p, launches_p, info_p = timed(plain, args.steps)
+    diff = max(float(np.max(np.abs(a.astype(np.float64) - x.cpu().numpy()))) for a, x in zip(x_b, xs))
+    bytes_b = sum(algorithmic_bytes(n, 1, i.passes) for i in info_b)
+    peak, _ = peaks()
+    for h in hs:
+        h.close()
+    return {"workload": "%d x volume_2d_256x128 (n=%d, m=1, one step each)" % (B, n),
+            "batched": {"ms": t_b, "steps_per_s": B / (t_b / 1e3), "launches": launches_b,
+                        "passes_per_instance": passes_b / B,
+                        "roofline": {"bound": "hbm", "achieved": bytes_b / (t_b / 1e3) / 1e9, "peak": peak,
+                                     "unit": "GB/s", "frac": bytes_b / (t_b / 1e3) / 1e9 / peak,
+                                     "algorithmic_bytes_per_launch": bytes_b}},
+            "plain": {"ms": t_p, "steps_per_s": B / (t_p / 1e3), "launches": launches_p,
+                      "passes_per_instance": passes_p / B},
+            "max_abs_diff_x_batched_vs_plain": diff,
+            "timing": "median of %d CUDA-event-timed repetitions, L2 flushed (256 MiB write) before each" % args.steps}
+
+
 # --------------------------------------------------------------------------- serving
 
 def run_serving(args, local_rank=0):
@@ -509,6 +597,8 @@ def main():
     ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--serve-sessions", type=int, default=48)
     ap.add_argument("--serve-waves", type=int, default=6)
     ap.add_argument("--serve-nmax", type=int, default=1 << 20)
@@ -529,6 +619,8 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     res = run_ours(args, rank, world, local_rank)
+    if rank == 0 and world == 1 and not args.no_batched:
+        res["batched"] = run_batched(args, local_rank)
     if rank == 0 and world == 1 and not args.no_serving:
         res["serving"] = run_serving(args, local_rank)
     if rank == 0:

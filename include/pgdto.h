@@ -84,7 +84,11 @@ typedef struct {
     int engine;             /* 0 auto, 1 grid (all SMs, grid-wide reductions), 2 cluster (one
                                thread-block cluster, reductions in distributed shared memory;
                                single and independent rows only).  Auto: cluster for n up to
-                               the handle's threshold, grid above it */
+                               131072, grid above it */
+    int cluster_elems;      /* cluster engine: variables per thread block; a problem's cluster
+                               has ceil(n / cluster_elems) blocks rounded up to a power of two,
+                               at most 16.  It depends on n alone, so a problem's result is the
+                               same alone and in any batch.  0 = 16384 */
 } pgdto_params;
 
 /* Per-call report. */
@@ -180,13 +184,16 @@ pgdto_status pgdto_project(pgdto_handle* h, const float* z, const float* A, cons
                            float* x_out, double* lambda_out, pgdto_info* info);
 
 /*
- * Batched form: `count` independent steps in ONE launch (the cluster engine runs one
- * problem per thread-block cluster and takes the next from the list).  Handles must be in
- * SINGLE or INDEPENDENT mode and share the first handle's stream.  Per handle k:
- * x[k], grad_f[k], A[k] as for pgdto_step; g_val[4k + j], G[4k + j] its row scalars.
- * Each handle's state advances as after pgdto_step.  infos: NULL for an asynchronous
- * call, else `count` reports (waits for the stream).  The list of problems is uploaded
- * to a device buffer owned by the first handle (grown on demand).
+ * Batched form: `count` independent steps, each on a thread-block cluster of its own
+ * whose size follows from its n (params.cluster_elems), so a problem's result is the same
+ * alone and in any batch.  Problems of one cluster size share one launch, largest first;
+ * launches of different sizes (at most five) run side by side on streams forked from and
+ * joined back into the first handle's stream.  Handles must be in SINGLE or INDEPENDENT
+ * mode and share the first handle's stream.  Per handle k: x[k], grad_f[k], A[k] as for
+ * pgdto_step; g_val[4k + j], G[4k + j] its row scalars.  Each handle's state advances as
+ * after pgdto_step.  infos: NULL for an asynchronous call, else `count` reports (waits
+ * for the stream).  The list of problems is uploaded through pinned and device buffers
+ * owned by the first handle (grown on demand).
  */
 pgdto_status pgdto_step_many(int count, pgdto_handle* const* hs, float* const* x, const float* const* grad_f,
                              const float* const* A, const double* g_val, const double* G, pgdto_info* infos);
@@ -201,10 +208,9 @@ pgdto_status pgdto_project_many(int count, pgdto_handle* const* hs, const float*
  * batching: every session keeps its design x and optimizer state on the device between
  * its steps; a submitted step's inputs are copied by DMA from the caller's buffers on a
  * copy stream and, while one cycle runs on the GPU, newly arrived steps queue for the
- * next.  A cycle launches every queued single/independent session up to 131072 variables
- * as one batched step (pgdto_step_many), then each larger or coupled-row session in a
- * launch of its own, smallest first; each launch's results are delivered as soon as that
- * launch completes.  Sessions are admitted while their device memory fits the HBM budget;
+ * next.  A cycle launches every queued single/independent session as one batched step
+ * (pgdto_step_many), then each coupled-row session in a launch of its own, smallest
+ * first; each launch's results are delivered as soon as that launch completes.  Sessions are admitted while their device memory fits the HBM budget;
  * otherwise submit returns PGDTO_ERR_BUSY and the caller retries after sessions close.
  * The paper has no serving layer; the step each request runs is Alg. 3 as above.
  */

@@ -4,6 +4,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "../../include/pgdto.h"
@@ -44,10 +47,34 @@ struct pgdto_handle {
     int64_t launches;
     int last_was_project;
     int engine;               // 1 grid, 2 cluster
-    int cl_size, cl_max;      // cluster engine shape on this device
+    int cl_size, cl_max;      // this problem's cluster size; clusters co-resident at the largest size
+    int res_grid, res_cluster;  // shared-memory residency floats per array on each engine (0 = off)
     SegArgs* items;           // device list for the batched entries (grown on demand)
+    SegArgs* items_host;      // pinned staging of that list
+    cudaEvent_t items_ev;     // the last upload of items_host (it is rewritten only after)
     int items_cap;
+    cudaStream_t aux[4];      // batched launches: one stream per further cluster size
+    cudaEvent_t fork_ev, join_ev[4];
 };
+
+static const int64_t kClusterElemsDefault = 16384;
+
+// Residency floats per array for a problem split over nb blocks (0 when a block's share
+// does not fit the shared memory).
+static int res_elems(const int64_t* seg, int m, int nb) {
+    const int need = seg_res_need_max(seg, m, nb);
+    return need <= kResMaxElems ? ((need + 3) & ~3) : 0;
+}
+
+// Blocks of a problem's cluster: ceil(n / per_cta) rounded up to a power of two, at most
+// the device's largest cluster.  A function of n alone, so a problem reduces in the same
+// order alone and in any batch.
+static int cluster_size_for(int64_t n, int64_t per_cta, int s_max) {
+    const int64_t want = (n + per_cta - 1) / per_cta;
+    int s = 1;
+    while (s < want && s * 2 <= s_max) s *= 2;
+    return s;
+}
 
 // Problems up to this many variables run on one thread-block cluster by default: their
 // steps are bound by synchronisation latency, which the cluster barriers cut, while
@@ -84,6 +111,7 @@ extern "C" pgdto_status pgdto_params_default(pgdto_params* p) {
     p->mode = PGDTO_AUTO;
     p->fault_inject = 0;
     p->engine = 0;
+    p->cluster_elems = 0;
     return PGDTO_OK;
 }
 
@@ -102,6 +130,13 @@ static void free_handle(pgdto_handle* h) {
     cudaFree(h->hg);
     cudaFree(h->hA);
     cudaFree(h->items);
+    cudaFreeHost(h->items_host);
+    if (h->items_ev) cudaEventDestroy(h->items_ev);
+    for (int g = 0; g < 4; ++g) {
+        if (h->aux[g]) cudaStreamDestroy(h->aux[g]);
+        if (h->join_ev[g]) cudaEventDestroy(h->join_ev[g]);
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     delete h;
 }
 
@@ -109,7 +144,7 @@ static bool params_ok(const pgdto_params& p) {
     return p.C > 0 && isfinite(p.C) && p.alpha_max > 0 && p.alpha_fallback > 0 && p.tol_N >= 0 && p.omega > 0 &&
            p.eps_alpha >= 0 && p.tol_lambda > 0 && p.tol_lambda < 1e-2 && p.t_warmup >= 0 &&
            p.maxiter_newton >= 1 && p.max_passes >= 1 && p.max_passes <= 100000 && p.barrier_timeout_ms >= 1 &&
-           (p.fault_inject == 0 || p.fault_inject == 1) && p.engine >= 0 && p.engine <= 2;
+           (p.fault_inject == 0 || p.fault_inject == 1) && p.engine >= 0 && p.engine <= 2 && p.cluster_elems >= 0;
 }
 
 extern "C" pgdto_status pgdto_create(pgdto_handle** out, int64_t n, int m, const int64_t* seg_offsets, float lo,
@@ -182,7 +217,11 @@ extern "C" pgdto_status pgdto_create(pgdto_handle** out, int64_t n, int m, const
     }
     h->engine = 1;
     if (mode != PGDTO_COUPLED) {
-        seg_cluster_shape(h->device, &h->cl_size, &h->cl_max);
+        int s_max = 0;
+        seg_cluster_shape(h->device, &s_max, &h->cl_max);
+        h->cl_size = cluster_size_for(n, p.cluster_elems > 0 ? p.cluster_elems : kClusterElemsDefault, s_max);
+        h->res_grid = res_elems(h->seg, m, h->blocks);
+        h->res_cluster = res_elems(h->seg, m, h->cl_size);
         if (p.engine == 2 || (p.engine == 0 && n <= kClusterMaxN)) h->engine = 2;
     } else if (p.engine == 2) {
         delete h;
@@ -381,10 +420,13 @@ static pgdto_status launch(pgdto_handle* h, bool proj, float* x, const float* g,
     } else {
         SegArgs a;
         fill_seg_args(h, proj, x, g, A, bconst, z_in, x_out, force_fallback, a);
-        if (h->engine == 2 && !h->p.fault_inject)
-            e = launch_seg_clusters(a, nullptr, 1, 1, h->cl_size, seg_args_aligned(a), h->stream);
-        else
+        if (h->engine == 2 && !h->p.fault_inject) {
+            a.sm_elems = h->res_cluster;
+            e = launch_seg_clusters(a, nullptr, 1, 1, h->cl_size, seg_args_aligned(a), h->stream, a.sm_elems);
+        } else {
+            a.sm_elems = h->res_grid;
             e = launch_seg(a, h->blocks, h->stream);
+        }
     }
     if (e != cudaSuccess) return cuda_fail(e);
     h->launches += 1;
@@ -465,31 +507,96 @@ extern "C" int pgdto_trace(pgdto_handle* h, double* us_out, int max_marks) {
 // ------------------------------------------------------------------ batched entries
 
 static pgdto_status ensure_items(pgdto_handle* h, int count) {
+    if (!h->items_ev) {
+        cudaError_t e = cudaEventCreateWithFlags(&h->items_ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
     if (h->items_cap >= count) return PGDTO_OK;
+    cudaEventSynchronize(h->items_ev);  // the old buffers may still be read by a queued copy
+    cudaStreamSynchronize(h->stream);
     cudaFree(h->items);
+    cudaFreeHost(h->items_host);
     h->items = nullptr;
+    h->items_host = nullptr;
     h->items_cap = 0;
     int cap = count < 64 ? 64 : count;
     cudaError_t e = cudaMalloc(&h->items, sizeof(SegArgs) * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->items_host, sizeof(SegArgs) * (size_t)cap);
     if (e != cudaSuccess) return cuda_fail(e);
     h->items_cap = cap;
     return PGDTO_OK;
 }
 
+static pgdto_status ensure_fork(pgdto_handle* h, int groups) {
+    if (!h->fork_ev && cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+        return PGDTO_ERR_CUDA;
+    for (int g = 0; g + 1 < groups; ++g) {
+        if (!h->aux[g] && cudaStreamCreateWithFlags(&h->aux[g], cudaStreamNonBlocking) != cudaSuccess)
+            return PGDTO_ERR_CUDA;
+        if (!h->join_ev[g] && cudaEventCreateWithFlags(&h->join_ev[g], cudaEventDisableTiming) != cudaSuccess)
+            return PGDTO_ERR_CUDA;
+    }
+    return PGDTO_OK;
+}
+
+// One cluster per problem.  Problems are grouped by cluster size (one launch per size, the
+// launches of different sizes run side by side on forked streams and join the handle's
+// stream), and each group lists its problems largest first: the block scheduler starts
+// clusters in order, so the longest do not trail at the end.
 static pgdto_status launch_many(int count, pgdto_handle* const* hs, SegArgs* args, bool vec) {
     pgdto_handle* h0 = hs[0];
-    if (count > 1) {
-        pgdto_status s = ensure_items(h0, count);
+    for (int k = 0; k < count; ++k) args[k].sm_elems = hs[k]->res_cluster;
+    if (count == 1) {
+        cudaError_t e = launch_seg_clusters(args[0], nullptr, 1, 1, h0->cl_size, vec, h0->stream, args[0].sm_elems);
+        if (e != cudaSuccess) return cuda_fail(e);
+        h0->launches += 1;
+        return PGDTO_OK;
+    }
+    pgdto_status s = ensure_items(h0, count);
+    if (s != PGDTO_OK) return s;
+    std::vector<int> order(count);
+    for (int k = 0; k < count; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (hs[a]->cl_size != hs[b]->cl_size) return hs[a]->cl_size > hs[b]->cl_size;
+        return hs[a]->n > hs[b]->n;
+    });
+    cudaEventSynchronize(h0->items_ev);
+    for (int k = 0; k < count; ++k) h0->items_host[k] = args[order[k]];
+    cudaError_t e = cudaMemcpyAsync(h0->items, h0->items_host, sizeof(SegArgs) * (size_t)count,
+                                    cudaMemcpyHostToDevice, h0->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h0->items_ev, h0->stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int starts[6], sizes[6], smem[6], ng = 0;
+    for (int k = 0; k < count; ++k) {
+        if (k == 0 || hs[order[k]]->cl_size != hs[order[k - 1]]->cl_size) {
+            starts[ng] = k;
+            sizes[ng] = hs[order[k]]->cl_size;
+            smem[ng] = 0;
+            ++ng;
+        }
+        smem[ng - 1] = hs[order[k]]->res_cluster > smem[ng - 1] ? hs[order[k]]->res_cluster : smem[ng - 1];
+    }
+    starts[ng] = count;
+    if (ng > 1) {
+        s = ensure_fork(h0, ng);
         if (s != PGDTO_OK) return s;
-        // pageable source: the copy is staged before the call returns, args may be reused
-        cudaError_t e = cudaMemcpyAsync(h0->items, args, sizeof(SegArgs) * (size_t)count, cudaMemcpyHostToDevice,
-                                        h0->stream);
+        e = cudaEventRecord(h0->fork_ev, h0->stream);
         if (e != cudaSuccess) return cuda_fail(e);
     }
-    int ncl = count < h0->cl_max ? count : h0->cl_max;
-    cudaError_t e = launch_seg_clusters(args[0], h0->items, count, ncl, h0->cl_size, vec, h0->stream);
-    if (e != cudaSuccess) return cuda_fail(e);
-    for (int k = 0; k < count; ++k) hs[k]->launches += (k == 0);
+    for (int g = 0; g < ng; ++g) {
+        cudaStream_t st = g == 0 ? h0->stream : h0->aux[g - 1];
+        if (g > 0 && (e = cudaStreamWaitEvent(st, h0->fork_ev, 0)) != cudaSuccess) return cuda_fail(e);
+        const int cnt = starts[g + 1] - starts[g];
+        e = launch_seg_clusters(h0->items_host[starts[g]], h0->items + starts[g], cnt, cnt, sizes[g], vec, st,
+                                smem[g]);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (g > 0) {
+            if ((e = cudaEventRecord(h0->join_ev[g - 1], st)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(h0->stream, h0->join_ev[g - 1], 0)) != cudaSuccess)
+                return cuda_fail(e);
+        }
+    }
+    h0->launches += ng;
     return PGDTO_OK;
 }
 

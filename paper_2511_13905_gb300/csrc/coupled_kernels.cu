@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
 
     if (!a.proj) {
         // ------------------------------------------------------------ phase A
-        Acc<6> acc;
+        AccSplit<6, 0> acc;
         acc.init();
         float gmax = 0.0f;
         if (a.t > 0) {
@@ -641,7 +641,7 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
         const float ch = a.proj ? 0.0f : bc.c_hi, cl = a.proj ? 0.0f : bc.c_lo;
         const float bh = a.proj ? 0.0f : bc.beta_hi, bl = a.proj ? 0.0f : bc.beta_lo;
         const bool first = a.t == 0;
-        Acc<4 * M> acc;
+        AccSplit<4 * M, 0> acc;
         acc.init();
         float lsat[M];
 #pragma unroll
@@ -777,7 +777,7 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
                 float p[K];
 #pragma unroll
                 for (int k = 0; k < K; ++k) p[k] = bc.pts[j][k];
-                Acc<2 * K> acc;
+                AccSplit<K, K> acc;
                 acc.init();
                 const float* Aj = a.A + (int64_t)j * n;
                 auto e = [&](float z, float zl, float av) {
@@ -830,7 +830,7 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
                 clh[c] = bc.lam_hi[crow[c]];
                 cll[c] = bc.lam_lo[crow[c]];
             }
-            Acc<M * M> acc;
+            AccSplit<M * M, 0> acc;
             acc.init();
             auto e = [&](float z, float zl, const float (&av)[M]) {
 #pragma unroll
@@ -890,7 +890,7 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
                 ll[j] = bc.it_lo[j];
             }
             constexpr int NJ = M * (M + 1) / 2;
-            Acc<2 * M + NJ> acc;
+            AccSplit<M, M + NJ> acc;
             acc.init();
             auto e = [&](float z, float zl, const float (&av)[M]) {
                 float w = z, wl = zl;
@@ -963,7 +963,7 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
             }
 #pragma unroll
             for (int k = 0; k < K; ++k) p[k] = bc.pts[0][k];
-            Acc<2 * K> acc;
+            AccSplit<K, K> acc;
             acc.init();
             auto e = [&](float z, float zl, const float (&av)[M]) {
                 float w = z, wl = zl, u = 0.0f;
@@ -1027,7 +1027,7 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
             lh[j] = bc.lam_hi[j];
             ll[j] = bc.lam_lo[j];
         }
-        Acc<M + 2> acc;
+        AccSplit<M + 2, 0> acc;
         acc.init();
         // x = clip(z - sum_j lam_j a_j): hi parts with TwoSum, lo parts and product errors
         // gathered separately, so x is exact to FP32 rounding of the result

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "kernels.h"
+
 namespace pgdto {
 
 constexpr int kThreads = 512;
@@ -325,14 +327,7 @@ __device__ __forceinline__ void load_cg(T& dst, const T* src) {
 
 // Contiguous chunk [cb, ce) of [s, e) owned by block `blk` of `nb`, multiple of 4 long.
 __device__ __forceinline__ void block_chunk(int64_t s, int64_t e, int blk, int nb, int64_t& cb, int64_t& ce) {
-    int64_t len = e - s;
-    int64_t per = (len + nb - 1) / nb;
-    per = (per + 3) & ~int64_t(3);
-    if (per < 4) per = 4;
-    cb = s + per * blk;
-    ce = cb + per;
-    if (cb > e) cb = e;
-    if (ce > e) ce = e;
+    seg_chunk(s, e, blk, nb, cb, ce);
 }
 
 }  // namespace pgdto

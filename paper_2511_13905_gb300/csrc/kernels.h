@@ -46,7 +46,53 @@ struct SegArgs {
     long long timeout_cycles;
     SegWork* ws;          // grid engine workspace
     DeviceInfo* info_out; // cluster engine: where this problem's report goes
+    int sm_elems;         // shared-memory residency: floats per array (z_hi, z_lo, a); 0 = off
 };
+
+// Shared-memory residency of a CTA's share of a problem.  The CTA's chunk of row j is
+// [cb_j, ce_j) (block_chunk); it is kept from base_j = cb_j rounded down to a multiple of
+// four, at a float4-aligned offset, rows one after another.  seg_res_need is the number
+// of floats per array the CTA needs; the host sizes the launch's dynamic shared memory
+// with the same function the device uses to decide.
+__host__ __device__ inline void seg_chunk(int64_t s, int64_t e, int blk, int nb, int64_t& cb, int64_t& ce) {
+    int64_t len = e - s;
+    int64_t per = (len + nb - 1) / nb;
+    per = (per + 3) & ~int64_t(3);
+    if (per < 4) per = 4;
+    cb = s + per * blk;
+    ce = cb + per;
+    if (cb > e) cb = e;
+    if (ce > e) ce = e;
+}
+
+__host__ __device__ inline int seg_res_span(int64_t cb, int64_t ce) {
+    const int64_t b4 = cb & ~int64_t(3);
+    return (int)(((ce - b4) + 3) & ~int64_t(3));
+}
+
+__host__ __device__ inline int seg_res_need(const int64_t* seg, int nrows, int blk, int nb) {
+    int tot = 0;
+    for (int j = 0; j < nrows; ++j) {
+        int64_t cb, ce;
+        seg_chunk(seg[j], seg[j + 1], blk, nb, cb, ce);
+        tot += seg_res_span(cb, ce);
+    }
+    return tot;
+}
+
+// Largest need over the CTAs of a problem split over nb blocks.
+inline int seg_res_need_max(const int64_t* seg, int nrows, int nb) {
+    int mx = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int v = seg_res_need(seg, nrows, b, nb);
+        mx = v > mx ? v : mx;
+    }
+    return mx;
+}
+
+// Residency capacity per array (floats): three arrays fit next to the static scratch in
+// the 227 KB a CTA may hold.
+constexpr int kResMaxElems = 16384 + 32;
 
 // Arguments of the coupled-rows (Alg. 2) step / projection kernel.
 struct CoupledArgs {
@@ -83,12 +129,14 @@ DeviceInfo* coupled_work_info(CoupledWork* ws);
 size_t seg_work_ctrl_bytes();       // leading GridCtrl block to clear after an error
 size_t coupled_work_ctrl_bytes();
 
-// Launch helpers: cooperative launch on `stream` with `blocks` CTAs of kThreads threads.
+// Launch helpers: cooperative launch on `stream` with `blocks` CTAs of kThreads threads
+// (dynamic shared memory for a.sm_elems floats per residency array).
 cudaError_t launch_seg(const SegArgs& a, int blocks, cudaStream_t stream);
 // Cluster engine: `items` (device array of `nitems` problems) on `nclusters` clusters of
-// `cluster` CTAs each.  vec: every pointer of every item is 16-byte aligned.
+// `cluster` CTAs each.  vec: every pointer of every item is 16-byte aligned.  sm_elems:
+// residency floats per array, at least every item's sm_elems (a multiple of 4).
 cudaError_t launch_seg_clusters(const SegArgs& first, const SegArgs* items, int nitems, int nclusters, int cluster,
-                                bool vec, cudaStream_t stream);
+                                bool vec, cudaStream_t stream, int sm_elems);
 bool seg_args_aligned(const SegArgs& a);
 // Largest cluster size (<= 16) the cluster engine can use, and how many such clusters fit.
 int seg_cluster_shape(int device, int* cluster, int* max_clusters);

@@ -256,14 +256,22 @@ struct ClusterSyncSeg {
 };
 
 // One PGD-TO step (or projection) on the problem `a`, executed by the CTAs of `sy`.
+// Dynamic shared memory of the residency (three arrays of SegArgs::sm_elems floats).
+extern __shared__ float4 seg_dyn_sm[];
+
+template <bool B>
+struct BoolC {
+    static constexpr bool value = B;
+};
+
 template <bool VEC, class Sync>
-__device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, SegBcast& bc) {
+__device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, SegBcast& bc, float* sm) {
     const int nb = sy.size(), blk = sy.rank();
     const float lo = a.lo, hi = a.hi;
 
     if (!a.proj) {
         // ------------------------------------------------------------ phase A
-        Acc<6> acc;
+        AccSplit<6, 0> acc;
         acc.init();
         float gmax = 0.0f;
         int64_t cb, ce;
@@ -328,15 +336,26 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
     }
 
     // ---------------------------------------------------------------- phase B
+    // Residency: when this CTA's share fits the dynamic shared memory, phase B keeps the
+    // trial point (z_hi, z_lo) and the coefficients there and phases C and D read them
+    // back from it instead of global memory (z is then not written to global memory).
+    const bool res = sm != nullptr && a.sm_elems > 0 && seg_res_need(a.seg, a.nrows, blk, nb) <= a.sm_elems;
+    float* const smz = sm;
+    float* const sml = sm + a.sm_elems;
+    float* const sma = sm + 2 * a.sm_elems;
     {
         const float ch = a.proj ? 0.0f : bc.c_hi, bh = a.proj ? 0.0f : bc.beta_hi;
         const bool first = a.t == 0;
+        int roff = 0;
         for (int j = 0; j < a.nrows; ++j) {
-            Acc<4> acc;
+            AccSplit<4, 0> acc;
             acc.init();
             float lsat = 0.0f;
             int64_t cb, ce;
             block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
+            const int64_t rb = cb & ~int64_t(3);
+            const int off = roff;
+            roff += seg_res_span(cb, ce);
             auto e = [&](float z, float av, float x) {
                 acc.f[0] = fmaf(av, x, acc.f[0]);
                 const float xc = clampf(z, lo, hi);
@@ -357,10 +376,20 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                         e(z.y, av.y, 0.0f);
                         e(z.z, av.z, 0.0f);
                         e(z.w, av.w, 0.0f);
+                        if (res) {
+                            const int q = (off >> 2) + (int)(v - (rb >> 2));
+                            reinterpret_cast<float4*>(smz)[q] = z;
+                            reinterpret_cast<float4*>(sma)[q] = av;
+                        }
                         acc.tick();
                     },
                     [&](int64_t i) {
-                        e(a.z_in[i], a.A[i], 0.0f);
+                        const float z = a.z_in[i], av = a.A[i];
+                        e(z, av, 0.0f);
+                        if (res) {
+                            smz[off + (int)(i - rb)] = z;
+                            sma[off + (int)(i - rb)] = av;
+                        }
                         acc.tick();
                     });
             } else {
@@ -401,19 +430,32 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                         st(x.z, g.z, dp.z, av.z, d.z, zh.z, zl.z);
                         st(x.w, g.w, dp.w, av.w, d.w, zh.w, zl.w);
                         __stcs(reinterpret_cast<float4*>(a.d_new) + v, d);
-                        reinterpret_cast<float4*>(a.z)[v] = zh;
-                        reinterpret_cast<float4*>(a.zlo)[v] = zl;
+                        if (res) {
+                            const int q = (off >> 2) + (int)(v - (rb >> 2));
+                            reinterpret_cast<float4*>(smz)[q] = zh;
+                            reinterpret_cast<float4*>(sml)[q] = zl;
+                            reinterpret_cast<float4*>(sma)[q] = av;
+                        } else {
+                            reinterpret_cast<float4*>(a.z)[v] = zh;
+                            reinterpret_cast<float4*>(a.zlo)[v] = zl;
+                        }
                         __stcs(reinterpret_cast<float4*>(a.x_prev) + v, x);
                         __stcs(reinterpret_cast<float4*>(a.g_prev) + v, g);
                         acc.tick();
                     },
                     [&](int64_t i) {
-                        const float x = a.x[i], g = a.g[i];
+                        const float x = a.x[i], g = a.g[i], av = a.A[i];
                         float d, zh, zl;
-                        st(x, g, first ? 0.0f : a.d_prev[i], a.A[i], d, zh, zl);
+                        st(x, g, first ? 0.0f : a.d_prev[i], av, d, zh, zl);
                         a.d_new[i] = d;
-                        a.z[i] = zh;
-                        a.zlo[i] = zl;
+                        if (res) {
+                            smz[off + (int)(i - rb)] = zh;
+                            sml[off + (int)(i - rb)] = zl;
+                            sma[off + (int)(i - rb)] = av;
+                        } else {
+                            a.z[i] = zh;
+                            a.zlo[i] = zl;
+                        }
                         a.x_prev[i] = x;
                         a.g_prev[i] = g;
                         acc.tick();
@@ -436,15 +478,19 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
     const float* zsrc = a.proj ? a.z_in : a.z;
     const bool has_lo = !a.proj;
     while (bc.any_active) {
+        int roff = 0;
         for (int j = 0; j < a.nrows; ++j) {
+            int64_t cb, ce;
+            block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
+            const int64_t rb = cb & ~int64_t(3);
+            const int off = roff;
+            roff += seg_res_span(cb, ce);
             if (!bc.active[j]) continue;
             float p[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) p[k] = bc.pts[j][k];
-            Acc<2 * K> acc;
+            AccSplit<K, K> acc;
             acc.init();
-            int64_t cb, ce;
-            block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
             auto e = [&](float z, float zl, float av) {
                 const float aa = av * av;
 #pragma unroll
@@ -454,11 +500,25 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                     acc.f[K + k] += (w >= lo && w <= hi) ? aa : 0.0f;
                 }
             };
-            if (has_lo) {
+            // one element loop per source (shared or global memory) and per trial point form
+            // (with or without z_lo), fixed at compile time
+            auto run = [&](auto rc, auto lc) {
+                constexpr bool R = decltype(rc)::value;
+                constexpr bool HL = decltype(lc)::value;
                 for_chunk<VEC>(
                     cb, ce,
                     [&](int64_t v) {
-                        float4 z = LD4L2(zsrc, v), zl = LD4L2(a.zlo, v), av = LD4L2(a.A, v);
+                        float4 z, zl = make_float4(0.f, 0.f, 0.f, 0.f), av;
+                        if constexpr (R) {
+                            const int q = (off >> 2) + (int)(v - (rb >> 2));
+                            z = reinterpret_cast<const float4*>(smz)[q];
+                            if constexpr (HL) zl = reinterpret_cast<const float4*>(sml)[q];
+                            av = reinterpret_cast<const float4*>(sma)[q];
+                        } else {
+                            z = LD4L2(zsrc, v);
+                            if constexpr (HL) zl = LD4L2(a.zlo, v);
+                            av = LD4L2(a.A, v);
+                        }
                         e(z.x, zl.x, av.x);
                         e(z.y, zl.y, av.y);
                         e(z.z, zl.z, av.z);
@@ -466,24 +526,21 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                         acc.tick();
                     },
                     [&](int64_t i) {
-                        e(zsrc[i], a.zlo[i], a.A[i]);
+                        if constexpr (R) {
+                            const int q = off + (int)(i - rb);
+                            e(smz[q], HL ? sml[q] : 0.0f, sma[q]);
+                        } else {
+                            e(zsrc[i], HL ? a.zlo[i] : 0.0f, a.A[i]);
+                        }
                         acc.tick();
                     });
+            };
+            if (res) {
+                if (has_lo) run(BoolC<true>{}, BoolC<true>{});
+                else run(BoolC<true>{}, BoolC<false>{});
             } else {
-                for_chunk<VEC>(
-                    cb, ce,
-                    [&](int64_t v) {
-                        float4 z = LD4L2(zsrc, v), av = LD4L2(a.A, v);
-                        e(z.x, 0.0f, av.x);
-                        e(z.y, 0.0f, av.y);
-                        e(z.z, 0.0f, av.z);
-                        e(z.w, 0.0f, av.w);
-                        acc.tick();
-                    },
-                    [&](int64_t i) {
-                        e(zsrc[i], 0.0f, a.A[i]);
-                        acc.tick();
-                    });
+                if (has_lo) run(BoolC<false>{}, BoolC<true>{});
+                else run(BoolC<false>{}, BoolC<false>{});
             }
             acc.fold();
             block_reduce<2 * K, 0>(acc.d, nullptr, sc, 2 * K * j, 0);
@@ -497,12 +554,16 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
 
     // ---------------------------------------------------------------- phase D
     {
-        Acc<kMaxRows + 2> acc;
+        AccSplit<kMaxRows + 2, 0> acc;
         acc.init();
+        int roff = 0;
         for (int j = 0; j < a.nrows; ++j) {
             const float lh = bc.lam_hi[j], ll = bc.lam_lo[j];
             int64_t cb, ce;
             block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
+            const int64_t rb = cb & ~int64_t(3);
+            const int off = roff;
+            roff += seg_res_span(cb, ce);
             float axj = 0.0f;
             DF axd = df_zero();
             int cnt = 0;
@@ -520,7 +581,15 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 for_chunk<VEC>(
                     cb, ce,
                     [&](int64_t v) {
-                        float4 z = LD4L2(a.z_in, v), av = LD4L2(a.A, v);
+                        float4 z, av;
+                        if (res) {
+                            const int q = (off >> 2) + (int)(v - (rb >> 2));
+                            z = reinterpret_cast<const float4*>(smz)[q];
+                            av = reinterpret_cast<const float4*>(sma)[q];
+                        } else {
+                            z = LD4L2(a.z_in, v);
+                            av = LD4L2(a.A, v);
+                        }
                         float4 o;
                         o.x = e(z.x, av.x);
                         o.y = e(z.y, av.y);
@@ -533,7 +602,10 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                             cnt = 0;
                         }
                     },
-                    [&](int64_t i) { a.x_out[i] = e(a.z_in[i], a.A[i]); });
+                    [&](int64_t i) {
+                        const int q = off + (int)(i - rb);
+                        a.x_out[i] = res ? e(smz[q], sma[q]) : e(a.z_in[i], a.A[i]);
+                    });
             } else {
                 // x_{t+1} = clip(z - lam a) with z = z_hi + z_lo and lam = lam_hi + lam_lo
                 auto e = [&](float x, float zh, float zl, float av) -> float {
@@ -549,7 +621,17 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 for_chunk<VEC>(
                     cb, ce,
                     [&](int64_t v) {
-                        float4 x = LD4L2(a.x, v), zh = LD4(a.z, v), zl = LD4(a.zlo, v), av = LD4(a.A, v);
+                        float4 x = LD4L2(a.x, v), zh, zl, av;
+                        if (res) {
+                            const int q = (off >> 2) + (int)(v - (rb >> 2));
+                            zh = reinterpret_cast<const float4*>(smz)[q];
+                            zl = reinterpret_cast<const float4*>(sml)[q];
+                            av = reinterpret_cast<const float4*>(sma)[q];
+                        } else {
+                            zh = LD4(a.z, v);
+                            zl = LD4(a.zlo, v);
+                            av = LD4(a.A, v);
+                        }
                         float4 o;
                         o.x = e(x.x, zh.x, zl.x, av.x);
                         o.y = e(x.y, zh.y, zl.y, av.y);
@@ -563,7 +645,10 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                             acc.fold();
                         }
                     },
-                    [&](int64_t i) { a.x[i] = e(a.x[i], a.z[i], a.zlo[i], a.A[i]); });
+                    [&](int64_t i) {
+                        const int q = off + (int)(i - rb);
+                        a.x[i] = res ? e(a.x[i], smz[q], sml[q], sma[q]) : e(a.x[i], a.z[i], a.zlo[i], a.A[i]);
+                    });
             }
             axd = df_add_f(axd, axj);
             acc.d[j] = df_add(acc.d[j], axd);
@@ -595,7 +680,7 @@ __global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
     // test hook: block 0 never arrives, so every other block's first wait runs out its budget
     if (a.fault_inject == 1 && blockIdx.x == 0) return;
     GridSyncSeg sy{ws, a.timeout_cycles};
-    seg_body<VEC>(a, sy, sc, bc);
+    seg_body<VEC>(a, sy, sc, bc, a.sm_elems > 0 ? reinterpret_cast<float*>(seg_dyn_sm) : nullptr);
 }
 
 // Cluster engine over a list of problems: cluster c takes problems c, c + nclusters, ...
@@ -619,7 +704,7 @@ __global__ void __launch_bounds__(kThreads, 1) seg_cluster_kernel(SegArgs first,
             vc->ntrace = 0;
         }
         ClusterSyncSeg sy{&st, tr};
-        seg_body<VEC>(a, sy, sc, bc);
+        seg_body<VEC>(a, sy, sc, bc, a.sm_elems > 0 ? reinterpret_cast<float*>(seg_dyn_sm) : nullptr);
         if (cl.block_rank() == 0 && threadIdx.x == 0 && a.info_out) {
             const unsigned* src = reinterpret_cast<const unsigned*>(&st.info);
             unsigned* dst = reinterpret_cast<unsigned*>(a.info_out);
@@ -629,10 +714,24 @@ __global__ void __launch_bounds__(kThreads, 1) seg_cluster_kernel(SegArgs first,
     }
 }
 
+static size_t res_bytes(int sm_elems) { return (size_t)3 * (size_t)sm_elems * sizeof(float); }
+
+// Both kernels may take the largest residency; set once per kernel.
+template <class K>
+static void allow_res_smem(K kernel) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_bytes(kResMaxElems));
+}
+
 template <bool VEC>
 static cudaError_t launch_seg_t(const SegArgs& a, int blocks, cudaStream_t stream) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        allow_res_smem(seg_kernel<VEC>);
+        attr_set = true;
+    }
     void* args[] = {const_cast<SegArgs*>(&a)};
-    return cudaLaunchCooperativeKernel((void*)seg_kernel<VEC>, dim3(blocks), dim3(kThreads), args, 0, stream);
+    return cudaLaunchCooperativeKernel((void*)seg_kernel<VEC>, dim3(blocks), dim3(kThreads), args,
+                                       res_bytes(a.sm_elems), stream);
 }
 
 cudaError_t launch_seg(const SegArgs& a, int blocks, cudaStream_t stream) {
@@ -645,16 +744,17 @@ cudaError_t launch_seg(const SegArgs& a, int blocks, cudaStream_t stream) {
 
 template <bool VEC>
 static cudaError_t launch_clusters_t(const SegArgs& first, const SegArgs* items, int nitems, int ncl, int S,
-                                     cudaStream_t stream) {
+                                     int sm_elems, cudaStream_t stream) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(seg_cluster_kernel<VEC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        allow_res_smem(seg_cluster_kernel<VEC>);
         attr_set = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ncl * S);
     cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = res_bytes(sm_elems);
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -667,10 +767,11 @@ static cudaError_t launch_clusters_t(const SegArgs& first, const SegArgs* items,
 }
 
 cudaError_t launch_seg_clusters(const SegArgs& first, const SegArgs* items, int nitems, int nclusters, int cluster,
-                                bool vec, cudaStream_t stream) {
+                                bool vec, cudaStream_t stream, int sm_elems) {
     if (nitems < 1 || nclusters < 1 || cluster < 1 || cluster > 16) return cudaErrorInvalidValue;
-    return vec ? launch_clusters_t<true>(first, items, nitems, nclusters, cluster, stream)
-               : launch_clusters_t<false>(first, items, nitems, nclusters, cluster, stream);
+    if (sm_elems < 0 || sm_elems > kResMaxElems || (sm_elems & 3)) return cudaErrorInvalidValue;
+    return vec ? launch_clusters_t<true>(first, items, nitems, nclusters, cluster, sm_elems, stream)
+               : launch_clusters_t<false>(first, items, nitems, nclusters, cluster, sm_elems, stream);
 }
 
 bool seg_args_aligned(const SegArgs& a) {
@@ -715,9 +816,12 @@ int seg_cluster_shape(int device, int* cluster, int* max_clusters) {
 int max_blocks_seg(int device) {
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, seg_kernel<true>, kThreads, 0);
+    // co-resident blocks with the largest residency (a cooperative launch needs them all)
+    allow_res_smem(seg_kernel<true>);
+    allow_res_smem(seg_kernel<false>);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, seg_kernel<true>, kThreads, res_bytes(kResMaxElems));
     int per2 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, seg_kernel<false>, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, seg_kernel<false>, kThreads, res_bytes(kResMaxElems));
     per = per < per2 ? per : per2;
     if (per < 1) per = 1;
     int nb = sms * per;

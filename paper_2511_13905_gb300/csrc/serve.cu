@@ -29,7 +29,6 @@ struct Session {
     int m = 0;
     int64_t a_len = 0;
     bool coupled = false;
-    bool own_launch = false;  // coupled rows, or too large for the batched cluster launch
     pgdto_handle* h = nullptr;
     float* x = nullptr;       // device design (persists across steps)
     float* g = nullptr;       // device staging of grad f
@@ -56,10 +55,6 @@ struct Done {
 };
 
 }  // namespace
-
-// Single/independent sessions up to this size share one batched cluster launch; larger
-// ones (and coupled rows) get a grid launch of their own, shortest first.
-static const int64_t kServeBatchMaxN = int64_t(1) << 17;
 
 struct pgdto_server {
     uint64_t budget = 0, in_use = 0;
@@ -135,13 +130,19 @@ void finish_unit(pgdto_server* srv, cudaEvent_t ev, std::vector<Request>& unit) 
     }
 }
 
-// One cycle: the batched group (one cluster launch for every small single/independent
-// session), then each large or coupled session in its own launch, shortest first; each
-// unit's results are reported as soon as its own event completes.
+// One cycle: every single/independent session in one batched step (pgdto_step_many: one
+// thread-block cluster per session, sized by its n, all side by side), then each coupled
+// session in a launch of its own, smallest first; each unit's results are reported as
+// soon as its own event completes.  A cycle with one single/independent session runs it
+// through pgdto_step, on the engine its handle chose (the whole GPU for a large n).
 void run_cycle(pgdto_server* srv, std::vector<Request>& batch) {
     std::vector<Request> group;
     std::vector<Request> own;
-    for (Request& r : batch) (r.s->own_launch ? own : group).push_back(r);
+    for (Request& r : batch) (r.s->coupled ? own : group).push_back(r);
+    if (group.size() == 1) {
+        own.push_back(group[0]);
+        group.clear();
+    }
     std::sort(own.begin(), own.end(), [](const Request& a, const Request& b) { return a.s->n < b.s->n; });
     while (srv->unit_done.size() < own.size() + 1) {
         cudaEvent_t e;
@@ -249,7 +250,6 @@ extern "C" pgdto_status pgdto_submit(pgdto_server* srv, const pgdto_request* req
         s->m = req->m;
         s->a_len = a_len;
         s->coupled = coupled;
-        s->own_launch = coupled || req->n > kServeBatchMaxN;
         s->bytes = bytes;
         pgdto_params p = srv->params;
         p.mode = PGDTO_AUTO;

@@ -349,6 +349,50 @@ struct Acc {
     }
 };
 
+// Accumulators whose first NP entries (residual sums, whose rounding moves the dual root)
+// fold into double-float after every float4 group, and whose other NQ entries (slopes and
+// magnitudes, which only scale a Newton correction) after every kFoldSlow groups.
+constexpr int kFoldSlow = 4;
+
+template <int NP, int NQ>
+struct AccSplit {
+    static constexpr int N = NP + NQ;
+    float f[N];
+    DF d[N];
+    int cnt;
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            f[i] = 0.0f;
+            d[i] = df_zero();
+        }
+        cnt = 0;
+    }
+    __device__ __forceinline__ void fold() {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            d[i] = df_add_f(d[i], f[i]);
+            f[i] = 0.0f;
+        }
+        cnt = 0;
+    }
+    __device__ __forceinline__ void tick() {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            d[i] = df_add_f(d[i], f[i]);
+            f[i] = 0.0f;
+        }
+        if (++cnt == kFoldSlow) {
+#pragma unroll
+            for (int i = NP; i < N; ++i) {
+                d[i] = df_add_f(d[i], f[i]);
+                f[i] = 0.0f;
+            }
+            cnt = 0;
+        }
+    }
+};
+
 // Iterate the block's share [cb, ce): f4(v) for aligned float4 groups v (elements 4v..4v+3),
 // f1(i) for the unaligned head and tail, then tick() per group.
 template <bool VEC, class F4, class F1>

@@ -185,3 +185,52 @@ def test_step_many_rejects_bad_lists(dev):
     assert st == binding.PGDTO_ERR_ARG  # coupled rows are not served by the cluster engine
     h.close()
     hc.close()
+
+
+@pytest.mark.parametrize("S", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("name,make", CFGS[:1] + CFGS[3:], ids=["wl1", "wl3_ragged"])
+def test_cluster_sizes(dev, S, name, make):
+    """The cluster engine at every cluster size (params.cluster_elems sets it from n)."""
+    import torch
+    from paper_2511_13905_gb300 import binding
+    cfg = make()
+    n = cfg["n"]
+    h = binding.Handle(n, cfg["m"], seg=cfg.get("seg"), engine=CLUSTER, cluster_elems=-(-n // S))
+    h.set_state(T(cfg["x_prev"], dev), T(cfg["g_prev"], dev), T(cfg["d_prev"], dev), cfg["t"])
+    x = T(cfg["x"], dev)
+    st, info = h.step(x, T(cfg["g"], dev), T(cfg["A"], dev), cfg["gval"], cfg["G"])
+    torch.cuda.synchronize()
+    h.close()
+    assert st == 0
+    ref = oracle_for(cfg)
+    check(errors(cfg, ref, x.cpu().numpy().astype(np.float64), np.array(list(info.lambda_)[:cfg["m"]])),
+          "%s S=%d" % (name, S))
+
+
+def test_step_many_every_cluster_size(dev):
+    """One batch whose problems need clusters of 1, 2, 4, 8 and 16 blocks (five launches on
+    forked streams): each result equals the same problem run alone, and the oracle's."""
+    import torch
+    from paper_2511_13905_gb300 import binding
+    cfgs = [inputs.config1(dims=d, seed_offset=k) for k, d in
+            enumerate([(50, 40), (250, 120), (300, 200), (400, 300), (512, 500), (61, 29), (128, 128)])]
+    hs, xs = [], []
+    for c in cfgs:
+        h = binding.Handle(c["n"], 1)
+        h.set_state(T(c["x_prev"], dev), T(c["g_prev"], dev), T(c["d_prev"], dev), c["t"])
+        hs.append(h)
+        xs.append(T(c["x"], dev))
+    st, infos = binding.step_many(hs, xs, [T(c["g"], dev) for c in cfgs], [T(c["A"], dev) for c in cfgs],
+                                  [c["gval"] for c in cfgs], [c["G"] for c in cfgs])
+    torch.cuda.synchronize()
+    assert st == 0
+    launches = sum(h.kernel_launches() for h in hs)
+    assert launches == 5, launches
+    for c, h, x, info in zip(cfgs, hs, xs, infos):
+        st1, info1, x1 = step_one(dev, c, CLUSTER)
+        assert st1 == 0
+        xm = x.cpu().numpy().astype(np.float64)
+        assert np.array_equal(xm, x1), c["name"]
+        ref = oracle_for(c)
+        check(errors(c, ref, xm, np.array(list(info.lambda_)[:1])), c["name"] + " in batch")
+        h.close()
