@@ -36,7 +36,8 @@ WORKLOADS = {
     4: "volume_com_3d_256x128x128 (n=4194304, m=4 coupled)",
 }
 KERNEL_SOURCES = ["paper_2511_13905_gb300/csrc/seg_kernels.cu", "paper_2511_13905_gb300/csrc/dev_common.cuh",
-                  "paper_2511_13905_gb300/csrc/coupled_kernels.cu"]
+                  "paper_2511_13905_gb300/csrc/coupled_kernels.cu", "paper_2511_13905_gb300/csrc/step_common.cuh",
+                  "paper_2511_13905_gb300/csrc/kernels.h"]
 
 
 def kernel_hash():
