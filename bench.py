@@ -360,6 +360,9 @@ def run_batched(args, local_rank=0):
             l0 = sum(h.kernel_launches() for h in hs)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            # a bounded spin (about 2 ms) keeps the device busy while the host marshals the
+            # B problems, so the events bracket device work only
+            torch.cuda._sleep(4_000_000)
             e0.record(stream)
             fn()
             e1.record(stream)
@@ -387,11 +390,13 @@ def run_batched(args, local_rank=0):
                         "passes_per_instance": passes_b / B,
                         "roofline": {"bound": "hbm", "achieved": bytes_b / (t_b / 1e3) / 1e9, "peak": peak,
                                      "unit": "GB/s", "frac": bytes_b / (t_b / 1e3) / 1e9 / peak,
+                                     "traffic": measured_traffic("batched") if B == 256 else None,
                                      "algorithmic_bytes_per_launch": bytes_b}},
             "plain": {"ms": t_p, "steps_per_s": B / (t_p / 1e3), "launches": launches_p,
                       "passes_per_instance": passes_p / B},
             "max_abs_diff_x_batched_vs_plain": diff,
-            "timing": "median of %d CUDA-event-timed repetitions, L2 flushed (256 MiB write) before each" % args.steps}
+            "timing": "median of %d CUDA-event-timed repetitions, L2 flushed (256 MiB write) before each; "
+                      "the events bracket device work (the host marshals behind a spin kernel)" % args.steps}
 
 
 # --------------------------------------------------------------------------- serving
