@@ -644,15 +644,20 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
         AccSplit<4 * M, 0> acc;
         acc.init();
         float lsat[M];
+        // a_j^T x_t enters b_j: exact products, hi parts summed with TwoSum, the rest in bl
+        float bsh[M], bsl[M];
 #pragma unroll
-        for (int j = 0; j < M; ++j) lsat[j] = 0.0f;
+        for (int j = 0; j < M; ++j) lsat[j] = bsh[j] = bsl[j] = 0.0f;
         auto rowsum = [&](float z, const float (&av)[M], float x) {
             const bool fr = z >= lo && z <= hi;
             const float xc = clampf(z, lo, hi);
 #pragma unroll
             for (int j = 0; j < M; ++j) {
                 const float aj = av[j];
-                acc.f[4 * j + 0] = fmaf(aj, x, acc.f[4 * j + 0]);
+                const float ph = aj * x;
+                const DF t = two_sum(bsh[j], ph);
+                bsh[j] = t.hi;
+                bsl[j] = __fadd_rn(bsl[j], __fadd_rn(t.lo, fmaf(aj, x, -ph)));
                 acc.f[4 * j + 1] = fmaf(aj, xc, acc.f[4 * j + 1]);
                 acc.f[4 * j + 2] = fr ? fmaf(aj, aj, acc.f[4 * j + 2]) : acc.f[4 * j + 2];
                 acc.f[4 * j + 3] += aj > 0.0f ? aj * lo : (aj < 0.0f ? aj * hi : 0.0f);
@@ -744,6 +749,8 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
                 acc.tick();
             });
         acc.fold();
+#pragma unroll
+        for (int j = 0; j < M; ++j) acc.d[4 * j] = df_add(acc.d[4 * j], fast_two_sum(bsh[j], bsl[j]));
         block_reduce<4 * M, M>(acc.d, lsat, sc);
         if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 4 * M, M, a.timeout_cycles, [&](BlockScratch& s) {
                 cupd_after_trial<M>(a, s, ws);

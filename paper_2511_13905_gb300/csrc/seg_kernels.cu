@@ -33,7 +33,7 @@ namespace pgdto {
 struct SegBcast {
     double alpha, beta, c;
     float c_hi, c_lo, beta_hi, beta_lo;
-    int branch, any_active, status, pad;
+    int branch, any_active, status, refine;  // refine: phase D runs again at the refined lam
     float pts[kMaxRows][K];
     int active[kMaxRows];
     float lam_hi[kMaxRows], lam_lo[kMaxRows];
@@ -146,21 +146,53 @@ __device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegState*
     volatile SegBcast* bc = &ws->bc;
     double rc = 0.0;
     if (lane == 1 && !a.proj) {
-        const double dd = df_to_double(sc.tot[a.nrows]);
-        const double nn = df_to_double(sc.tot[a.nrows + 1]);
+        const double dd = df_to_double(sc.tot[2 * a.nrows]);
+        const double nn = df_to_double(sc.tot[2 * a.nrows + 1]);
         rc = nn > 0.0 ? sqrt(dd / nn) : INFINITY;
     }
     rc = __shfl_sync(kFull, rc, 1);
     if (lane != 0) return;
+    // One Newton step per searched row on the accurate residual of this pass.  The
+    // search's FP32 trial sums carry rounding noise (well under 1e-6 (|b| + |a^T x|)),
+    // which can leave its root outside its last bracket by up to that noise over the
+    // slope, on a neighbouring linear piece.  A correction within four bracket widths or
+    // that noise scale is taken; one larger than 1e-7 lam (the estimate was on another
+    // piece) runs this pass again at the corrected lam, at most eight times.
+    int again = 0;
+    double lam_out[kMaxRows];
+    for (int j = 0; j < a.nrows; ++j) {
+        const double ax = df_to_double(sc.tot[j]);
+        double lam = rows[j].lam;
+        if (rows[j].how == 2 && lam > 0.0) {
+            const double reg = rows[j].reg;
+            const double S = df_to_double(sc.tot[a.nrows + j]) + reg;
+            const double r = ax - rows[j].b - reg * lam;
+            const double dl = S > 0.0 ? r / S : 0.0;
+            const double w = (double)rows[j].fH - (double)rows[j].fL;
+            const double noise = S > 0.0 ? 1e-6 * (fabs(rows[j].b) + fabs(ax)) / S : 0.0;
+            if (fabs(dl) <= fmax(4.0 * w, noise) && lam + dl > 0.0) {
+                lam += dl;
+                if (fabs(dl) > 1e-7 * lam && rows[j].nrefine < 8) {
+                    rows[j].nrefine = rows[j].nrefine + 1;
+                    rows[j].lam = lam;
+                    publish_lambda(bc, j, lam);
+                    again = 1;
+                }
+            }
+        }
+        lam_out[j] = lam;
+    }
+    bc->refine = again;
+    if (again) return;
     int status = bc->status;
     int passes = 0;
     double phi = 0.0;
     for (int j = 0; j < a.nrows; ++j) {
         const double ax = df_to_double(sc.tot[j]);
-        inf->lambda[j] = rows[j].lam;
+        inf->lambda[j] = lam_out[j];
         inf->viol[j] = ax - rows[j].b;
         inf->b[j] = rows[j].b;
-        passes = max(passes, rows[j].passes);
+        passes = max(passes, rows[j].passes + rows[j].nrefine);
         phi = fmax(phi, fabs(rows[j].rlast));
         if (rows[j].how == 3 && status == kOk) status = kNotConverged;
         if (!isfinite(ax) && status == kOk) status = kErrNonfinite;
@@ -356,11 +388,22 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
             const int64_t rb = cb & ~int64_t(3);
             const int off = roff;
             roff += seg_res_span(cb, ce);
-            auto e = [&](float z, float av, float x) {
-                acc.f[0] = fmaf(av, x, acc.f[0]);
-                const float xc = clampf(z, lo, hi);
-                acc.f[1] = fmaf(av, xc, acc.f[1]);
-                acc.f[2] = (z >= lo && z <= hi) ? fmaf(av, av, acc.f[2]) : acc.f[2];
+            // a^T x_t (it enters b) and r(0) + b = a^T clip(z_hi + z_lo) decide whether the row
+            // binds: exact products, hi parts summed with TwoSum, everything else in the lo sum
+            float axh = 0.0f, axl = 0.0f, r0h = 0.0f, r0l = 0.0f;
+            auto e = [&](float z, float zl, float av, float x) {
+                const float ph = av * x;
+                const DF t = two_sum(axh, ph);
+                axh = t.hi;
+                axl = __fadd_rn(axl, __fadd_rn(t.lo, fmaf(av, x, -ph)));
+                // free when z_hi + z_lo lies in [lo, hi] (z_hi at a bound decides by z_lo's sign)
+                const bool fr = (z > lo || (z == lo && zl >= 0.0f)) && (z < hi || (z == hi && zl <= 0.0f));
+                const float xc = fr ? z : (z < lo || (z == lo && zl < 0.0f) ? lo : hi);
+                const float q = av * xc;
+                const DF u = two_sum(r0h, q);
+                r0h = u.hi;
+                r0l = __fadd_rn(r0l, __fadd_rn(u.lo, fmaf(av, xc, -q) + (fr ? av * zl : 0.0f)));
+                acc.f[2] = fr ? fmaf(av, av, acc.f[2]) : acc.f[2];
                 acc.f[3] += av > 0.0f ? av * lo : (av < 0.0f ? av * hi : 0.0f);
                 if (av != 0.0f) {
                     const float bp = (av > 0.0f ? z - lo : z - hi) / av;
@@ -372,10 +415,10 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                     cb, ce,
                     [&](int64_t v) {
                         float4 z = LD4L2(a.z_in, v), av = LD4L2(a.A, v);
-                        e(z.x, av.x, 0.0f);
-                        e(z.y, av.y, 0.0f);
-                        e(z.z, av.z, 0.0f);
-                        e(z.w, av.w, 0.0f);
+                        e(z.x, 0.0f, av.x, 0.0f);
+                        e(z.y, 0.0f, av.y, 0.0f);
+                        e(z.z, 0.0f, av.z, 0.0f);
+                        e(z.w, 0.0f, av.w, 0.0f);
                         if (res) {
                             const int q = (off >> 2) + (int)(v - (rb >> 2));
                             reinterpret_cast<float4*>(smz)[q] = z;
@@ -385,7 +428,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                     },
                     [&](int64_t i) {
                         const float z = a.z_in[i], av = a.A[i];
-                        e(z, av, 0.0f);
+                        e(z, 0.0f, av, 0.0f);
                         if (res) {
                             smz[off + (int)(i - rb)] = z;
                             sma[off + (int)(i - rb)] = av;
@@ -417,7 +460,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                     dout = u.hi;
                     zh = z.hi;
                     zl = z.lo;
-                    e(z.hi, av, x);
+                    e(z.hi, z.lo, av, x);
                 };
                 for_chunk<VEC>(
                     cb, ce,
@@ -462,6 +505,8 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                     });
             }
             acc.fold();
+            acc.d[0] = df_add(acc.d[0], fast_two_sum(axh, axl));
+            acc.d[1] = df_add(acc.d[1], fast_two_sum(r0h, r0l));
             float mx[1] = {lsat};
             block_reduce<4, 1>(acc.d, mx, sc, 4 * j, j);
         }
@@ -553,8 +598,13 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
     }
 
     // ---------------------------------------------------------------- phase D
-    {
-        AccSplit<kMaxRows + 2, 0> acc;
+    // x = clip(z - lam a) from the double-float difference w = (z_hi + z_lo) - (lam_hi +
+    // lam_lo) a, and the residual sum a^T x with exact products accumulated in
+    // double-float per element, with the free-set slope beside it: update_final refines
+    // lam by a Newton step on that residual and may ask for this pass again at the
+    // refined lam (x_t is read from x_prev, so a repeated pass sees the same input).
+    for (;;) {
+        AccSplit<2 * kMaxRows + 2, 0> acc;
         acc.init();
         int roff = 0;
         for (int j = 0; j < a.nrows; ++j) {
@@ -564,20 +614,35 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
             const int64_t rb = cb & ~int64_t(3);
             const int off = roff;
             roff += seg_res_span(cb, ce);
-            float axj = 0.0f;
-            DF axd = df_zero();
+            float sh = 0.0f, sl = 0.0f, sfree = 0.0f;  // a^T x as hi (TwoSum) + lo; slope
             int cnt = 0;
+            auto e = [&](float x, float zh, float zl, float av) -> float {
+                const float p = lh * av;
+                const float pe = fmaf(lh, av, -p);
+                const DF s = two_sum(zh, -p);
+                const DF w = fast_two_sum(s.hi, __fadd_rn(s.lo, __fsub_rn(zl, fmaf(ll, av, pe))));
+                // free when w_hi + w_lo lies in [lo, hi] (w_hi at a bound decides by w_lo's sign)
+                const bool below = w.hi < lo || (w.hi == lo && w.lo < 0.0f);
+                const bool above = w.hi > hi || (w.hi == hi && w.lo > 0.0f);
+                const bool fr = !below && !above;
+                const float xn = fr ? w.hi : (below ? lo : hi);
+                const float xl = fr ? w.lo : 0.0f;
+                const float ph = av * xn;
+                const DF t = two_sum(sh, ph);
+                sh = t.hi;
+                sl = __fadd_rn(sl, __fadd_rn(t.lo, fmaf(av, xn, -ph) + av * xl));
+                sfree = fr ? fmaf(av, av, sfree) : sfree;
+                const float dx = xn - x;
+                acc.f[2 * kMaxRows] = fmaf(dx, dx, acc.f[2 * kMaxRows]);
+                acc.f[2 * kMaxRows + 1] = fmaf(xn, xn, acc.f[2 * kMaxRows + 1]);
+                return xn;
+            };
+            auto fold = [&]() {
+                acc.d[j] = df_add(acc.d[j], fast_two_sum(sh, sl));
+                acc.d[kMaxRows + j] = df_add_f(acc.d[kMaxRows + j], sfree);
+                sh = sl = sfree = 0.0f;
+            };
             if (a.proj) {
-                auto e = [&](float z, float av) -> float {
-                    const float qh = lh * av;
-                    const float qe = fmaf(lh, av, -qh);
-                    const float ql = fmaf(ll, av, qe);
-                    const DF s = two_sum(z, -qh);
-                    const float w = __fadd_rn(s.hi, __fsub_rn(s.lo, ql));
-                    const float xo = clampf(w, lo, hi);
-                    axj = fmaf(av, xo, axj);
-                    return xo;
-                };
                 for_chunk<VEC>(
                     cb, ce,
                     [&](int64_t v) {
@@ -591,37 +656,25 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                             av = LD4L2(a.A, v);
                         }
                         float4 o;
-                        o.x = e(z.x, av.x);
-                        o.y = e(z.y, av.y);
-                        o.z = e(z.z, av.z);
-                        o.w = e(z.w, av.w);
+                        o.x = e(0.0f, z.x, 0.0f, av.x);
+                        o.y = e(0.0f, z.y, 0.0f, av.y);
+                        o.z = e(0.0f, z.z, 0.0f, av.z);
+                        o.w = e(0.0f, z.w, 0.0f, av.w);
                         reinterpret_cast<float4*>(a.x_out)[v] = o;
                         if (++cnt == kFoldEvery) {
-                            axd = df_add_f(axd, axj);
-                            axj = 0.0f;
+                            fold();
                             cnt = 0;
                         }
                     },
                     [&](int64_t i) {
                         const int q = off + (int)(i - rb);
-                        a.x_out[i] = res ? e(smz[q], sma[q]) : e(a.z_in[i], a.A[i]);
+                        a.x_out[i] = res ? e(0.0f, smz[q], 0.0f, sma[q]) : e(0.0f, a.z_in[i], 0.0f, a.A[i]);
                     });
             } else {
-                // x_{t+1} = clip(z - lam a) with z = z_hi + z_lo and lam = lam_hi + lam_lo
-                auto e = [&](float x, float zh, float zl, float av) -> float {
-                    const float t1 = fmaf(-lh, av, zh);
-                    const float t2 = fmaf(-ll, av, zl);
-                    const float xn = clampf(__fadd_rn(t1, t2), lo, hi);
-                    axj = fmaf(av, xn, axj);
-                    const float dx = xn - x;
-                    acc.f[kMaxRows] = fmaf(dx, dx, acc.f[kMaxRows]);
-                    acc.f[kMaxRows + 1] = fmaf(xn, xn, acc.f[kMaxRows + 1]);
-                    return xn;
-                };
                 for_chunk<VEC>(
                     cb, ce,
                     [&](int64_t v) {
-                        float4 x = LD4L2(a.x, v), zh, zl, av;
+                        float4 x = LD4L2(a.x_prev, v), zh, zl, av;
                         if (res) {
                             const int q = (off >> 2) + (int)(v - (rb >> 2));
                             zh = reinterpret_cast<const float4*>(smz)[q];
@@ -639,29 +692,37 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                         o.w = e(x.w, zh.w, zl.w, av.w);
                         reinterpret_cast<float4*>(a.x)[v] = o;
                         if (++cnt == kFoldEvery) {
-                            axd = df_add_f(axd, axj);
-                            axj = 0.0f;
+                            fold();
                             cnt = 0;
                             acc.fold();
                         }
                     },
                     [&](int64_t i) {
                         const int q = off + (int)(i - rb);
-                        a.x[i] = res ? e(a.x[i], smz[q], sml[q], sma[q]) : e(a.x[i], a.z[i], a.zlo[i], a.A[i]);
+                        a.x[i] = res ? e(a.x_prev[i], smz[q], sml[q], sma[q])
+                                     : e(a.x_prev[i], a.z[i], a.zlo[i], a.A[i]);
                     });
             }
-            axd = df_add_f(axd, axj);
-            acc.d[j] = df_add(acc.d[j], axd);
+            fold();
         }
         acc.fold();
-        const int nv = a.nrows + (a.proj ? 0 : 2);
-        if (a.nrows < kMaxRows) {
-            // pack the two norms right after the rows
-            acc.d[a.nrows] = acc.d[kMaxRows];
-            acc.d[a.nrows + 1] = acc.d[kMaxRows + 1];
+        // pack: rows' a^T x, rows' slopes, then the two norms
+        const int nr = a.nrows;
+        DF packed[2 * kMaxRows + 2];
+#pragma unroll
+        for (int k = 0; k < 2 * kMaxRows + 2; ++k) packed[k] = df_zero();
+        for (int k = 0; k < nr; ++k) {
+            packed[k] = acc.d[k];
+            packed[nr + k] = acc.d[kMaxRows + k];
         }
-        block_reduce<kMaxRows + 2, 0>(acc.d, nullptr, sc);
-        sy.reduce(sc, nv, 0, [&](BlockScratch& s, SegState* st) { update_final(a, s, st, sy.sticky(), sy.launches()); });
+        packed[2 * nr] = acc.d[2 * kMaxRows];
+        packed[2 * nr + 1] = acc.d[2 * kMaxRows + 1];
+        const int nv = 2 * nr + (a.proj ? 0 : 2);
+        block_reduce<2 * kMaxRows + 2, 0>(packed, nullptr, sc);
+        if (!sy.reduce(sc, nv, 0, [&](BlockScratch& s, SegState* st) { update_final(a, s, st, sy.sticky(), sy.launches()); }))
+            return;
+        sy.fetch(bc);
+        if (!bc.refine) break;
     }
 }
 

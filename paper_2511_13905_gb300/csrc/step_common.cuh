@@ -20,7 +20,7 @@ constexpr unsigned kFull = 0xffffffffu;
 // with r(L) > 0 >= r(H); SL, SH are the slopes -dr/dt at the ends.
 struct RowState {
     double b, L, rL, SL, H, rH, SH, lam, rlast, reg;
-    int active, passes, how, pad;
+    int active, passes, how, nrefine;  // nrefine: extra final passes at a refined root
     // the same bracket in float / double-float form: the per-pass update works on these
     // (FP64 issues at a small fraction of the FP32 rate here and sits on the critical path)
     float b_hi, b_lo, fL, fH, rL_hi, rL_lo, rH_hi, rH_lo, fSL, fSH, freg, fpad;
@@ -146,6 +146,7 @@ __device__ __forceinline__ void store_row(volatile RowState* r, double b, double
     r->active = active;
     r->passes = passes;
     r->how = how;
+    r->nrefine = 0;
     float h, l;
     split_double(b, h, l);
     r->b_hi = h;
