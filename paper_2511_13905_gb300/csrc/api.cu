@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of include/pgdto.h: argument checks, handle and workspace
 // ownership, state rotation, launches on the caller's stream, and the report read-back.
 #include <math.h>
+#include <stddef.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -46,6 +47,7 @@ struct pgdto_handle {
     int64_t a_len;            // floats in A for this mode
     int64_t launches;
     int last_was_project;
+    int warm;                 // the last report is a step's: its lam seeds the next step's search
     int engine;               // 1 grid, 2 cluster
     int cl_size, cl_max;      // this problem's cluster size; clusters co-resident at the largest size
     int res_grid, res_cluster;  // shared-memory residency floats per array on each engine (0 = off)
@@ -274,6 +276,7 @@ extern "C" pgdto_status pgdto_set_state(pgdto_handle* h, const float* x_prev, co
     if (d_prev) CK(cudaMemcpyAsync(dcur, d_prev, nb, cudaMemcpyDeviceToDevice, h->stream));
     else CK(cudaMemsetAsync(dcur, 0, nb, h->stream));
     h->t = t;
+    h->warm = 0;
     return PGDTO_OK;
 }
 
@@ -376,6 +379,11 @@ static void fill_seg_args(pgdto_handle* h, bool proj, float* x, const float* g, 
     a.timeout_cycles = h->timeout_cycles;
     a.ws = (SegWork*)h->work;
     a.info_out = h->dev_info;
+    // warm start from the previous step's lam, still in the handle's report on the device
+    a.lam_prev = (!proj && h->warm)
+                     ? reinterpret_cast<const double*>(reinterpret_cast<const char*>(h->dev_info) +
+                                                       offsetof(DeviceInfo, lambda))
+                     : nullptr;
 }
 
 static pgdto_status launch(pgdto_handle* h, bool proj, float* x, const float* g, const float* A, const double* bconst,
@@ -450,6 +458,7 @@ extern "C" pgdto_status pgdto_step(pgdto_handle* h, float* x, const float* grad_
     h->cur = 1 - h->cur;  // d_t becomes d_prev
     h->t += 1;
     h->last_was_project = 0;
+    h->warm = h->mode != PGDTO_COUPLED;
     if (info) return read_info(h, info, nullptr);
     return PGDTO_OK;
 }
@@ -490,6 +499,7 @@ extern "C" pgdto_status pgdto_project(pgdto_handle* h, const float* z, const flo
     pgdto_status s = launch(h, true, nullptr, nullptr, A, bb, z, x_out, false);
     if (s != PGDTO_OK) return s;
     h->last_was_project = 1;
+    h->warm = 0;
     if (info || lambda_out) return read_info(h, info, lambda_out);
     return PGDTO_OK;
 }
@@ -648,6 +658,7 @@ extern "C" pgdto_status pgdto_step_many(int count, pgdto_handle* const* hs, floa
         hs[k]->cur = 1 - hs[k]->cur;
         hs[k]->t += 1;
         hs[k]->last_was_project = 0;
+        hs[k]->warm = 1;
     }
     if (!infos) return PGDTO_OK;
     pgdto_status worst = PGDTO_OK;
@@ -686,7 +697,10 @@ extern "C" pgdto_status pgdto_project_many(int count, pgdto_handle* const* hs, c
     s = launch_many(count, hs, args, vec);
     delete[] args;
     if (s != PGDTO_OK) return s;
-    for (int k = 0; k < count; ++k) hs[k]->last_was_project = 1;
+    for (int k = 0; k < count; ++k) {
+        hs[k]->last_was_project = 1;
+        hs[k]->warm = 0;
+    }
     if (!infos && !lambda_out) return PGDTO_OK;
     pgdto_status worst = PGDTO_OK;
     for (int k = 0; k < count; ++k) {

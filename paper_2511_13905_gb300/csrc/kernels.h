@@ -47,6 +47,7 @@ struct SegArgs {
     SegWork* ws;          // grid engine workspace
     DeviceInfo* info_out; // cluster engine: where this problem's report goes
     int sm_elems;         // shared-memory residency: floats per array (z_hi, z_lo, a); 0 = off
+    const double* lam_prev;  // warm start: the previous step's lam per row (device), or null
 };
 
 // Shared-memory residency of a CTA's share of a problem.  The CTA's chunk of row j is

@@ -110,7 +110,8 @@ __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, Seg
     else if (k == 1) q = rH / two_c;
     const double NL = __shfl_sync(kFull, q, lane & ~7);
     const double NH = H + __shfl_sync(kFull, q, (lane & ~7) + 1);
-    const float p = next_point(lane, 0.0, r0, H, rH, NL, NH);
+    const double lp = a.lam_prev ? a.lam_prev[jj] : -1.0;
+    const float p = next_point_warm(lane, 0.0, r0, H, rH, NL, NH, lp);
     if (row && k == 0) {
         ws->info.b[j] = b;
         rows[j].reg = two_c;

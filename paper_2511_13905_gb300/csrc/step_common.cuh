@@ -131,6 +131,32 @@ __device__ __forceinline__ float next_point(int lane, double L, double rL, doubl
     return group8_sort(f, lane);
 }
 
+// First points of a search that has the previous step's root lp (warm start): Newton from
+// both ends, the secant, the midpoint, and a ladder lp (1 -+ 0.003), lp (1 -+ 0.03) around
+// it, since a design's dual moves little from one step to the next.  Without a usable lp
+// (outside (L, H)) the points are next_point's.  Either way any lp only changes where the
+// first pass looks.  Every lane reaches the one group8_sort (full-warp shuffles).
+__device__ __forceinline__ float next_point_warm(int lane, double L, double rL, double H, double rH, double NL,
+                                                 double NH, double lp) {
+    const int k = lane & 7;
+    const bool warm = lp > L && lp < H;
+    const double w = H - L;
+    double v;
+    if (k == 0) v = NL;
+    else if (k == 1) v = NH;
+    else if (k == 2) v = L + rL * w / (rL - rH);
+    else if (!warm) v = L + w * (double)(k - 2) * (1.0 / 6.0);
+    else if (k == 3) v = L + 0.5 * w;
+    else v = lp * (k == 4 ? 0.97 : k == 5 ? 0.997 : k == 6 ? 1.003 : 1.03);
+    if (!(v > L && v < H)) v = L + w * ((double)k + 0.5) * 0.125;
+    float fv = (float)v;
+    if (!((double)fv > L && (double)fv < H)) {
+        fv = (float)(0.5 * (L + H));
+        if (!((double)fv > L && (double)fv < H)) fv = (float)H;
+    }
+    return group8_sort(fv, lane);
+}
+
 __device__ __forceinline__ void store_row(volatile RowState* r, double b, double L, double rL, double SL, double H,
                                           double rH, double SH, double lam, double rlast, int active, int passes,
                                           int how) {

@@ -165,3 +165,32 @@ def test_loop_until_relative_change_stop(dev):
     h.close()
     assert stop_gpu == stop_ref
     assert float(np.max(np.abs(xd.cpu().numpy().astype(np.float64) - x.astype(np.float64)))) < 1e-4
+
+
+def test_warm_started_steps_match_the_oracle(dev):
+    """Consecutive steps of one handle seed each search with the previous step's lam (warm
+    start); each step still equals the oracle's step from the same state (read back with
+    pgdto_get_state)."""
+    import torch
+    from paper_2511_13905_gb300 import binding
+    cfg = inputs.config2(dims=(48, 24, 24))
+    n = cfg["n"]
+    h = binding.Handle(n, 1)
+    h.set_state(None, None, None, 0)
+    x = T(cfg["x"], dev)
+    xp, gp, dp = (torch.empty(n, device=dev) for _ in range(3))
+    passes = []
+    for t in range(14):
+        x_now = x.cpu().numpy()
+        t_now = h.get_state(xp, gp, dp)
+        assert t_now == t
+        A, gval = inputs.config2_inputs(cfg, x_now)
+        st, info = h.step(x, T(cfg["g"], dev), T(A, dev), gval, cfg["G"])
+        torch.cuda.synchronize()
+        assert st == 0, (t, st)
+        ref = oracle_step(x_now, xp.cpu().numpy(), cfg["g"], gp.cpu().numpy(), dp.cpu().numpy(), A, gval, cfg["G"], t)
+        check(parity_errors(x.cpu().numpy(), [info.lambda_[0]], ref["x_new"], ref["lam"], A, ref["b"], C, 0.0, 1.0),
+              "warm t=%d" % t)
+        passes.append(info.passes)
+    h.close()
+    assert max(passes) <= 20
