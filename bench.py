@@ -442,7 +442,7 @@ def run_serving(args, local_rank=0):
     warm = True
     t_total = 0.0
     for w in range(waves + 1):
-        t0 = time.perf_counter()
+        t0 = srv.clock_us()
         tickets = []
         for i, p in enumerate(probs):
             st, t = srv.submit(i, p["n"], p["m"], grads[i][w % 2], np.ascontiguousarray(p["A"]), gvals[i], p["G"],
@@ -450,21 +450,18 @@ def run_serving(args, local_rank=0):
             if st != binding.PGDTO_OK:
                 raise RuntimeError("submit failed: %s" % st)
             tickets.append(t)
-        pending = set(range(len(tickets)))
         done_at = {}
-        while pending:
-            for i in list(pending):
-                st, d, _ = srv.poll(tickets[i])
-                if d != binding.PGDTO_ERR_BUSY:
-                    if d not in (binding.PGDTO_OK, binding.PGDTO_NOT_CONVERGED):
-                        raise RuntimeError("served step failed: %s" % d)
-                    nc_served += int(d == binding.PGDTO_NOT_CONVERGED)
-                    done_at[i] = time.perf_counter()
-                    pending.discard(i)
-        t1 = time.perf_counter()
+        for i in range(len(tickets)):
+            # blocking waits; each completion time was stamped by the server when published
+            st, d, _, t_done = srv.wait(tickets[i])
+            if st != binding.PGDTO_OK or d not in (binding.PGDTO_OK, binding.PGDTO_NOT_CONVERGED):
+                raise RuntimeError("served step failed: %s / %s" % (st, d))
+            nc_served += int(d == binding.PGDTO_NOT_CONVERGED)
+            done_at[i] = t_done
+        t1 = max(done_at.values())
         if not warm:
-            lat += [done_at[i] - t0 for i in range(len(probs))]
-            t_total += t1 - t0
+            lat += [(done_at[i] - t0) * 1e-6 for i in range(len(probs))]
+            t_total += (t1 - t0) * 1e-6
         warm = False
         gvals = [constraint_values(p, outs[i]) for i, p in enumerate(probs)]
     stats = srv.stats()

@@ -247,6 +247,16 @@ pgdto_status pgdto_submit(pgdto_server* srv, const pgdto_request* req, uint64_t*
  * the first poll that reports it. */
 pgdto_status pgdto_poll(pgdto_server* srv, uint64_t ticket, pgdto_status* done, pgdto_info* info);
 
+/* Blocking form of pgdto_poll: waits up to timeout_ms for the step.  *done as for
+ * pgdto_poll (PGDTO_ERR_BUSY when the wait ran out); completed_us (nullable) receives the
+ * moment the result was published, on the server's clock (pgdto_server_clock_us).
+ * PGDTO_ERR_ARG for an unknown or already reported ticket. */
+pgdto_status pgdto_wait(pgdto_server* srv, uint64_t ticket, int timeout_ms, pgdto_status* done, pgdto_info* info,
+                        int64_t* completed_us);
+
+/* Microseconds since the server was created (steady clock); -1 for NULL. */
+int64_t pgdto_server_clock_us(const pgdto_server* srv);
+
 /* Counters: launches (batches), steps completed, sessions open, bytes in use. */
 pgdto_status pgdto_server_stats(pgdto_server* srv, int64_t* batches, int64_t* steps, int* sessions,
                                 uint64_t* bytes_in_use);

@@ -107,6 +107,9 @@ def load(path=None):
                                                ctypes.POINTER(Params), P]),
         "pgdto_submit": (ctypes.c_int, [H, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
         "pgdto_poll": (ctypes.c_int, [H, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Info)]),
+        "pgdto_wait": (ctypes.c_int, [H, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Info),
+                                      ctypes.POINTER(ctypes.c_int64)]),
+        "pgdto_server_clock_us": (ctypes.c_int64, [H]),
         "pgdto_server_stats": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_uint64)]),
         "pgdto_server_destroy": (None, [H]),
@@ -338,6 +341,22 @@ class Server:
         if st == PGDTO_OK and d.value != PGDTO_ERR_BUSY:
             self._keep.pop(ticket, None)
         return st, d.value, info
+
+    def wait(self, ticket, timeout_ms=60000):
+        """Blocking poll: (call status, done status or PGDTO_ERR_BUSY, Info, completion time
+        in microseconds on the server's clock)."""
+        d = ctypes.c_int()
+        info = Info()
+        t = ctypes.c_int64()
+        st = self.lib.pgdto_wait(self.h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(d), ctypes.byref(info),
+                                 ctypes.byref(t))
+        if st == PGDTO_OK and d.value != PGDTO_ERR_BUSY:
+            self._keep.pop(ticket, None)
+        return st, d.value, info, t.value
+
+    def clock_us(self):
+        """Microseconds since the server was created (the clock of wait's completion times)."""
+        return int(self.lib.pgdto_server_clock_us(self.h))
 
     def stats(self):
         b, s_, n = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -52,6 +53,7 @@ struct Request {
 struct Done {
     pgdto_status status = PGDTO_OK;
     pgdto_info info;
+    int64_t t_us = 0;  // completion on the server's clock
 };
 
 }  // namespace
@@ -65,7 +67,9 @@ struct pgdto_server {
     cudaStream_t dtoh = nullptr;    // result downloads
     std::vector<cudaEvent_t> unit_done;  // one per launch unit of a cycle (batched group, own launches)
     std::mutex mu;
-    std::condition_variable cv;
+    std::condition_variable cv;       // service thread: work queued
+    std::condition_variable cv_done;  // waiters: a result was published
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
     std::thread worker;
     bool stop = false;
     uint64_t next_ticket = 1;
@@ -77,6 +81,10 @@ struct pgdto_server {
 };
 
 namespace {
+
+int64_t clock_us(const pgdto_server* srv) {
+    return std::chrono::duration_cast<std::chrono::microseconds>(std::chrono::steady_clock::now() - srv->t0).count();
+}
 
 uint64_t session_bytes(int64_t n, int64_t a_len) {
     // handle: x_prev, g_prev, d[2], z, z_lo (6 n floats) + workspace; session: x, g, A
@@ -111,6 +119,8 @@ void finish_unit(pgdto_server* srv, cudaEvent_t ev, std::vector<Request>& unit) 
     }
     if (cudaStreamSynchronize(srv->dtoh) != cudaSuccess)
         for (Done& d : results) d.status = PGDTO_ERR_CUDA;
+    const int64_t now = clock_us(srv);
+    for (Done& d : results) d.t_us = now;
     std::lock_guard<std::mutex> lock(srv->mu);
     for (size_t i = 0; i < unit.size(); ++i) {
         Request& r = unit[i];
@@ -128,6 +138,7 @@ void finish_unit(pgdto_server* srv, cudaEvent_t ev, std::vector<Request>& unit) 
         }
         srv->steps += 1;
     }
+    srv->cv_done.notify_all();
 }
 
 // One cycle: every single/independent session in one batched step (pgdto_step_many: one
@@ -332,6 +343,37 @@ extern "C" pgdto_status pgdto_poll(pgdto_server* srv, uint64_t ticket, pgdto_sta
         }
     return PGDTO_ERR_ARG;  // unknown or already reported
 }
+
+extern "C" pgdto_status pgdto_wait(pgdto_server* srv, uint64_t ticket, int timeout_ms, pgdto_status* done,
+                                   pgdto_info* info, int64_t* completed_us) {
+    if (!srv || !done || timeout_ms < 0) return PGDTO_ERR_ARG;
+    std::unique_lock<std::mutex> lock(srv->mu);
+    auto known = [&] {
+        for (const Request& r : srv->pending)
+            if (r.ticket == ticket) return true;
+        for (const Request& r : srv->running)
+            if (r.ticket == ticket) return true;
+        return false;
+    };
+    const auto until = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+    for (;;) {
+        auto it = srv->done.find(ticket);
+        if (it != srv->done.end()) {
+            *done = it->second.status;
+            if (info) *info = it->second.info;
+            if (completed_us) *completed_us = it->second.t_us;
+            srv->done.erase(it);
+            return PGDTO_OK;
+        }
+        if (!known()) return PGDTO_ERR_ARG;  // unknown or already reported
+        if (srv->cv_done.wait_until(lock, until) == std::cv_status::timeout && srv->done.count(ticket) == 0) {
+            *done = PGDTO_ERR_BUSY;
+            return PGDTO_OK;
+        }
+    }
+}
+
+extern "C" int64_t pgdto_server_clock_us(const pgdto_server* srv) { return srv ? clock_us(srv) : -1; }
 
 extern "C" pgdto_status pgdto_server_stats(pgdto_server* srv, int64_t* batches, int64_t* steps, int* sessions,
                                            uint64_t* bytes_in_use) {

@@ -147,3 +147,33 @@ def test_admission_budget_and_one_step_per_session(dev):
     done, _ = _wait(srv, t1)
     assert done == binding.PGDTO_OK
     srv.close()
+
+
+def test_wait_blocks_and_stamps_completion(dev):
+    """pgdto_wait: blocks until the step is published, returns the same report as a poll
+    would, and stamps the completion on the server's clock; a reported or unknown ticket
+    is an argument error."""
+    from paper_2511_13905_gb300 import binding
+    sess = _sessions()
+    srv = binding.Server(budget_bytes=8 << 30, max_sessions=64)
+    t0 = srv.clock_us()
+    tickets = []
+    for r, p in sess:
+        g, gval = _grads(p, p["x"], 0)
+        out = np.empty(p["n"], np.float32)
+        st, t = srv.submit(r["id"], p["n"], p["m"], g, np.ascontiguousarray(p["A"]), gval, p["G"], out,
+                           x0=p["x"], seg=p.get("seg"))
+        assert st == binding.PGDTO_OK
+        tickets.append((t, out))
+    stamps = []
+    for t, out in reversed(tickets):
+        st, done, info, t_done = srv.wait(t, timeout_ms=60000)
+        assert st == binding.PGDTO_OK and done == binding.PGDTO_OK
+        assert np.all(np.isfinite(out)) and info.passes >= 0
+        assert t0 <= t_done <= srv.clock_us()
+        stamps.append(t_done)
+        st, _, _, _ = srv.wait(t, timeout_ms=0)
+        assert st == binding.PGDTO_ERR_ARG  # reported once
+    st, _, _, _ = srv.wait(123456789, timeout_ms=0)
+    assert st == binding.PGDTO_ERR_ARG
+    srv.close()
