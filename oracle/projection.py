@@ -54,11 +54,23 @@ def jacobian_h(z, A, lam, lo, hi, C):
     return Af @ Af.T + (2.0 / C) * np.eye(A.shape[0])
 
 
-def phi(h, y):
-    """Phi_j(y) = max(h_j, 0) + sign(max(-h_j, 0)) * y_j  (eq. phi)."""
+def eq_mask(eq, m):
+    """Boolean mask of the equality rows among m rows (Sec. 3.2.4); None: all inequalities."""
+    out = np.zeros(m, dtype=bool)
+    if eq is not None:
+        out[:] = np.asarray(eq, dtype=bool)
+    return out
+
+
+def phi(h, y, eq=None):
+    """Phi_j(y) = max(h_j, 0) + sign(max(-h_j, 0)) * y_j  (eq. phi); for an equality row
+    Phi_j = h_j, the row being always active (Sec. 3.2.4)."""
     h = np.asarray(h, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
-    return np.maximum(h, 0.0) + np.sign(np.maximum(-h, 0.0)) * y
+    out = np.maximum(h, 0.0) + np.sign(np.maximum(-h, 0.0)) * y
+    E = eq_mask(eq, h.size)
+    out[E] = h[E]
+    return out
 
 
 def row_scale(A, b, x):
@@ -127,7 +139,7 @@ def _piecewise_root(w, u, c, lo, hi, reg):
     return max(gam, left)
 
 
-def solve_single_exact(z, a, b, lo, hi, C):
+def solve_single_exact(z, a, b, lo, hi, C, equality=False):
     """Exact root of the regularised single-row dual equation (App. A.2 + eq. h).
 
     r(lam) = a^T clip(z - lam a) - b - 2 lam / C is piecewise linear and strictly
@@ -136,16 +148,24 @@ def solve_single_exact(z, a, b, lo, hi, C):
     is inactive and lam = 0 (Alg. 1's feasibility test); otherwise the root is found
     exactly on its linear piece (_piecewise_root).  Past the last breakpoint the free
     set is empty and the root is lam = (C/2)(S_min - b).
+
+    An equality row (Sec. 3.2.4) is always active: lam ranges over R and r(lam) = 0.
+    When r(0) < 0 the root is negative.  With mu = -lam, r(-mu) = -psi(mu) where psi is
+    the residual of the mirrored row (-a, -b), which is positive at 0, so the root is
+    minus the mirrored row's (positive) root.
     """
     z = np.asarray(z, dtype=np.float64)
     a = np.asarray(a, dtype=np.float64)
     b = float(b)
-    if _r1(z, a, b, lo, hi, C, 0.0) <= 0.0:
+    r0 = _r1(z, a, b, lo, hi, C, 0.0)
+    if r0 > 0.0:
+        return _piecewise_root(z, a, b, lo, hi, 2.0 / C)
+    if not equality or r0 == 0.0:
         return 0.0
-    return _piecewise_root(z, a, b, lo, hi, 2.0 / C)
+    return -_piecewise_root(z, -a, -b, lo, hi, 2.0 / C)
 
 
-def solve_single_bisect(z, a, b, lo, hi, C, tol_B=1e-8, rel_tol=0.0, max_iter=100000):
+def solve_single_bisect(z, a, b, lo, hi, C, tol_B=1e-8, rel_tol=0.0, max_iter=100000, equality=False):
     """Alg. 1 (single-constraint bisection) written for lam = -y, regularised as eq. h.
 
     Steps, in the paper's order: test lam = 0 (delta(0) feasible -> return 0); bracket
@@ -153,13 +173,19 @@ def solve_single_bisect(z, a, b, lo, hi, C, tol_B=1e-8, rel_tol=0.0, max_iter=10
     max(tol_B, rel_tol * lam_hi_current) wide; return the midpoint.  When even the
     saturated point violates the row, r is linear beyond lam_hi and its root
     (C/2)(S_min - b) is returned directly (the regularised reading of the bracket).
+    An equality row (Sec. 3.2.4) with r(0) < 0 runs the same steps on the mirrored row
+    (-a, -b) and returns minus its root (see solve_single_exact).
     Returns (lam, number_of_halvings).
     """
     z = np.asarray(z, dtype=np.float64)
     a = np.asarray(a, dtype=np.float64)
     b = float(b)
-    if _r1(z, a, b, lo, hi, C, 0.0) <= 0.0:
-        return 0.0, 0
+    r0 = _r1(z, a, b, lo, hi, C, 0.0)
+    if r0 <= 0.0:
+        if not equality or r0 == 0.0:
+            return 0.0, 0
+        lam, it = solve_single_bisect(z, -a, -b, lo, hi, C, tol_B, rel_tol, max_iter)
+        return -lam, it
     lam_lo = 0.0
     lam_hi = _saturation_bound(z, a, lo, hi)
     if _r1(z, a, b, lo, hi, C, lam_hi) > 0.0:
@@ -176,28 +202,31 @@ def solve_single_bisect(z, a, b, lo, hi, C, tol_B=1e-8, rel_tol=0.0, max_iter=10
     return 0.5 * (lam_lo + lam_hi), it
 
 
-def solve_independent_exact(z, a, seg, b, lo, hi, C):
+def solve_independent_exact(z, a, seg, b, lo, hi, C, eq=None):
     """Sec. 3.2.2: rows with disjoint supports seg[j]:seg[j+1] are m separate single-row solves.
 
     ``a`` holds one coefficient per variable (the value of the row that owns it).
     Variables outside every segment (none in the shipped workloads) are only clipped.
+    ``eq`` marks equality rows (Sec. 3.2.4).
     """
     seg = [int(s) for s in seg]
+    E = eq_mask(eq, len(seg) - 1)
     lam = np.zeros(len(seg) - 1)
     for j in range(len(seg) - 1):
         s, e = seg[j], seg[j + 1]
-        lam[j] = solve_single_exact(z[s:e], a[s:e], b[j], lo, hi, C)
+        lam[j] = solve_single_exact(z[s:e], a[s:e], b[j], lo, hi, C, equality=bool(E[j]))
     return lam
 
 
-def solve_independent_bisect(z, a, seg, b, lo, hi, C, tol_B=1e-8, rel_tol=0.0):
+def solve_independent_bisect(z, a, seg, b, lo, hi, C, tol_B=1e-8, rel_tol=0.0, eq=None):
     """Sec. 3.2.2 with Alg. 1 per row; returns (lam, halvings per row)."""
     seg = [int(s) for s in seg]
+    E = eq_mask(eq, len(seg) - 1)
     lam = np.zeros(len(seg) - 1)
     its = []
     for j in range(len(seg) - 1):
         s, e = seg[j], seg[j + 1]
-        lam[j], it = solve_single_bisect(z[s:e], a[s:e], b[j], lo, hi, C, tol_B, rel_tol)
+        lam[j], it = solve_single_bisect(z[s:e], a[s:e], b[j], lo, hi, C, tol_B, rel_tol, equality=bool(E[j]))
         its.append(it)
     return lam, its
 
@@ -225,7 +254,7 @@ def segmented_to_dense(a, seg, n):
 
 # --------------------------------------------------------------------------- coupled rows
 
-def _newton_stage2(z, A, b, lo, hi, C, y0, tol, maxiter, c1=1e-4, c2=0.9):
+def _newton_stage2(z, A, b, lo, hi, C, y0, tol, maxiter, c1=1e-4, c2=0.9, eq=None):
     """Alg. 2 stage 2: semismooth Newton on Phi(y) with a backtracking line search on M.
 
     Each iteration: h(y) (eq. h), Phi (eq. phi), J_h (eq. reg_jacobian),
@@ -235,22 +264,29 @@ def _newton_stage2(z, A, b, lo, hi, C, y0, tol, maxiter, c1=1e-4, c2=0.9):
     clamp keeps the iterate dual feasible (reading of eq. phi, whose roots with y_j > 0
     are not KKT points).  The curvature condition with c2 is evaluated and recorded
     only.  Stops when ||Phi||_inf <= tol * scale_j row by row or after maxiter.
+    Equality rows (Sec. 3.2.4): Phi_j = h_j, its row of J_Phi is J_h's, and y_j is not
+    clamped.
     Returns (y, iterations, converged, curvature_failures).
     """
     m = A.shape[0]
-    y = np.minimum(np.asarray(y0, dtype=np.float64).copy(), 0.0)
+    E = eq_mask(eq, m)
+
+    def clamp(v):
+        return np.where(E, v, np.minimum(v, 0.0))
+
+    y = clamp(np.asarray(y0, dtype=np.float64).copy())
     curv_fail = 0
     for k in range(maxiter + 1):
         lam = -y
         h = residual(z, A, b, lam, lo, hi, C)
-        Ph = phi(h, y)
+        Ph = phi(h, y, E)
         scale = row_scale(A, b, primal_from_dual(z, A, lam, lo, hi))
         if np.all(np.abs(Ph) <= tol * scale):
             return y, k, True, curv_fail
         if k == maxiter:
             break
         Jh = jacobian_h(z, A, lam, lo, hi, C)
-        Dphi = np.diag((h > 0).astype(np.float64))
+        Dphi = np.diag(((h > 0) | E).astype(np.float64))
         Jphi = Dphi @ Jh + np.eye(m) - Dphi
         Delta = np.linalg.solve(Jphi, Ph)
         M0 = 0.5 * float(Ph @ Ph)
@@ -258,14 +294,14 @@ def _newton_stage2(z, A, b, lo, hi, C, y0, tol, maxiter, c1=1e-4, c2=0.9):
         gamma = 1.0
         accepted = None
         for _ in range(41):
-            y_new = np.minimum(y - gamma * Delta, 0.0)
+            y_new = clamp(y - gamma * Delta)
             h_new = residual(z, A, b, -y_new, lo, hi, C)
-            P_new = phi(h_new, y_new)
+            P_new = phi(h_new, y_new, E)
             if 0.5 * float(P_new @ P_new) <= M0 - c1 * gamma * slope:
                 accepted = y_new
                 # curvature condition of App. A.3.3, recorded only
                 Jh_n = jacobian_h(z, A, -y_new, lo, hi, C)
-                D_n = np.diag((h_new > 0).astype(np.float64))
+                D_n = np.diag(((h_new > 0) | E).astype(np.float64))
                 J_n = D_n @ Jh_n + np.eye(m) - D_n
                 if float((J_n.T @ P_new) @ Delta) > c2 * slope:
                     curv_fail += 1
@@ -273,7 +309,7 @@ def _newton_stage2(z, A, b, lo, hi, C, y0, tol, maxiter, c1=1e-4, c2=0.9):
             gamma *= 0.5
         if accepted is None:
             # no decrease found on the grid: keep the smallest clamped step and go on
-            accepted = np.minimum(y - gamma * Delta, 0.0)
+            accepted = clamp(y - gamma * Delta)
         y = accepted
     return y, maxiter, False, curv_fail
 
@@ -344,7 +380,7 @@ def _solve_on_rows(z, A, b, lo, hi, C, S, lam_init, max_iter=200):
     return lam
 
 
-def solve_coupled_exact(z, A, b, lo, hi, C, lam0=None, kkt_tol=1e-11):
+def solve_coupled_exact(z, A, b, lo, hi, C, lam0=None, kkt_tol=1e-11, eq=None):
     """Unique optimum of the regularised projection for coupled rows (Thm 2).
 
     A KKT point has some set S of rows with lam_j >= 0 free to move and r_j <= 0 on the
@@ -352,7 +388,8 @@ def solve_coupled_exact(z, A, b, lo, hi, C, lam0=None, kkt_tol=1e-11):
     (_solve_on_rows); the candidate is the answer when lam_S >= 0 and every other row
     satisfies r_j <= 0.  The first candidate is the set of rows that Alg. 2's stage 1
     single-row candidates mark active (lam0 > 0); after it every subset of the m <= 4
-    rows is tried, largest first.  Returns (lam, info dict with the scaled KKT report).
+    rows is tried, largest first.  Equality rows (``eq``, Sec. 3.2.4) belong to every
+    candidate set and keep their sign.  Returns (lam, info dict with the scaled KKT report).
     """
     from itertools import combinations
 
@@ -362,22 +399,28 @@ def solve_coupled_exact(z, A, b, lo, hi, C, lam0=None, kkt_tol=1e-11):
     A = np.atleast_2d(np.asarray(A, dtype=np.float64))
     b = np.asarray(b, dtype=np.float64)
     m = A.shape[0]
+    E = eq_mask(eq, m)
     if lam0 is None:
-        lam0 = np.array([solve_single_exact(z, A[j], b[j], lo, hi, C) for j in range(m)])
+        lam0 = np.array([solve_single_exact(z, A[j], b[j], lo, hi, C, equality=bool(E[j])) for j in range(m)])
     lam0 = np.asarray(lam0, dtype=np.float64)
-    first = tuple(j for j in range(m) if lam0[j] > 0)
-    order = [first] + [S for k in range(m, 0, -1) for S in combinations(range(m), k) if S != first]
-    if () not in order:
-        order.append(())
+    ineq = [j for j in range(m) if not E[j]]
+    always = set(np.flatnonzero(E).tolist())
+    first = tuple(sorted(always | {j for j in ineq if lam0[j] > 0}))
+    order = [first]
+    for k in range(len(ineq), -1, -1):
+        for S in combinations(ineq, k):
+            S = tuple(sorted(always | set(S)))
+            if S not in order:
+                order.append(S)
     best = None
     for tried, S in enumerate(order):
         S = list(S)
         lam = _solve_on_rows(z, A, b, lo, hi, C, S, lam0) if S else np.zeros(m)
         tiny = 1e-13 * max(1.0, float(np.max(np.abs(lam))))
-        if np.any(lam[S] < -tiny):
+        if np.any((lam < -tiny) & ~E):
             continue
-        lam = np.maximum(lam, 0.0)
-        rep = kkt_report(z, A, b, lam, primal_from_dual(z, A, lam, lo, hi), lo, hi, C)
+        lam = np.where(E, lam, np.maximum(lam, 0.0))
+        rep = kkt_report(z, A, b, lam, primal_from_dual(z, A, lam, lo, hi), lo, hi, C, eq=E)
         if best is None or rep["worst"] < best[1]["worst"]:
             best = (lam, rep, tried + 1)
         if rep["worst"] <= kkt_tol:
@@ -387,7 +430,7 @@ def solve_coupled_exact(z, A, b, lo, hi, C, lam0=None, kkt_tol=1e-11):
 
 
 def alg2_general_projection(z, A, b, lo, hi, C, tol_B=1e-8, tol_N=1e-6, maxiter=200,
-                            single="bisect", rel_tol_B=0.0):
+                            single="bisect", rel_tol_B=0.0, eq=None):
     """Alg. 2, general multi-constraint projection, step by step.
 
     Stage 1: for each row j, Alg. 1 gives a candidate lam_j with the other rows at
@@ -397,24 +440,30 @@ def alg2_general_projection(z, A, b, lo, hi, C, tol_B=1e-8, tol_N=1e-6, maxiter=
     The candidates are tested one at a time with the others at zero (the text's
     "if one such solution is feasible"); Stage 2 starts from all candidates together.
     Stage 2: semismooth Newton (see _newton_stage2) until ||Phi||_inf <= tol_N * scale.
+    Equality rows (``eq``, Sec. 3.2.4): the stage-1 candidate of such a row is its
+    single-row root over all of R; a candidate is accepted only if every equality row
+    holds (|h_k| <= tol_N * scale_k); stage 2 uses Phi_k = h_k for them.
     Returns (lam, info dict with 'stage', 'newton_iters', 'converged').
     """
     z = np.asarray(z, dtype=np.float64)
     A = np.atleast_2d(np.asarray(A, dtype=np.float64))
     b = np.asarray(b, dtype=np.float64)
     m = A.shape[0]
+    E = eq_mask(eq, m)
     cand = np.zeros(m)
     for j in range(m):
         if single == "exact":
-            lj = solve_single_exact(z, A[j], b[j], lo, hi, C)
+            lj = solve_single_exact(z, A[j], b[j], lo, hi, C, equality=bool(E[j]))
         else:
-            lj, _ = solve_single_bisect(z, A[j], b[j], lo, hi, C, tol_B, rel_tol_B)
+            lj, _ = solve_single_bisect(z, A[j], b[j], lo, hi, C, tol_B, rel_tol_B, equality=bool(E[j]))
         cand[j] = lj
         lam = np.zeros(m)
         lam[j] = lj
         x = primal_from_dual(z, A, lam, lo, hi)
         viol = A @ x - b
-        if np.all(viol <= tol_N * row_scale(A, b, x)):
+        h = viol - 2.0 * lam / C
+        sc = row_scale(A, b, x)
+        if np.all(np.where(E, np.abs(h), viol) <= tol_N * sc):
             return lam, {"stage": 1, "accepted_row": j, "newton_iters": 0, "converged": True}
-    y, its, conv, curv = _newton_stage2(z, A, b, lo, hi, C, -cand, tol_N, maxiter)
+    y, its, conv, curv = _newton_stage2(z, A, b, lo, hi, C, -cand, tol_N, maxiter, eq=E)
     return -y, {"stage": 2, "newton_iters": its, "converged": conv, "curvature_failures": curv}

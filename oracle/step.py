@@ -78,13 +78,14 @@ def step_scalars(x, x_prev, g, g_prev, t, gval, G, p: StepParams):
 
 
 def oracle_step(x, x_prev, g, g_prev, d_prev, A, gval, G, t, p: StepParams | None = None,
-                mode="single", seg=None, projector="exact", lo=0.0, hi=1.0):
+                mode="single", seg=None, projector="exact", lo=0.0, hi=1.0, eq=None):
     """One Alg. 3 iteration.  Returns a dict with x_new, d, z, lam, b, alpha, beta, ...
 
     mode: 'single' (A is one row), 'independent' (A holds one coefficient per variable
     and seg the row offsets), 'coupled' (A is m x n).  projector: 'exact' gives the
     unique optimum (what parity is measured against); 'paper' runs Alg. 1 / Alg. 2 with
-    the paper's tolerances (what the CPU baseline times).
+    the paper's tolerances (what the CPU baseline times).  eq: boolean mask of the
+    equality rows g_j(x) = G_j (Sec. 3.2.4), linearised the same way.
     """
     p = p or StepParams()
     x = np.asarray(x, dtype=np.float64)
@@ -102,24 +103,26 @@ def oracle_step(x, x_prev, g, g_prev, d_prev, A, gval, G, t, p: StepParams | Non
         ax = np.array([a[seg[j]:seg[j + 1]] @ x[seg[j]:seg[j + 1]] for j in range(len(seg) - 1)])
         b = G - gval + ax
         if projector == "exact":
-            lam = P.solve_independent_exact(z, a, seg, b, lo, hi, p.C)
+            lam = P.solve_independent_exact(z, a, seg, b, lo, hi, p.C, eq=eq)
         else:
-            lam, _ = P.solve_independent_bisect(z, a, seg, b, lo, hi, p.C, p.tol_B)
+            lam, _ = P.solve_independent_bisect(z, a, seg, b, lo, hi, p.C, p.tol_B, eq=eq)
         x_new = P.independent_primal(z, a, seg, lam, lo, hi)
         ax_new = np.array([a[seg[j]:seg[j + 1]] @ x_new[seg[j]:seg[j + 1]] for j in range(len(seg) - 1)])
     else:
         A2 = np.atleast_2d(np.asarray(A, dtype=np.float64))
         b = G - gval + A2 @ x
+        E = P.eq_mask(eq, A2.shape[0])
         if A2.shape[0] == 1 or mode == "single":
             if projector == "exact":
-                lam = np.array([P.solve_single_exact(z, A2[0], b[0], lo, hi, p.C)])
+                lam = np.array([P.solve_single_exact(z, A2[0], b[0], lo, hi, p.C, equality=bool(E[0]))])
             else:
-                lam = np.array([P.solve_single_bisect(z, A2[0], b[0], lo, hi, p.C, p.tol_B)[0]])
+                lam = np.array([P.solve_single_bisect(z, A2[0], b[0], lo, hi, p.C, p.tol_B,
+                                                      equality=bool(E[0]))[0]])
         elif projector == "exact":
-            lam, info = P.solve_coupled_exact(z, A2, b, lo, hi, p.C)
+            lam, info = P.solve_coupled_exact(z, A2, b, lo, hi, p.C, eq=E)
         else:
             lam, info = P.alg2_general_projection(z, A2, b, lo, hi, p.C, p.tol_B, p.tol_N,
-                                                  p.maxiter_newton)
+                                                  p.maxiter_newton, eq=E)
         x_new = P.primal_from_dual(z, A2, lam, lo, hi)
         ax_new = A2 @ x_new
     nrm = float(np.linalg.norm(x_new))

@@ -96,6 +96,31 @@ def _pins(mod):
     except Exception as e:
         failed.append("bruteforce:exception:%s" % e)
     try:
+        # equality rows (Sec. 3.2.4): single row from both sides, and coupled with one
+        # equality row, against the brute-force enumeration; Alg. 2 on the coupled case
+        for seed, m, side, eq in [(901, 1, 1.0, [True]), (902, 1, -1.0, [True]), (951, 2, 1.0, [True, False]),
+                                  (953, 3, 1.0, [False, True, False]), (957, 3, -1.0, [True, False, True])]:
+            r = np.random.default_rng(seed)
+            z = r.uniform(-0.3, 1.3, 5)
+            A = r.uniform(0.2, 1.5, (m, 5))
+            b = A @ np.clip(z, 0, 1) + side * 0.3 * A.sum(axis=1) / 5
+            _, lam_bf, _ = mod.project_bruteforce(z, A, b, 0.0, 1.0, C, eq=eq)
+            lam, _ = P.solve_coupled_exact(z, A, b, 0.0, 1.0, C, eq=eq)
+            ok = np.allclose(lam, lam_bf, rtol=1e-9, atol=1e-12)
+            if m == 1:
+                l1 = P.solve_single_exact(z, A[0], b[0], 0.0, 1.0, C, equality=True)
+                lb, _ = P.solve_single_bisect(z, A[0], b[0], 0.0, 1.0, C, tol_B=1e-14, equality=True)
+                ok = ok and np.isclose(l1, lam_bf[0], rtol=1e-10, atol=1e-12) and np.isclose(lb, lam_bf[0], rtol=1e-8)
+            else:
+                l2, inf2 = P.alg2_general_projection(z, A, b, 0.0, 1.0, C, tol_N=1e-12, single="exact", eq=eq)
+                # semismooth Newton settles a 5-variable problem in a few steps
+                ok = ok and np.allclose(l2, lam_bf, rtol=1e-7, atol=1e-10) and inf2["newton_iters"] <= 20
+            if not ok:
+                failed.append("equality:%d" % seed)
+                break
+    except Exception as e:
+        failed.append("equality:exception:%s" % e)
+    try:
         rng = np.random.default_rng(5)
         z = rng.uniform(-0.3, 1.3, 200)
         A = rng.standard_normal((3, 200))
@@ -131,6 +156,14 @@ MUTANTS = [
     ("projection.py", "Af = A[:, chi]", "Af = A"),                                 # Jacobian ignores the free set
     ("projection.py", "return A @ x - np.asarray(b, dtype=np.float64) - 2.0 * lam / C",
      "return A @ x - np.asarray(b, dtype=np.float64)"),                            # dropped slack term of eq. h
+    ("projection.py", "    return -_piecewise_root(z, -a, -b, lo, hi, 2.0 / C)",
+     "    return _piecewise_root(z, -a, -b, lo, hi, 2.0 / C)"),                    # equality: mirrored root's sign
+    ("projection.py", "    if not equality or r0 == 0.0:\n        return 0.0\n    return -_piecewise_root",
+     "    if True:\n        return 0.0\n    return -_piecewise_root"),            # equality read as an inequality
+    ("projection.py", "lam = np.where(E, lam, np.maximum(lam, 0.0))", "lam = np.maximum(lam, 0.0)"),  # equality clamped
+    ("projection.py", "Dphi = np.diag(((h > 0) | E).astype(np.float64))",
+     "Dphi = np.diag((h > 0).astype(np.float64))"),                               # Alg. 2: Phi = h dropped
+    ("bruteforce.py", "if np.any(lam[Sineq] < -tol", "if np.any(lam[S] < -tol"),  # pin itself: sign test on equality rows
 ]
 
 

@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 from oracle import projection as P
+from oracle.bruteforce import project_bruteforce
 from oracle.checks import kkt_report
 from oracle.step import StepParams, oracle_step, step_scalars
 from paper_2511_13905_gb300 import inputs
@@ -296,3 +297,135 @@ def test_config4_infeasible_seed_is_regularised():
     assert out["lam"][2] > 1e9
     rep = kkt_report(out["z"], A, out["b"], out["lam"], out["x_new"], 0.0, 1.0, C)
     assert rep["worst"] < 1e-11
+
+
+# --------------------------------------------------------------------------- equality rows
+# Sec. 3.2.4: an equality row is always active; its multiplier has either sign and the
+# regularised residual a^T x - b - 2 lam / C is zero.  Pinned by the brute-force KKT
+# enumeration (equality rows in every active set, no sign condition), SciPy on the primal
+# QP with a free slack, closed forms, and the C -> infinity limit.
+
+def _eq_problem(n, m, seed, side):
+    """Tiny problem whose equality rows bind from `side` ('above': the inequality reading
+    would leave them inactive, so lam < 0; 'below': lam > 0)."""
+    rng = np.random.default_rng(seed)
+    z = rng.uniform(-0.3, 1.3, n)
+    A = rng.uniform(0.2, 1.5, (m, n)) * rng.choice([-1.0, 1.0], (m, n), p=[0.2, 0.8])
+    xc = np.clip(z, 0.0, 1.0)
+    target = A @ xc
+    b = target + (0.3 if side == "above" else -0.3) * np.abs(A).sum(axis=1) / n
+    return z, A, b
+
+
+@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("side", ["above", "below"])
+def test_equality_single_row_matches_bruteforce(seed, side):
+    z, A, b = _eq_problem(6, 1, 900 + seed, side)
+    for Cc in (C, 4.0):
+        _, lam_bf, _ = project_bruteforce(z, A, b, 0.0, 1.0, Cc, eq=[True])
+        lam = P.solve_single_exact(z, A[0], b[0], 0.0, 1.0, Cc, equality=True)
+        assert lam == pytest.approx(lam_bf[0], rel=1e-10, abs=1e-12)
+        lb, _ = P.solve_single_bisect(z, A[0], b[0], 0.0, 1.0, Cc, tol_B=1e-14, equality=True)
+        assert lb == pytest.approx(lam, rel=1e-9, abs=1e-12)
+        if side == "above" and Cc == C:
+            assert lam < 0.0  # the inequality reading would have lam = 0
+            assert P.solve_single_exact(z, A[0], b[0], 0.0, 1.0, Cc) == 0.0
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_equality_coupled_matches_bruteforce(seed):
+    rng = np.random.default_rng(950 + seed)
+    m = 2 + seed % 2
+    z, A, b = _eq_problem(5, m, 950 + seed, "above" if seed % 3 else "below")
+    eq = rng.uniform(size=m) < 0.5
+    eq[seed % m] = True
+    for Cc in (C, 3.0):
+        _, lam_bf, _ = project_bruteforce(z, A, b, 0.0, 1.0, Cc, eq=eq)
+        lam, info = P.solve_coupled_exact(z, A, b, 0.0, 1.0, Cc, eq=eq)
+        assert np.allclose(lam, lam_bf, rtol=1e-9, atol=1e-12), (lam, lam_bf, eq)
+        assert info["kkt"]["worst"] < 1e-10
+        lam2, inf2 = P.alg2_general_projection(z, A, b, 0.0, 1.0, Cc, tol_N=1e-12, single="exact", eq=eq)
+        assert np.allclose(lam2, lam_bf, rtol=1e-7, atol=1e-10), (lam2, lam_bf, inf2)
+        assert inf2["newton_iters"] <= 20  # semismooth Newton: a few steps on 5 variables
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_equality_primal_qp_matches_slsqp(seed):
+    """min ||x - z||^2 + (C/2)||s||^2 s.t. lo <= x <= hi, a_j^T x - s_j <= b_j (s_j >= 0) for
+    inequality rows and a_j^T x - s_j = b_j (s_j free) for equality rows."""
+    opt = pytest.importorskip("scipy.optimize")
+    Cc = 20.0
+    z, A, b = _eq_problem(7, 2, 980 + seed, "above")
+    eq = np.array([True, False])
+    m, n = A.shape
+
+    def f(v):
+        x, s = v[:n], v[n:]
+        return float((x - z) @ (x - z) + 0.5 * Cc * s @ s)
+
+    cons = [{"type": "eq", "fun": lambda v: A[0] @ v[:n] - v[n] - b[0]},
+            {"type": "ineq", "fun": lambda v: b[1] + v[n + 1] - A[1] @ v[:n]}]
+    bounds = [(0.0, 1.0)] * n + [(None, None), (0.0, None)]
+    res = opt.minimize(f, np.concatenate([np.clip(z, 0, 1), np.zeros(m)]), method="SLSQP", bounds=bounds,
+                       constraints=cons, options={"ftol": 1e-15, "maxiter": 500})
+    lam, _ = P.solve_coupled_exact(z, A, b, 0.0, 1.0, Cc, eq=eq)
+    x = P.primal_from_dual(z, A, lam, 0.0, 1.0)
+    assert np.allclose(x, res.x[:n], atol=2e-6)
+    assert 2.0 * lam[0] / Cc == pytest.approx(res.x[n], abs=2e-6)  # slack s = 2 lam / C, either sign
+
+
+def test_equality_closed_forms():
+    rng = np.random.default_rng(11)
+    n = 50
+    a = rng.uniform(0.5, 1.5, n)
+    z = rng.uniform(0.4, 0.6, n)
+    # all free: lam = (a^T z - b) / (|a|^2 + 2/C), here negative
+    b = float(a @ z) + 0.01
+    lam = P.solve_single_exact(z, a, b, 0.0, 1.0, C, equality=True)
+    assert lam == pytest.approx((a @ z - b) / (a @ a + 2.0 / C), rel=1e-12)
+    assert lam < 0.0
+    # unreachable from above (b beyond a^T hi): every x at the row-maximising bound and
+    # lam = (C/2)(S_max - b)
+    b2 = float(a.sum()) + 3.0
+    lam2 = P.solve_single_exact(z, a, b2, 0.0, 1.0, C, equality=True)
+    assert lam2 == pytest.approx(0.5 * C * (a.sum() - b2), rel=1e-10)
+    # exactly met at lam = 0
+    b3 = float(a @ np.clip(z, 0, 1))
+    assert P.solve_single_exact(z, a, b3, 0.0, 1.0, C, equality=True) == 0.0
+
+
+def test_equality_met_exactly_in_the_limit():
+    """C -> infinity (Sec. 3.2.3): a feasible equality row holds to rounding, and the
+    result is the Euclidean projection onto box and hyperplane (the same at 1e12 and 1e15)."""
+    z, A, b = _eq_problem(400, 1, 990, "above")
+    l1 = P.solve_single_exact(z, A[0], b[0], 0.0, 1.0, 1e12, equality=True)
+    l2 = P.solve_single_exact(z, A[0], b[0], 0.0, 1.0, 1e15, equality=True)
+    x1 = P.primal_from_dual(z, A, [l1], 0.0, 1.0)
+    x2 = P.primal_from_dual(z, A, [l2], 0.0, 1.0)
+    assert abs(float(A[0] @ x1) - b[0]) < 1e-9 * abs(b[0])
+    assert np.allclose(x1, x2, atol=1e-9)
+
+
+def test_equality_with_nonnegative_multiplier_equals_the_inequality():
+    """When the equality row's multiplier comes out >= 0 the inequality reading has the
+    same optimum (an active inequality)."""
+    for seed in range(6):
+        z, A, b = _eq_problem(30, 2, 1000 + seed, "below")
+        lam_e, _ = P.solve_coupled_exact(z, A, b, 0.0, 1.0, C, eq=[True, True])
+        if np.all(lam_e >= 0):
+            lam_i, _ = P.solve_coupled_exact(z, A, b, 0.0, 1.0, C)
+            assert np.allclose(lam_e, lam_i, rtol=1e-9, atol=1e-12)
+
+
+def test_equality_rows_in_a_full_step():
+    """oracle_step with equality rows: independent rows (one of them an equality) and a
+    coupled pair, against the same projections written out directly."""
+    cfg = inputs.config3(dims=(10, 8, 6), materials=2)
+    eq = [True, False]
+    ref = oracle_step(cfg["x"], cfg["x_prev"], cfg["g"], cfg["g_prev"], cfg["d_prev"], cfg["A"],
+                      cfg["gval"], cfg["G"], cfg["t"], mode="independent", seg=cfg["seg"], eq=eq)
+    lam = P.solve_independent_exact(ref["z"], cfg["A"].astype(np.float64), cfg["seg"], ref["b"], 0.0, 1.0, C, eq=eq)
+    assert np.allclose(ref["lam"], lam)
+    seg = cfg["seg"]
+    ax = float(cfg["A"][seg[0]:seg[1]].astype(np.float64) @ ref["x_new"][seg[0]:seg[1]])
+    assert abs(ax - ref["b"][0] - 2.0 * ref["lam"][0] / C) < 1e-9 * abs(ref["b"][0])
