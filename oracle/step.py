@@ -43,13 +43,18 @@ class StepParams:
     maxiter_newton: int = 200
 
 
-def step_scalars(x, x_prev, g, g_prev, t, gval, G, p: StepParams):
-    """alpha_t and beta_t of Alg. 3 (eq. final_alpha, eq. alpha, eq. CG) and which branch set alpha."""
+def step_scalars(x, x_prev, g, g_prev, t, gval, G, p: StepParams, eq=None):
+    """alpha_t and beta_t of Alg. 3 (eq. final_alpha, eq. alpha, eq. CG) and which branch set alpha.
+
+    The fallback trigger measures the violation g_j - G_j of an inequality row and
+    |g_j - G_j| of an equality row (Sec. 3.2.4: the row must hold either way)."""
     x = np.asarray(x, dtype=np.float64)
     g = np.asarray(g, dtype=np.float64)
     gnorm_inf = float(np.max(np.abs(g))) if g.size else 0.0
     fallback_alpha = p.alpha_max if gnorm_inf == 0.0 else min(p.alpha_max, p.alpha_fallback / gnorm_inf)
-    viol = float(np.max(np.maximum(np.asarray(gval, dtype=np.float64) - np.asarray(G, dtype=np.float64), 0.0)))
+    dg = np.atleast_1d(np.asarray(gval, dtype=np.float64) - np.asarray(G, dtype=np.float64))
+    E = P.eq_mask(eq, dg.size)
+    viol = float(np.max(np.where(E, np.abs(dg), np.maximum(dg, 0.0))))
     if t == 0 or (t >= p.t_warmup and viol > p.tol_N):
         alpha, branch = fallback_alpha, "fallback"
     else:
@@ -90,7 +95,7 @@ def oracle_step(x, x_prev, g, g_prev, d_prev, A, gval, G, t, p: StepParams | Non
     p = p or StepParams()
     x = np.asarray(x, dtype=np.float64)
     g = np.asarray(g, dtype=np.float64)
-    sc = step_scalars(x, x_prev, g, g_prev, t, gval, G, p)
+    sc = step_scalars(x, x_prev, g, g_prev, t, gval, G, p, eq=eq)
     alpha, beta = sc["alpha"], sc["beta"]
     d = -g if t == 0 else -g + beta * np.asarray(d_prev, dtype=np.float64)
     z = x + p.omega * alpha * d

@@ -114,6 +114,7 @@ extern "C" pgdto_status pgdto_params_default(pgdto_params* p) {
     p->fault_inject = 0;
     p->engine = 0;
     p->cluster_elems = 0;
+    p->eq_mask = 0;
     return PGDTO_OK;
 }
 
@@ -146,7 +147,8 @@ static bool params_ok(const pgdto_params& p) {
     return p.C > 0 && isfinite(p.C) && p.alpha_max > 0 && p.alpha_fallback > 0 && p.tol_N >= 0 && p.omega > 0 &&
            p.eps_alpha >= 0 && p.tol_lambda > 0 && p.tol_lambda < 1e-2 && p.t_warmup >= 0 &&
            p.maxiter_newton >= 1 && p.max_passes >= 1 && p.max_passes <= 100000 && p.barrier_timeout_ms >= 1 &&
-           (p.fault_inject == 0 || p.fault_inject == 1) && p.engine >= 0 && p.engine <= 2 && p.cluster_elems >= 0;
+           (p.fault_inject == 0 || p.fault_inject == 1) && p.engine >= 0 && p.engine <= 2 && p.cluster_elems >= 0 &&
+           p.eq_mask >= 0 && p.eq_mask < 16;
 }
 
 extern "C" pgdto_status pgdto_create(pgdto_handle** out, int64_t n, int m, const int64_t* seg_offsets, float lo,
@@ -162,6 +164,7 @@ extern "C" pgdto_status pgdto_create(pgdto_handle** out, int64_t n, int m, const
         pgdto_params_default(&p);
     }
     if (!params_ok(p)) return PGDTO_ERR_ARG;
+    if (p.eq_mask >> m) return PGDTO_ERR_ARG;  // equality flags only for existing rows
     pgdto_mode mode = p.mode;
     if (mode == PGDTO_AUTO) mode = (m == 1) ? PGDTO_SINGLE : (seg_offsets ? PGDTO_INDEPENDENT : PGDTO_COUPLED);
     if (mode == PGDTO_SINGLE && m != 1) return PGDTO_ERR_ARG;
@@ -379,6 +382,7 @@ static void fill_seg_args(pgdto_handle* h, bool proj, float* x, const float* g, 
     a.timeout_cycles = h->timeout_cycles;
     a.ws = (SegWork*)h->work;
     a.info_out = h->dev_info;
+    a.eq_mask = h->p.eq_mask;
     // warm start from the previous step's lam, still in the handle's report on the device
     a.lam_prev = (!proj && h->warm)
                      ? reinterpret_cast<const double*>(reinterpret_cast<const char*>(h->dev_info) +
@@ -424,6 +428,7 @@ static pgdto_status launch(pgdto_handle* h, bool proj, float* x, const float* g,
         a.fault_inject = h->p.fault_inject;
         a.timeout_cycles = h->timeout_cycles;
         a.ws = (CoupledWork*)h->work;
+        a.eq_mask = h->p.eq_mask;
         e = launch_coupled(a, h->blocks, h->stream);
     } else {
         SegArgs a;
@@ -449,7 +454,8 @@ extern "C" pgdto_status pgdto_step(pgdto_handle* h, float* x, const float* grad_
     for (int j = 0; j < h->m; ++j) {
         if (!(isfinite(g_val[j]) && isfinite(G[j]))) return PGDTO_ERR_NONFINITE;
         bconst[j] = G[j] - g_val[j];
-        viol = fmax(viol, g_val[j] - G[j]);
+        // Alg. 3's fallback trigger: violation g - G of an inequality, |g - G| of an equality
+        viol = fmax(viol, ((h->p.eq_mask >> j) & 1) ? fabs(g_val[j] - G[j]) : g_val[j] - G[j]);
     }
     // Alg. 3: fallback step at t = 0, or after the warm-up when a constraint is violated
     const bool fallback = h->t == 0 || (h->t >= h->p.t_warmup && viol > h->p.tol_N);
@@ -645,7 +651,7 @@ extern "C" pgdto_status pgdto_step_many(int count, pgdto_handle* const* hs, floa
                 return PGDTO_ERR_NONFINITE;
             }
             bconst[j] = gg - gv;
-            viol = fmax(viol, gv - gg);
+            viol = fmax(viol, ((h->p.eq_mask >> j) & 1) ? fabs(gv - gg) : gv - gg);
         }
         const bool fallback = h->t == 0 || (h->t >= h->p.t_warmup && viol > h->p.tol_N);
         fill_seg_args(h, false, x[k], grad_f[k], A[k], bconst, nullptr, nullptr, fallback, args[k]);

@@ -64,6 +64,7 @@ struct NewtonState {
     int how;                // 3 if an iteration limit was hit
     int ls_expand;          // 1: line-search bracket open on the right, 2: closed by the cap
     int stall;              // evaluations in a row without progress at the rounding floor
+    int eq_mask;            // equality rows (always in the working set, never clamped or capped)
     int trial;              // lam is the full Newton step from base, not yet accepted
     int pad;
 };
@@ -83,7 +84,8 @@ size_t coupled_work_ctrl_bytes() { return sizeof(GridCtrl); }
 DeviceInfo* coupled_work_info(CoupledWork* ws) { return &ws->info; }
 
 // sc.tot layout of each pass
-//   B:   4 per row (a^T x_t, a^T clip(z), free curvature at 0, S_min), max per row
+//   B:   5 per row (a^T x_t, a^T clip(z), free curvature at 0, S_min, S_max), 2 maxima
+//        per row (the upper saturation bound, minus the lower one)
 //   S1:  2K per row
 //   F:   m per candidate row (sums of every row at that candidate)
 //   E:   [0, m) h sums a_j^T x, [m, 2m) sum |a_j x|, [2m, 2m + 10) J upper triangle
@@ -96,7 +98,8 @@ __device__ __forceinline__ int jidx(int j, int k) {  // row-major upper-triangle
 
 // ----------------------------------------------------------------------- scalar updates
 
-// Phase B: inputs of the single-row searches (Alg. 2 stage 1), as for a single row.
+// Phase B: inputs of the single-row searches (Alg. 2 stage 1), as for a single row; an
+// equality row (Sec. 3.2.4) with r(0) < 0 searches below 0 (see the single-row kernel).
 template <int M>
 __device__ void cupd_after_trial(const CoupledArgs& a, const BlockScratch& sc, CoupledWork* ws) {
     const int lane = threadIdx.x, j = lane >> 3, k = lane & 7;
@@ -105,36 +108,55 @@ __device__ void cupd_after_trial(const CoupledArgs& a, const BlockScratch& sc, C
     const bool row = j < M;
     const int jj = row ? j : 0;
     const double two_c = 2.0 / a.C;
-    const double ax = a.proj ? 0.0 : df_to_double(sc.tot[4 * jj + 0]);
-    const double r0s = df_to_double(sc.tot[4 * jj + 1]);
-    const double sf = df_to_double(sc.tot[4 * jj + 2]);
-    const double smin = df_to_double(sc.tot[4 * jj + 3]);
-    const double lsat = (double)sc.totmax[jj];
-    const bool finite = isfinite(ax) && isfinite(r0s) && isfinite(sf) && isfinite(smin);
+    const double ax = a.proj ? 0.0 : df_to_double(sc.tot[5 * jj + 0]);
+    const double r0s = df_to_double(sc.tot[5 * jj + 1]);
+    const double sf = df_to_double(sc.tot[5 * jj + 2]);
+    const double smin = df_to_double(sc.tot[5 * jj + 3]);
+    const double smax = df_to_double(sc.tot[5 * jj + 4]);
+    const double lsat = (double)sc.totmax[2 * jj];
+    const double lneg = -(double)sc.totmax[2 * jj + 1];
+    const bool eq = (a.eq_mask >> jj) & 1;
+    const bool finite = isfinite(ax) && isfinite(r0s) && isfinite(sf) && isfinite(smin) && isfinite(smax);
     const double b = a.bconst[jj] + ax;
     const double r0 = r0s - b;
-    float Hf = (float)(lsat * (1.0 + 1e-5) + 1e-30);
-    if (!((double)Hf > 0.0)) Hf = FLT_MIN;
-    const double H = (double)Hf;
-    const double rH = smin - b - two_c * H;
-    const bool inactive = !(r0 > 0.0);
-    const bool closed = !inactive && rH > 0.0;
-    const bool search = row && finite && !inactive && !closed;
-    const double SL = sf + two_c;
+    const bool up = r0 > 0.0;
+    const bool down = eq && r0 < 0.0;
+    double L, rL, SLs, H, rH, SHs;
+    if (down) {
+        float Lf = (float)(lneg * (1.0 + 1e-5) - 1e-30);
+        if (!((double)Lf < 0.0)) Lf = -FLT_MIN;
+        L = (double)Lf;
+        rL = smax - b - two_c * L;
+        SLs = two_c;
+        H = 0.0;
+        rH = r0;
+        SHs = sf + two_c;
+    } else {
+        float Hf = (float)(lsat * (1.0 + 1e-5) + 1e-30);
+        if (!((double)Hf > 0.0)) Hf = FLT_MIN;
+        L = 0.0;
+        rL = r0;
+        SLs = sf + two_c;
+        H = (double)Hf;
+        rH = smin - b - two_c * H;
+        SHs = two_c;
+    }
+    const bool closed = down ? rL < 0.0 : (up && rH > 0.0);
+    const bool search = row && finite && (up || down) && !closed;
     double q = 0.0;
-    if (k == 0) q = r0 / SL;
-    else if (k == 1) q = rH / two_c;
-    const double NL = __shfl_sync(kFull, q, lane & ~7);
+    if (k == 0) q = rL / SLs;
+    else if (k == 1) q = rH / SHs;
+    const double NL = L + __shfl_sync(kFull, q, lane & ~7);
     const double NH = H + __shfl_sync(kFull, q, (lane & ~7) + 1);
-    const float p = next_point(lane, 0.0, r0, H, rH, NL, NH);
+    const float p = next_point(lane, L, rL, H, rH, NL, NH);
     if (row && k == 0) {
         ws->info.b[j] = b;
         rows[j].reg = two_c;
         if (search) {
-            store_row(&rows[j], b, 0.0, r0, SL, H, rH, two_c, 0.0, 0.0, 1, 0, 2);
+            store_row(&rows[j], b, L, rL, SLs, H, rH, SHs, 0.0, 0.0, 1, 0, 2);
             bc->active[j] = 1;
         } else if (closed) {
-            const double lam = 0.5 * a.C * (smin - b);
+            const double lam = 0.5 * a.C * ((down ? smax : smin) - b);
             store_row(&rows[j], b, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, lam, 0.0, 0, 0, 1);
             publish_lambda(bc, j, lam);
         } else {
@@ -159,6 +181,7 @@ __device__ void cupd_after_trial(const CoupledArgs& a, const BlockScratch& sc, C
         nt->trial = 0;
         nt->phi = INFINITY;
         nt->tol = 1e-8;  // relative tolerance of the line search (the next Newton step corrects)
+        nt->eq_mask = a.eq_mask;
     }
 }
 
@@ -170,7 +193,7 @@ __device__ void cupd_plan_feasibility(CoupledWork* ws) {
     if (threadIdx.x != 0) return;
     int nc = 0;
     for (int j = 0; j < M; ++j)
-        if (rows[j].lam > 0.0) bc->cand_row[nc++] = j;
+        if (rows[j].lam != 0.0) bc->cand_row[nc++] = j;  // equality rows may be negative
     bc->ncand = nc;
     volatile NewtonState* nt = &ws->nt;
     for (int j = 0; j < M; ++j) {
@@ -214,8 +237,10 @@ __device__ void cupd_after_feasibility(const CoupledArgs& a, const BlockScratch&
             if (k == j) continue;  // row j holds at its own root by construction
             const double r = df_to_double(sc.tot[c * M + k]) - rows[k].b;
             // admitted when the row holds to 1e-9 of its magnitude (tighter than tol_N so the
-            // accepted point is the regularised optimum to the parity tolerance)
-            if (!(r <= 1e-9 * fmax(1.0, fabs(rows[k].b)))) ok = false;
+            // accepted point is the regularised optimum to the parity tolerance); an
+            // equality row must hold from both sides
+            const double rr = ((a.eq_mask >> k) & 1) ? fabs(r) : r;
+            if (!(rr <= 1e-9 * fmax(1.0, fabs(rows[k].b)))) ok = false;
         }
         if (ok) accepted = j;
     }
@@ -240,9 +265,9 @@ __device__ void cstart_line_search(CoupledWork* ws) {
     volatile RowState* ls = &ws->ls;
     for (int j = 0; j < M; ++j) nt->lam[j] = nt->base[j];
     set_iterate(bc, nt, M);
-    double cap = INFINITY;
+    double cap = INFINITY;  // the step at which an inequality multiplier reaches 0
     for (int j = 0; j < M; ++j)
-        if (nt->d[j] < 0.0) cap = fmin(cap, nt->base[j] / (-nt->d[j]));
+        if (nt->d[j] < 0.0 && !((nt->eq_mask >> j) & 1)) cap = fmin(cap, nt->base[j] / (-nt->d[j]));
     nt->cap = cap;
     ls->b = nt->base_dtb;
     ls->reg = nt->base_dd;
@@ -291,7 +316,7 @@ __device__ void cupd_after_eval(const CoupledArgs& a, const BlockScratch& sc, Co
         h[j] = df_to_double(sc.tot[j]) - rows[j].b - two_c * nt->lam[j];
         scale[j] = fmax(1.0, fmax(fabs(rows[j].b), df_to_double(sc.tot[M + j])));
         const double tol = 1e-9 * scale[j];
-        if (nt->lam[j] > 0.0) {
+        if (nt->lam[j] > 0.0 || ((a.eq_mask >> j) & 1)) {
             if (!(fabs(h[j]) <= tol)) conv = false;
         } else if (!(h[j] <= tol)) {
             conv = false;
@@ -303,7 +328,8 @@ __device__ void cupd_after_eval(const CoupledArgs& a, const BlockScratch& sc, Co
         return;
     }
     double phi = 0.0;
-    for (int j = 0; j < M; ++j) phi = fmax(phi, (nt->lam[j] > 0.0 ? fabs(h[j]) : fmax(h[j], 0.0)) / scale[j]);
+    for (int j = 0; j < M; ++j)
+        phi = fmax(phi, (nt->lam[j] > 0.0 || ((a.eq_mask >> j) & 1) ? fabs(h[j]) : fmax(h[j], 0.0)) / scale[j]);
     if (nt->trial) {
         if (!(phi < nt->base_phi * (1.0 - 1e-4) || phi <= 1e-8)) {
             cstart_line_search<M>(ws);  // the full step did not reduce the residual
@@ -321,7 +347,7 @@ __device__ void cupd_after_eval(const CoupledArgs& a, const BlockScratch& sc, Co
     if (stall >= 2) conv = true;
     int S[M], ns = 0;
     for (int j = 0; j < M; ++j)
-        if (nt->lam[j] > 0.0 || h[j] > 0.0) S[ns++] = j;
+        if (nt->lam[j] > 0.0 || h[j] > 0.0 || ((a.eq_mask >> j) & 1)) S[ns++] = j;  // equality rows: always
     if (conv || ns == 0) {
         bc->mode = kModeDone;
         return;
@@ -365,7 +391,7 @@ __device__ void cupd_after_eval(const CoupledArgs& a, const BlockScratch& sc, Co
         bool dropped = false;
         for (int p = 0; p < ns; ++p) {
             const int j = S[p];
-            if (nt->lam[j] <= 0.0 && d[j] < 0.0) dropped = true;
+            if (nt->lam[j] <= 0.0 && d[j] < 0.0 && !((a.eq_mask >> j) & 1)) dropped = true;
             else S[keep++] = j;
         }
         if (!dropped || keep == 0) break;
@@ -394,7 +420,8 @@ __device__ void cupd_after_eval(const CoupledArgs& a, const BlockScratch& sc, Co
     nt->base_dtb = dtb;
     nt->base_dd = two_c * dd;
     // the full Newton step, kept in lam >= 0, is evaluated by the next E pass
-    for (int j = 0; j < M; ++j) nt->lam[j] = fmax(nt->lam[j] + d[j], 0.0);
+    for (int j = 0; j < M; ++j)
+        nt->lam[j] = ((a.eq_mask >> j) & 1) ? nt->lam[j] + d[j] : fmax(nt->lam[j] + d[j], 0.0);
     set_iterate(bc, nt, M);
     nt->trial = 1;
     bc->mode = kModeEval;
@@ -472,8 +499,10 @@ __device__ void cupd_after_line(const CoupledArgs& a, const BlockScratch& sc, Co
     for (int j = 0; j < M; ++j) {
         const double dj = nt->d[j];
         double v = nt->lam[j] + g * dj;
-        if (v < 0.0 || (at_cap && dj < 0.0 && nt->lam[j] / (-dj) <= cap * (1.0 + 1e-12))) v = fmax(v, 0.0);
-        if (at_cap && dj < 0.0 && nt->lam[j] / (-dj) <= cap * (1.0 + 1e-12)) v = 0.0;
+        if (!((a.eq_mask >> j) & 1)) {  // an equality multiplier keeps its sign
+            if (v < 0.0 || (at_cap && dj < 0.0 && nt->lam[j] / (-dj) <= cap * (1.0 + 1e-12))) v = fmax(v, 0.0);
+            if (at_cap && dj < 0.0 && nt->lam[j] / (-dj) <= cap * (1.0 + 1e-12)) v = 0.0;
+        }
         nt->lam[j] = v;
     }
     nt->iters = nt->iters + 1;
@@ -641,13 +670,14 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
         const float ch = a.proj ? 0.0f : bc.c_hi, cl = a.proj ? 0.0f : bc.c_lo;
         const float bh = a.proj ? 0.0f : bc.beta_hi, bl = a.proj ? 0.0f : bc.beta_lo;
         const bool first = a.t == 0;
-        AccSplit<4 * M, 0> acc;
+        AccSplit<5 * M, 0> acc;
         acc.init();
-        float lsat[M];
+        float mx[2 * M];  // per row: the upper saturation bound, minus the lower one
         // a_j^T x_t enters b_j: exact products, hi parts summed with TwoSum, the rest in bl
         float bsh[M], bsl[M];
 #pragma unroll
-        for (int j = 0; j < M; ++j) lsat[j] = bsh[j] = bsl[j] = 0.0f;
+        for (int j = 0; j < M; ++j) mx[2 * j] = mx[2 * j + 1] = bsh[j] = bsl[j] = 0.0f;
+        const int eqm = a.eq_mask;
         auto rowsum = [&](float z, const float (&av)[M], float x) {
             const bool fr = z >= lo && z <= hi;
             const float xc = clampf(z, lo, hi);
@@ -658,10 +688,14 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
                 const DF t = two_sum(bsh[j], ph);
                 bsh[j] = t.hi;
                 bsl[j] = __fadd_rn(bsl[j], __fadd_rn(t.lo, fmaf(aj, x, -ph)));
-                acc.f[4 * j + 1] = fmaf(aj, xc, acc.f[4 * j + 1]);
-                acc.f[4 * j + 2] = fr ? fmaf(aj, aj, acc.f[4 * j + 2]) : acc.f[4 * j + 2];
-                acc.f[4 * j + 3] += aj > 0.0f ? aj * lo : (aj < 0.0f ? aj * hi : 0.0f);
-                if (aj != 0.0f) lsat[j] = fmaxf(lsat[j], (aj > 0.0f ? z - lo : z - hi) / aj);
+                acc.f[5 * j + 1] = fmaf(aj, xc, acc.f[5 * j + 1]);
+                acc.f[5 * j + 2] = fr ? fmaf(aj, aj, acc.f[5 * j + 2]) : acc.f[5 * j + 2];
+                acc.f[5 * j + 3] += aj > 0.0f ? aj * lo : (aj < 0.0f ? aj * hi : 0.0f);
+                acc.f[5 * j + 4] += aj > 0.0f ? aj * hi : (aj < 0.0f ? aj * lo : 0.0f);
+                if (aj != 0.0f) {
+                    mx[2 * j] = fmaxf(mx[2 * j], (aj > 0.0f ? z - lo : z - hi) / aj);
+                    if ((eqm >> j) & 1) mx[2 * j + 1] = fmaxf(mx[2 * j + 1], -(aj > 0.0f ? z - hi : z - lo) / aj);
+                }
             }
         };
         // d_t and z = x + c d_t in double-float (as in the single-row kernel)
@@ -750,9 +784,9 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
             });
         acc.fold();
 #pragma unroll
-        for (int j = 0; j < M; ++j) acc.d[4 * j] = df_add(acc.d[4 * j], fast_two_sum(bsh[j], bsl[j]));
-        block_reduce<4 * M, M>(acc.d, lsat, sc);
-        if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 4 * M, M, a.timeout_cycles, [&](BlockScratch& s) {
+        for (int j = 0; j < M; ++j) acc.d[5 * j] = df_add(acc.d[5 * j], fast_two_sum(bsh[j], bsl[j]));
+        block_reduce<5 * M, 2 * M>(acc.d, mx, sc);
+        if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 5 * M, 2 * M, a.timeout_cycles, [&](BlockScratch& s) {
                 cupd_after_trial<M>(a, s, ws);
                 __syncwarp();
                 if (threadIdx.x == 0) {

@@ -48,6 +48,7 @@ struct SegArgs {
     DeviceInfo* info_out; // cluster engine: where this problem's report goes
     int sm_elems;         // shared-memory residency: floats per array (z_hi, z_lo, a); 0 = off
     const double* lam_prev;  // warm start: the previous step's lam per row (device), or null
+    int eq_mask;          // bit j: row j is an equality (always active, lam_j of either sign)
 };
 
 // Shared-memory residency of a CTA's share of a problem.  The CTA's chunk of row j is
@@ -120,6 +121,7 @@ struct CoupledArgs {
     int fault_inject;
     long long timeout_cycles;
     CoupledWork* ws;
+    int eq_mask;          // bit j: row j is an equality (always active, lam_j of either sign)
 };
 
 // Workspace management (sizes in bytes, device-resident, zero-initialised by the host).

@@ -81,6 +81,9 @@ __device__ __forceinline__ void publish_lambda(volatile SegBcast* bc, int j, dou
 
 // After phase B: feasibility at lam = 0, bracket [0, H] (Alg. 1), closed form when the row
 // is violated even with every variable at its row-minimising bound (regularised root).
+// An equality row (Sec. 3.2.4) with r(0) < 0 binds from below: its root is negative, in
+// [L, 0] with L the lowest breakpoint (every variable at its row-maximising bound below
+// it), or (C/2)(S_max - b) when even that point leaves r < 0.
 __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, SegState* ws) {
     const int lane = threadIdx.x, j = lane >> 3, k = lane & 7;
     volatile SegBcast* bc = &ws->bc;
@@ -88,38 +91,57 @@ __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, Seg
     const bool row = j < a.nrows;
     const int jj = row ? j : 0;
     const double two_c = 2.0 / a.C;  // one division, shared by every lane
-    const double ax = a.proj ? 0.0 : df_to_double(sc.tot[4 * jj + 0]);
-    const double r0s = df_to_double(sc.tot[4 * jj + 1]);
-    const double sf = df_to_double(sc.tot[4 * jj + 2]);
-    const double smin = df_to_double(sc.tot[4 * jj + 3]);
-    const double lsat = (double)sc.totmax[jj];
-    const bool finite = isfinite(ax) && isfinite(r0s) && isfinite(sf) && isfinite(smin);
+    const double ax = a.proj ? 0.0 : df_to_double(sc.tot[5 * jj + 0]);
+    const double r0s = df_to_double(sc.tot[5 * jj + 1]);
+    const double sf = df_to_double(sc.tot[5 * jj + 2]);
+    const double smin = df_to_double(sc.tot[5 * jj + 3]);
+    const double smax = df_to_double(sc.tot[5 * jj + 4]);
+    const double lsat = (double)sc.totmax[2 * jj];
+    const double lneg = -(double)sc.totmax[2 * jj + 1];
+    const bool eq = (a.eq_mask >> jj) & 1;
+    const bool finite = isfinite(ax) && isfinite(r0s) && isfinite(sf) && isfinite(smin) && isfinite(smax);
     const double b = a.bconst[jj] + ax;
     const double r0 = r0s - b;
-    float Hf = (float)(lsat * (1.0 + 1e-5) + 1e-30);
-    if (!((double)Hf > 0.0)) Hf = FLT_MIN;
-    const double H = (double)Hf;
-    const double rH = smin - b - two_c * H;
-    const bool inactive = !(r0 > 0.0);
-    const bool closed = !inactive && rH > 0.0;
-    const bool search = row && finite && !inactive && !closed;
-    const double SL = sf + two_c;
+    const bool up = r0 > 0.0;
+    const bool down = eq && r0 < 0.0;
+    double L, rL, SLs, H, rH, SHs;
+    if (down) {
+        float Lf = (float)(lneg * (1.0 + 1e-5) - 1e-30);
+        if (!((double)Lf < 0.0)) Lf = -FLT_MIN;
+        L = (double)Lf;
+        rL = smax - b - two_c * L;
+        SLs = two_c;
+        H = 0.0;
+        rH = r0;
+        SHs = sf + two_c;
+    } else {
+        float Hf = (float)(lsat * (1.0 + 1e-5) + 1e-30);
+        if (!((double)Hf > 0.0)) Hf = FLT_MIN;
+        L = 0.0;
+        rL = r0;
+        SLs = sf + two_c;
+        H = (double)Hf;
+        rH = smin - b - two_c * H;
+        SHs = two_c;
+    }
+    const bool closed = down ? rL < 0.0 : (up && rH > 0.0);
+    const bool search = row && finite && (up || down) && !closed;
     // every lane of the group computes the row's first Newton quotients
     double q = 0.0;
-    if (k == 0) q = r0 / SL;
-    else if (k == 1) q = rH / two_c;
-    const double NL = __shfl_sync(kFull, q, lane & ~7);
+    if (k == 0) q = rL / SLs;
+    else if (k == 1) q = rH / SHs;
+    const double NL = L + __shfl_sync(kFull, q, lane & ~7);
     const double NH = H + __shfl_sync(kFull, q, (lane & ~7) + 1);
-    const double lp = a.lam_prev ? a.lam_prev[jj] : -1.0;
-    const float p = next_point_warm(lane, 0.0, r0, H, rH, NL, NH, lp);
+    const double lp = a.lam_prev ? a.lam_prev[jj] : (down ? 1.0 : -1.0);
+    const float p = next_point_warm(lane, L, rL, H, rH, NL, NH, lp);
     if (row && k == 0) {
         ws->info.b[j] = b;
         rows[j].reg = two_c;
         if (search) {
-            store_row(&rows[j], b, 0.0, r0, SL, H, rH, two_c, 0.0, 0.0, 1, 0, 2);
+            store_row(&rows[j], b, L, rL, SLs, H, rH, SHs, 0.0, 0.0, 1, 0, 2);
             bc->active[j] = 1;
         } else if (closed) {
-            const double lam = 0.5 * a.C * (smin - b);
+            const double lam = 0.5 * a.C * ((down ? smax : smin) - b);
             store_row(&rows[j], b, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, lam, 0.0, 0, 0, 1);
             publish_lambda(bc, j, lam);
         } else {
@@ -164,16 +186,17 @@ __device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegState*
     for (int j = 0; j < a.nrows; ++j) {
         const double ax = df_to_double(sc.tot[j]);
         double lam = rows[j].lam;
-        if (rows[j].how == 2 && lam > 0.0) {
+        const bool eqj = (a.eq_mask >> j) & 1;
+        if (rows[j].how == 2 && (lam > 0.0 || eqj)) {
             const double reg = rows[j].reg;
             const double S = df_to_double(sc.tot[a.nrows + j]) + reg;
             const double r = ax - rows[j].b - reg * lam;
             const double dl = S > 0.0 ? r / S : 0.0;
             const double w = (double)rows[j].fH - (double)rows[j].fL;
             const double noise = S > 0.0 ? 1e-6 * (fabs(rows[j].b) + fabs(ax)) / S : 0.0;
-            if (fabs(dl) <= fmax(4.0 * w, noise) && lam + dl > 0.0) {
+            if (fabs(dl) <= fmax(4.0 * w, noise) && (lam + dl > 0.0 || eqj)) {
                 lam += dl;
-                if (fabs(dl) > 1e-7 * lam && rows[j].nrefine < 8) {
+                if (fabs(dl) > 1e-7 * fabs(lam) && rows[j].nrefine < 8) {
                     rows[j].nrefine = rows[j].nrefine + 1;
                     rows[j].lam = lam;
                     publish_lambda(bc, j, lam);
@@ -381,9 +404,10 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
         const bool first = a.t == 0;
         int roff = 0;
         for (int j = 0; j < a.nrows; ++j) {
-            AccSplit<4, 0> acc;
+            AccSplit<5, 0> acc;
             acc.init();
-            float lsat = 0.0f;
+            float lsat = 0.0f, lnegm = 0.0f;
+            const bool eqj = (a.eq_mask >> j) & 1;
             int64_t cb, ce;
             block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
             const int64_t rb = cb & ~int64_t(3);
@@ -406,9 +430,11 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 r0l = __fadd_rn(r0l, __fadd_rn(u.lo, fmaf(av, xc, -q) + (fr ? av * zl : 0.0f)));
                 acc.f[2] = fr ? fmaf(av, av, acc.f[2]) : acc.f[2];
                 acc.f[3] += av > 0.0f ? av * lo : (av < 0.0f ? av * hi : 0.0f);
+                acc.f[4] += av > 0.0f ? av * hi : (av < 0.0f ? av * lo : 0.0f);
                 if (av != 0.0f) {
                     const float bp = (av > 0.0f ? z - lo : z - hi) / av;
                     lsat = fmaxf(lsat, bp);
+                    if (eqj) lnegm = fmaxf(lnegm, -(av > 0.0f ? z - hi : z - lo) / av);
                 }
             };
             if (a.proj) {
@@ -508,10 +534,10 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
             acc.fold();
             acc.d[0] = df_add(acc.d[0], fast_two_sum(axh, axl));
             acc.d[1] = df_add(acc.d[1], fast_two_sum(r0h, r0l));
-            float mx[1] = {lsat};
-            block_reduce<4, 1>(acc.d, mx, sc, 4 * j, j);
+            float mx[2] = {lsat, lnegm};
+            block_reduce<5, 2>(acc.d, mx, sc, 5 * j, 2 * j);
         }
-        if (!sy.reduce(sc, 4 * a.nrows, a.nrows, [&](BlockScratch& s, SegState* st) { update_after_trial(a, s, st); }))
+        if (!sy.reduce(sc, 5 * a.nrows, 2 * a.nrows, [&](BlockScratch& s, SegState* st) { update_after_trial(a, s, st); }))
             return;
         sy.fetch(bc);
         if (bc.status != kOk) {

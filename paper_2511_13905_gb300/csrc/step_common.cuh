@@ -308,11 +308,13 @@ __device__ void search_pass_update(const BlockScratch& sc, int base, volatile Ro
     const DF gap = df_add(NL, df_neg(NH));
     const DF wd = two_sum(H, -L);
     const float w = wd.hi;
-    const float tol = (float)tol_lambda * fabsf(H);
+    // tolerances relative to the bracket's magnitude (a negative bracket ends at 0)
+    const float mag = fmaxf(fabsf(L), fabsf(H));
+    const float tol = (float)tol_lambda * mag;
     bool done = false;
     int how = 2;
     if (kH >= 0 && rH.hi == 0.0f && rH.lo == 0.0f) done = true;
-    else if (fabsf(gap.hi) <= tol || w <= tol || w <= 4.0f * float_ulp_f(H)) done = true;
+    else if (fabsf(gap.hi) <= tol || w <= tol || w <= 4.0f * float_ulp_f(mag)) done = true;
     if (!done && passes >= max_passes) {
         done = true;
         how = 3;  // not converged
