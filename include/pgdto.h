@@ -231,6 +231,7 @@ typedef struct {
     double g_val[4], G[4];       /* row scalars of this step */
     float* x_out;                /* host, n floats: receives rho_{t+1} when the step completes */
     int close_session;           /* 1: release the session's device memory after this step */
+    int eq_mask;                 /* equality rows as pgdto_params.eq_mask; read on the first request */
 } pgdto_request;
 
 /* budget_bytes: device memory the sessions may hold; max_sessions: open sessions at most;

@@ -56,7 +56,7 @@ class Request(ctypes.Structure):
                 ("seg_offsets", ctypes.POINTER(ctypes.c_int64)), ("lo", ctypes.c_float), ("hi", ctypes.c_float),
                 ("x0", ctypes.c_void_p), ("grad_f", ctypes.c_void_p), ("A", ctypes.c_void_p),
                 ("g_val", ctypes.c_double * 4), ("G", ctypes.c_double * 4), ("x_out", ctypes.c_void_p),
-                ("close_session", ctypes.c_int)]
+                ("close_session", ctypes.c_int), ("eq_mask", ctypes.c_int)]
 
 
 class PgdtoError(RuntimeError):
@@ -313,8 +313,10 @@ class Server:
         self.h = h
         self._keep = {}
 
-    def submit(self, session, n, m, grad_f, A, g_val, G, x_out, x0=None, seg=None, lo=0.0, hi=1.0, close=False):
+    def submit(self, session, n, m, grad_f, A, g_val, G, x_out, x0=None, seg=None, lo=0.0, hi=1.0, close=False,
+               eq_mask=0):
         r = Request()
+        r.eq_mask = int(eq_mask)
         r.session, r.n, r.m, r.lo, r.hi = int(session), int(n), int(m), float(lo), float(hi)
         segarr = None
         if seg is not None:

@@ -264,6 +264,7 @@ extern "C" pgdto_status pgdto_submit(pgdto_server* srv, const pgdto_request* req
         s->bytes = bytes;
         pgdto_params p = srv->params;
         p.mode = PGDTO_AUTO;
+        p.eq_mask = req->eq_mask;
         if (coupled) p.engine = 0;  // coupled rows run on the grid engine (one launch each)
         pgdto_status st = pgdto_create(&s->h, req->n, req->m, req->seg_offsets, req->lo, req->hi, &p, srv->stream);
         const size_t nb = (size_t)req->n * sizeof(float);

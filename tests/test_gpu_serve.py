@@ -177,3 +177,29 @@ def test_wait_blocks_and_stamps_completion(dev):
     st, _, _, _ = srv.wait(123456789, timeout_ms=0)
     assert st == binding.PGDTO_ERR_ARG
     srv.close()
+
+
+def test_served_equality_session_equals_a_handle(dev):
+    """A session whose row is an equality (eq_mask on its first request) gives the same
+    step as a handle created with that mask."""
+    import torch
+    from paper_2511_13905_gb300 import binding
+    p = inputs.request_problem({"id": 0, "n": 20000, "m": 1, "mode": "single", "seed": 77})
+    g, gval = _grads(p, p["x"], 0)
+    G = np.array(gval) + 0.02 * p["n"]  # more volume than now: binds from below as an equality
+    srv = binding.Server(budget_bytes=1 << 30, max_sessions=4)
+    out = np.empty(p["n"], np.float32)
+    st, t = srv.submit(5, p["n"], 1, g, np.ascontiguousarray(p["A"]), gval, G, out, x0=p["x"], eq_mask=1)
+    assert st == binding.PGDTO_OK
+    st, done, info, _ = srv.wait(t)
+    assert st == binding.PGDTO_OK and done == binding.PGDTO_OK
+    srv.close()
+    h = binding.Handle(p["n"], 1, eq_mask=1)
+    h.set_state(None, None, None, 0)
+    x = torch.from_numpy(p["x"].copy()).to(dev)
+    st, info1 = h.step(x, torch.from_numpy(g).to(dev), torch.from_numpy(np.ascontiguousarray(p["A"])).to(dev), gval, G)
+    torch.cuda.synchronize()
+    h.close()
+    assert st == 0 and info1.lambda_[0] < 0.0
+    assert np.array_equal(x.cpu().numpy(), out)
+    assert info.lambda_[0] == info1.lambda_[0]
