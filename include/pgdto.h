@@ -92,6 +92,10 @@ typedef struct {
     int eq_mask;            /* bit j set: row j is an equality g_j(x) = G_j (Sec. 3.2.4), always
                                active, lambda_j of either sign, and its violation for the
                                fallback rule is |g_j - G_j|; bits at or above m must be 0 */
+    int compaction;         /* single/independent rows: 1 (default) free-set compaction (Sec. 4.2.1)
+                               -- from the second root-search pass on, elements whose clip state
+                               the bracket has fixed are summed once and later passes visit the
+                               rest; 0: every pass visits every element */
 } pgdto_params;
 
 /* Per-call report. */
@@ -109,6 +113,8 @@ typedef struct {
     int branch;             /* step-size rule: 0 fallback, 1 BB1, 2 Lipschitz */
     int status;             /* pgdto_status of the device work */
     int t;                  /* iteration index the step used */
+    double visited;         /* element evaluations of the root-search passes (n per row and
+                               pass without compaction; fewer once its lists are in use) */
 } pgdto_info;
 
 typedef struct pgdto_handle pgdto_handle;

@@ -35,20 +35,21 @@ class Params(ctypes.Structure):
                 ("tol_lambda", ctypes.c_double), ("t_warmup", ctypes.c_int), ("maxiter_newton", ctypes.c_int),
                 ("max_passes", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int), ("mode", ctypes.c_int),
                 ("fault_inject", ctypes.c_int), ("engine", ctypes.c_int), ("cluster_elems", ctypes.c_int),
-                ("eq_mask", ctypes.c_int)]
+                ("eq_mask", ctypes.c_int), ("compaction", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("lambda_", ctypes.c_double * 4),
                 ("b", ctypes.c_double * 4), ("viol", ctypes.c_double * 4), ("rel_change", ctypes.c_double),
                 ("phi_inf", ctypes.c_double), ("passes", ctypes.c_int), ("newton_iters", ctypes.c_int),
-                ("stage", ctypes.c_int), ("branch", ctypes.c_int), ("status", ctypes.c_int), ("t", ctypes.c_int)]
+                ("stage", ctypes.c_int), ("branch", ctypes.c_int), ("status", ctypes.c_int), ("t", ctypes.c_int),
+                ("visited", ctypes.c_double)]
 
     def as_dict(self, m=4):
         return {"alpha": self.alpha, "beta": self.beta, "lambda": list(self.lambda_)[:m], "b": list(self.b)[:m],
                 "viol": list(self.viol)[:m], "rel_change": self.rel_change, "phi_inf": self.phi_inf,
                 "passes": self.passes, "newton_iters": self.newton_iters, "stage": self.stage,
-                "branch": self.branch, "status": self.status, "t": self.t}
+                "branch": self.branch, "status": self.status, "t": self.t, "visited": self.visited}
 
 
 class Request(ctypes.Structure):

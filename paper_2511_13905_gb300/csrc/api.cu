@@ -56,6 +56,8 @@ struct pgdto_handle {
     cudaEvent_t items_ev;     // the last upload of items_host (it is rewritten only after)
     int items_cap;
     cudaStream_t aux[4];      // batched launches: one stream per further cluster size
+    int* cidx;                // free-set compaction lists (both engines' layouts fit), or null
+    int* ccnt;
     cudaEvent_t fork_ev, join_ev[4];
 };
 
@@ -115,6 +117,7 @@ extern "C" pgdto_status pgdto_params_default(pgdto_params* p) {
     p->engine = 0;
     p->cluster_elems = 0;
     p->eq_mask = 0;
+    p->compaction = 1;
     return PGDTO_OK;
 }
 
@@ -133,6 +136,8 @@ static void free_handle(pgdto_handle* h) {
     cudaFree(h->hg);
     cudaFree(h->hA);
     cudaFree(h->items);
+    cudaFree(h->cidx);
+    cudaFree(h->ccnt);
     cudaFreeHost(h->items_host);
     if (h->items_ev) cudaEventDestroy(h->items_ev);
     for (int g = 0; g < 4; ++g) {
@@ -148,7 +153,7 @@ static bool params_ok(const pgdto_params& p) {
            p.eps_alpha >= 0 && p.tol_lambda > 0 && p.tol_lambda < 1e-2 && p.t_warmup >= 0 &&
            p.maxiter_newton >= 1 && p.max_passes >= 1 && p.max_passes <= 100000 && p.barrier_timeout_ms >= 1 &&
            (p.fault_inject == 0 || p.fault_inject == 1) && p.engine >= 0 && p.engine <= 2 && p.cluster_elems >= 0 &&
-           p.eq_mask >= 0 && p.eq_mask < 16;
+           p.eq_mask >= 0 && p.eq_mask < 16 && (p.compaction == 0 || p.compaction == 1);
 }
 
 extern "C" pgdto_status pgdto_create(pgdto_handle** out, int64_t n, int m, const int64_t* seg_offsets, float lo,
@@ -239,6 +244,17 @@ extern "C" pgdto_status pgdto_create(pgdto_handle** out, int64_t n, int m, const
         (e = cudaMalloc(&h->work, h->work_bytes)) != cudaSuccess) {
         free_handle(h);
         return cuda_fail(e);
+    }
+    if (mode != PGDTO_COUPLED && p.compaction && n < (int64_t)0x7fffffff) {
+        // compaction lists (32-bit element indices): room for the grid and the cluster layout
+        const int64_t lg = (int64_t)h->blocks * seg_list_cta(h->seg, m, h->blocks, kThreads);
+        const int64_t lc = (int64_t)h->cl_size * seg_list_cta(h->seg, m, h->cl_size, kThreads);
+        const int nbm = h->blocks > h->cl_size ? h->blocks : h->cl_size;
+        if ((e = cudaMalloc(&h->cidx, (size_t)(lg > lc ? lg : lc) * sizeof(int))) != cudaSuccess ||
+            (e = cudaMalloc(&h->ccnt, (size_t)nbm * kMaxRows * kThreads * sizeof(int))) != cudaSuccess) {
+            free_handle(h);
+            return cuda_fail(e);
+        }
     }
     h->dev_info = mode == PGDTO_COUPLED ? coupled_work_info((CoupledWork*)h->work) : seg_work_info((SegWork*)h->work);
     if ((e = cudaMemsetAsync(h->work, 0, h->work_bytes, h->stream)) != cudaSuccess ||
@@ -383,6 +399,8 @@ static void fill_seg_args(pgdto_handle* h, bool proj, float* x, const float* g, 
     a.ws = (SegWork*)h->work;
     a.info_out = h->dev_info;
     a.eq_mask = h->p.eq_mask;
+    a.cidx = h->cidx;
+    a.ccnt = h->ccnt;
     // warm start from the previous step's lam, still in the handle's report on the device
     a.lam_prev = (!proj && h->warm)
                      ? reinterpret_cast<const double*>(reinterpret_cast<const char*>(h->dev_info) +
@@ -433,11 +451,15 @@ static pgdto_status launch(pgdto_handle* h, bool proj, float* x, const float* g,
     } else {
         SegArgs a;
         fill_seg_args(h, proj, x, g, A, bconst, z_in, x_out, force_fallback, a);
+        // free-set compaction pays where a CTA's share streams from global memory; a
+        // resident share's passes are bound by their reductions, not by element work
         if (h->engine == 2 && !h->p.fault_inject) {
             a.sm_elems = h->res_cluster;
+            if (a.sm_elems > 0) a.cidx = nullptr;
             e = launch_seg_clusters(a, nullptr, 1, 1, h->cl_size, seg_args_aligned(a), h->stream, a.sm_elems);
         } else {
             a.sm_elems = h->res_grid;
+            if (a.sm_elems > 0) a.cidx = nullptr;
             e = launch_seg(a, h->blocks, h->stream);
         }
     }
@@ -561,7 +583,10 @@ static pgdto_status ensure_fork(pgdto_handle* h, int groups) {
 // clusters in order, so the longest do not trail at the end.
 static pgdto_status launch_many(int count, pgdto_handle* const* hs, SegArgs* args, bool vec) {
     pgdto_handle* h0 = hs[0];
-    for (int k = 0; k < count; ++k) args[k].sm_elems = hs[k]->res_cluster;
+    for (int k = 0; k < count; ++k) {
+        args[k].sm_elems = hs[k]->res_cluster;
+        if (args[k].sm_elems > 0) args[k].cidx = nullptr;  // resident: no compaction (see launch)
+    }
     if (count == 1) {
         cudaError_t e = launch_seg_clusters(args[0], nullptr, 1, 1, h0->cl_size, vec, h0->stream, args[0].sm_elems);
         if (e != cudaSuccess) return cuda_fail(e);

@@ -14,6 +14,7 @@ struct DeviceInfo {
     double lambda[kMaxRows], b[kMaxRows], viol[kMaxRows];
     double rel_change, phi_inf;
     int passes, newton_iters, stage, branch, status, t;
+    double visited;
 };
 
 struct SegWork;      // single / independent rows workspace (seg_kernels.cu)
@@ -49,7 +50,35 @@ struct SegArgs {
     int sm_elems;         // shared-memory residency: floats per array (z_hi, z_lo, a); 0 = off
     const double* lam_prev;  // warm start: the previous step's lam per row (device), or null
     int eq_mask;          // bit j: row j is an equality (always active, lam_j of either sign)
+    int* cidx;            // free-set compaction: per-thread lists of undecided elements, or null
+    int* ccnt;            // their lengths, per CTA, row and thread
 };
+
+// Free-set compaction lists.  Every thread keeps the elements of its own share that a
+// root search has not yet decided, entry q of thread t of a row at q * nthr + t (coalesced
+// when all threads read entry q), so appending needs no scan and the order is fixed.  A
+// thread visits at most seg_list_cap elements of a chunk in one sweep (float4 groups with
+// stride nthr, plus one element of the unaligned head and one of the tail).  The layout
+// uses the first CTA's chunk (the longest) for every CTA.
+__host__ __device__ inline int seg_list_cap(int64_t len, int nthr) {
+    const int64_t ng = len / 4 + 1;
+    return (int)(4 * ((ng + nthr - 1) / nthr) + 2);
+}
+
+__host__ __device__ inline int64_t seg_list_row_off(const int64_t* seg, int j, int nb, int nthr) {
+    int64_t off = 0;
+    for (int k = 0; k < j; ++k) {
+        const int64_t len = seg[k + 1] - seg[k];
+        const int64_t per = ((len + nb - 1) / nb + 3) & ~int64_t(3);
+        off += (int64_t)nthr * seg_list_cap(per < 4 ? 4 : per, nthr);
+    }
+    return off;
+}
+
+// Ints of one CTA's lists (every row).
+__host__ __device__ inline int64_t seg_list_cta(const int64_t* seg, int nrows, int nb, int nthr) {
+    return seg_list_row_off(seg, nrows, nb, nthr);
+}
 
 // Shared-memory residency of a CTA's share of a problem.  The CTA's chunk of row j is
 // [cb_j, ce_j) (block_chunk); it is kept from base_j = cb_j rounded down to a multiple of

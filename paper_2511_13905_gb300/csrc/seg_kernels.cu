@@ -37,6 +37,8 @@ struct SegBcast {
     float pts[kMaxRows][K];
     int active[kMaxRows];
     float lam_hi[kMaxRows], lam_lo[kMaxRows];
+    int cmode[kMaxRows];              // free-set compaction: 0 all elements, 1 all + build lists, 2 lists
+    float brL[kMaxRows], brH[kMaxRows];  // the bracket the current points lie in
 };
 
 // Search state of one problem: in global memory for the grid engine, in the shared memory
@@ -140,6 +142,9 @@ __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, Seg
         if (search) {
             store_row(&rows[j], b, L, rL, SLs, H, rH, SHs, 0.0, 0.0, 1, 0, 2);
             bc->active[j] = 1;
+            bc->cmode[j] = 0;
+            bc->brL[j] = rows[j].fL;
+            bc->brH[j] = rows[j].fH;
         } else if (closed) {
             const double lam = 0.5 * a.C * ((down ? smax : smin) - b);
             store_row(&rows[j], b, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, lam, 0.0, 0, 0, 1);
@@ -237,6 +242,9 @@ __device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegState*
     }
     inf->phi_inf = phi;
     inf->passes = passes;
+    double vis = 0.0;
+    for (int j = 0; j < a.nrows; ++j) vis += rows[j].visited;
+    inf->visited = vis;
     inf->newton_iters = 0;
     inf->stage = 0;
     inf->status = status;
@@ -547,8 +555,20 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
     }
 
     // ---------------------------------------------------------------- phase C
+    // Root-search passes.  Free-set compaction (Sec. 4.2.1): from the second pass on, an
+    // element whose state (below lo / free / above hi) is the same at both ends of the
+    // bracket the pass's points lie in keeps that state for every later (narrower)
+    // bracket, since w = z - lam a is linear in lam.  Its part of r is then a*bound or
+    // a z - lam a^2: such elements go into three per-row sums (exact products), and each
+    // thread keeps a list of the undecided rest of its share, which the later passes
+    // evaluate alone, filtering the list as they go.  The row update adds the decided part
+    // back (search_pass_update with CMP).  A margin of a few ulp keeps elements within
+    // rounding of a bound undecided.
     const float* zsrc = a.proj ? a.z_in : a.z;
     const bool has_lo = !a.proj;
+    const bool cmp = a.cidx != nullptr;
+    const int nthr = blockDim.x, tid = threadIdx.x;
+    const int64_t lstride = cmp ? seg_list_cta(a.seg, a.nrows, nb, nthr) : 0;
     while (bc.any_active) {
         int roff = 0;
         for (int j = 0; j < a.nrows; ++j) {
@@ -561,15 +581,46 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
             float p[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) p[k] = bc.pts[j][k];
-            AccSplit<K, K> acc;
+            const int mode = cmp ? bc.cmode[j] : 0;
+            const float bl = bc.brL[j], bu = bc.brH[j];
+            int* lst = cmp ? a.cidx + (int64_t)blk * lstride + seg_list_row_off(a.seg, j, nb, nthr) : nullptr;
+            int* cntp = cmp ? a.ccnt + ((int64_t)blk * kMaxRows + j) * nthr + tid : nullptr;
+            int nkeep = 0;
+            // acc.f[0, K): r sums at the points; [K, K + 3): the elements this pass decides
+            // (sum a*bound, sum a z, sum a^2; these steer the search only, the final pass
+            // recomputes r exactly); [K + 3, 2K + 3): free-set curvature at the points
+            AccSplit<K + 3, K, 2, 8> acc;
             acc.init();
+            int nvis = 0;  // elements this thread evaluates in this pass
             auto e = [&](float z, float zl, float av) {
                 const float aa = av * av;
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
                     const float w = __fadd_rn(fmaf(-p[k], av, z), zl);
                     acc.f[k] = fmaf(av, clampf(w, lo, hi), acc.f[k]);
-                    acc.f[K + k] += (w >= lo && w <= hi) ? aa : 0.0f;
+                    acc.f[K + 3 + k] += (w >= lo && w <= hi) ? aa : 0.0f;
+                }
+            };
+            // the K points, then (when classifying) the state at both bracket ends
+            auto visit = [&](int i, float z, float zl, float av) {
+                e(z, zl, av);
+                ++nvis;
+                if (mode == 0) return;
+                const float wl = __fadd_rn(fmaf(-bl, av, z), zl);
+                const float wu = __fadd_rn(fmaf(-bu, av, z), zl);
+                const float mg = 4e-7f * (fabsf(z) + fabsf(bl * av) + fabsf(bu * av) + (hi - lo));
+                const int sl = wl < lo - mg ? 0 : (wl > hi + mg ? 2 : (wl > lo + mg && wl < hi - mg ? 1 : 3));
+                const int su = wu < lo - mg ? 0 : (wu > hi + mg ? 2 : (wu > lo + mg && wu < hi - mg ? 1 : 3));
+                if (sl == su && sl != 3) {
+                    if (sl == 1) {
+                        acc.f[K + 1] = fmaf(av, z, fmaf(av, zl, acc.f[K + 1]));
+                        acc.f[K + 2] = fmaf(av, av, acc.f[K + 2]);
+                    } else {
+                        acc.f[K] = fmaf(av, sl == 0 ? lo : hi, acc.f[K]);
+                    }
+                } else {
+                    lst[nkeep * nthr + tid] = i;
+                    ++nkeep;
                 }
             };
             // one element loop per source (shared or global memory) and per trial point form
@@ -577,6 +628,24 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
             auto run = [&](auto rc, auto lc) {
                 constexpr bool R = decltype(rc)::value;
                 constexpr bool HL = decltype(lc)::value;
+                if (mode == 2) {
+                    const int cnt = *cntp;
+                    int q4 = 0;
+                    for (int q = 0; q < cnt; ++q) {
+                        const int i = lst[q * nthr + tid];
+                        if constexpr (R) {
+                            const int li = off + (int)(i - rb);
+                            visit(i, smz[li], HL ? sml[li] : 0.0f, sma[li]);
+                        } else {
+                            visit(i, zsrc[i], HL ? a.zlo[i] : 0.0f, a.A[i]);
+                        }
+                        if (++q4 == 4) {
+                            acc.tick();
+                            q4 = 0;
+                        }
+                    }
+                    return;
+                }
                 for_chunk<VEC>(
                     cb, ce,
                     [&](int64_t v) {
@@ -591,18 +660,19 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                             if constexpr (HL) zl = LD4L2(a.zlo, v);
                             av = LD4L2(a.A, v);
                         }
-                        e(z.x, zl.x, av.x);
-                        e(z.y, zl.y, av.y);
-                        e(z.z, zl.z, av.z);
-                        e(z.w, zl.w, av.w);
+                        const int i0 = (int)(4 * v);
+                        visit(i0, z.x, zl.x, av.x);
+                        visit(i0 + 1, z.y, zl.y, av.y);
+                        visit(i0 + 2, z.z, zl.z, av.z);
+                        visit(i0 + 3, z.w, zl.w, av.w);
                         acc.tick();
                     },
                     [&](int64_t i) {
                         if constexpr (R) {
                             const int q = off + (int)(i - rb);
-                            e(smz[q], HL ? sml[q] : 0.0f, sma[q]);
+                            visit((int)i, smz[q], HL ? sml[q] : 0.0f, sma[q]);
                         } else {
-                            e(zsrc[i], HL ? a.zlo[i] : 0.0f, a.A[i]);
+                            visit((int)i, zsrc[i], HL ? a.zlo[i] : 0.0f, a.A[i]);
                         }
                         acc.tick();
                     });
@@ -614,11 +684,38 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 if (has_lo) run(BoolC<false>{}, BoolC<true>{});
                 else run(BoolC<false>{}, BoolC<false>{});
             }
+            if (mode != 0) *cntp = nkeep;
             acc.fold();
-            block_reduce<2 * K, 0>(acc.d, nullptr, sc, 2 * K * j, 0);
+            DF v[2 * K + 4];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                v[k] = acc.d[k];
+                v[K + k] = acc.d[K + 3 + k];
+            }
+            v[2 * K] = acc.d[K];
+            v[2 * K + 1] = acc.d[K + 1];
+            v[2 * K + 2] = acc.d[K + 2];
+            v[2 * K + 3] = DF{(float)nvis, 0.0f};
+            block_reduce<2 * K + 4, 0>(v, nullptr, sc, (2 * K + 4) * j, 0);
         }
-        if (!sy.reduce(sc, 2 * K * a.nrows, 0, [&](BlockScratch& s, SegState* st) {
-                search_pass_update(s, 0, st->rows, &st->bc, a.nrows, a.tol_lambda, a.max_passes);
+        if (!sy.reduce(sc, (2 * K + 4) * a.nrows, 0, [&](BlockScratch& s, SegState* st) {
+                search_pass_update<SegBcast, true>(s, 0, st->rows, &st->bc, a.nrows, a.tol_lambda, a.max_passes);
+                __syncwarp();
+                // the next pass classifies against the bracket its points will lie in.  The
+                // lists are built once the bracket is within 10% of the root (the share of
+                // elements it leaves undecided follows its width) and used from then on
+                if (threadIdx.x < a.nrows) {
+                    const int r = threadIdx.x;
+                    volatile SegBcast* vb = &st->bc;
+                    if (vb->active[r]) {
+                        const float L = st->rows[r].fL, H = st->rows[r].fH;
+                        const int cm = vb->cmode[r];
+                        const bool narrow = (H - L) <= 0.1f * fmaxf(fabsf(L), fabsf(H));
+                        vb->cmode[r] = !a.cidx ? 0 : (cm >= 1 ? 2 : (narrow ? 1 : 0));
+                        vb->brL[r] = L;
+                        vb->brH[r] = H;
+                    }
+                }
             }))
             return;
         sy.fetch(bc);

@@ -20,6 +20,8 @@ constexpr unsigned kFull = 0xffffffffu;
 // with r(L) > 0 >= r(H); SL, SH are the slopes -dr/dt at the ends.
 struct RowState {
     double b, L, rL, SL, H, rH, SH, lam, rlast, reg;
+    double cC, cAA;  // free-set compaction: sum over decided elements of a*bound + a z, and of a^2
+    double visited;  // element evaluations of this row's passes
     int active, passes, how, nrefine;  // nrefine: extra final passes at a refined root
     // the same bracket in float / double-float form: the per-pass update works on these
     // (FP64 issues at a small fraction of the FP32 rate here and sits on the critical path)
@@ -113,6 +115,15 @@ __device__ __forceinline__ float group8_sort(float v, int lane) {
 // Trial point k of the next pass inside (L, H): Newton from the lower end (k = 0), from the
 // upper end (k = 1), the secant point (k = 2), and a uniform fill (k = 3..7) that
 // guarantees the bracket shrinks by at least a factor 6.  Returns the group-sorted value.
+// A bracket that contains 0 or spans more than a factor of 4 is searched on a geometric
+// ladder base * {1/8, 1/4, 1/2, 2, 4} around the Newton estimate from its zero end (the
+// secant otherwise) rather than on uniform points: the saturation bound that closes the
+// first bracket is often tens of times the root.
+__device__ __forceinline__ bool wide_bracket(double L, double H) {
+    const double a = fabs(L), b = fabs(H);
+    return L * H <= 0.0 || fmax(a, b) > 4.0 * fmin(a, b);
+}
+
 __device__ __forceinline__ float next_point(int lane, double L, double rL, double H, double rH, double NL,
                                             double NH) {
     const int k = lane & 7;
@@ -121,7 +132,13 @@ __device__ __forceinline__ float next_point(int lane, double L, double rL, doubl
     if (k == 0) v = NL;
     else if (k == 1) v = NH;
     else if (k == 2) v = L + rL * w / (rL - rH);
-    else v = L + w * (double)(k - 2) * (1.0 / 6.0);
+    else if (wide_bracket(L, H)) {
+        const double sec = L + rL * w / (rL - rH);
+        const double base = (L == 0.0 && NL > L && NL < H) ? NL : (H == 0.0 && NH > L && NH < H) ? NH : sec;
+        v = base * (k == 3 ? 0.125 : k == 4 ? 0.25 : k == 5 ? 0.5 : k == 6 ? 2.0 : 4.0);
+    } else {
+        v = L + w * (double)(k - 2) * (1.0 / 6.0);
+    }
     if (!(v > L && v < H)) v = L + w * ((double)k + 0.5) * 0.125;
     float f = (float)v;
     if (!((double)f > L && (double)f < H)) {
@@ -145,7 +162,11 @@ __device__ __forceinline__ float next_point_warm(int lane, double L, double rL, 
     if (k == 0) v = NL;
     else if (k == 1) v = NH;
     else if (k == 2) v = L + rL * w / (rL - rH);
-    else if (!warm) v = L + w * (double)(k - 2) * (1.0 / 6.0);
+    else if (!warm && wide_bracket(L, H)) {
+        const double sec = L + rL * w / (rL - rH);
+        const double base = (L == 0.0 && NL > L && NL < H) ? NL : (H == 0.0 && NH > L && NH < H) ? NH : sec;
+        v = base * (k == 3 ? 0.125 : k == 4 ? 0.25 : k == 5 ? 0.5 : k == 6 ? 2.0 : 4.0);
+    } else if (!warm) v = L + w * (double)(k - 2) * (1.0 / 6.0);
     else if (k == 3) v = L + 0.5 * w;
     else v = lp * (k == 4 ? 0.97 : k == 5 ? 0.997 : k == 6 ? 1.003 : 1.03);
     if (!(v > L && v < H)) v = L + w * ((double)k + 0.5) * 0.125;
@@ -173,6 +194,9 @@ __device__ __forceinline__ void store_row(volatile RowState* r, double b, double
     r->passes = passes;
     r->how = how;
     r->nrefine = 0;
+    r->cC = 0.0;
+    r->cAA = 0.0;
+    r->visited = 0.0;
     float h, l;
     split_double(b, h, l);
     r->b_hi = h;
@@ -238,11 +262,18 @@ __device__ __forceinline__ float float_ulp_f(float v) {
 __device__ __forceinline__ float next_point_f(int lane, float L, float rL, float H, float rH, float NL, float NH) {
     const int k = lane & 7;
     const float w = H - L;
+    const float am = fabsf(L), bm = fabsf(H);
     float v;
     if (k == 0) v = NL;
     else if (k == 1) v = NH;
     else if (k == 2) v = L + rL * __fdiv_rn(w, rL - rH);
-    else v = fmaf(w, (float)(k - 2) * (1.0f / 6.0f), L);
+    else if (L * H <= 0.0f || fmaxf(am, bm) > 4.0f * fminf(am, bm)) {
+        const float sec = L + rL * __fdiv_rn(w, rL - rH);
+        const float base = (L == 0.0f && NL > L && NL < H) ? NL : (H == 0.0f && NH > L && NH < H) ? NH : sec;
+        v = base * (k == 3 ? 0.125f : k == 4 ? 0.25f : k == 5 ? 0.5f : k == 6 ? 2.0f : 4.0f);
+    } else {
+        v = fmaf(w, (float)(k - 2) * (1.0f / 6.0f), L);
+    }
     if (!(v > L && v < H)) v = fmaf(w, ((float)k + 0.5f) * 0.125f, L);
     if (!(v > L && v < H)) {
         v = L + 0.5f * w;
@@ -257,9 +288,13 @@ __device__ __forceinline__ float next_point_f(int lane, float L, float rL, float
 // Newton from both ends of its bracket agrees (both ends on one linear piece), when the
 // bracket is within tol or a few float spacings, or at max_passes (flagged), and writes
 // the next points.  Works in float and double-float; FP64 only for a finished root.
-template <class Bcast>
+// CMP: the pass summed only the elements not yet decided (free-set compaction); each row
+// then adds the decided elements' part, C + sum a z - t_k sum a^2, from its row state,
+// and the pass's three extra sums (the elements it decided) join that state.
+template <class Bcast, bool CMP = false>
 __device__ void search_pass_update(const BlockScratch& sc, int base, volatile RowState* rows, volatile Bcast* bc,
                                    int nsearch, double tol_lambda, int max_passes) {
+    constexpr int stride = CMP ? 2 * K + 4 : 2 * K;
     const int lane = threadIdx.x, j = lane >> 3, k = lane & 7, g0 = lane & ~7;
     const int jj = j < nsearch ? j : 0;
     const bool row = j < nsearch && rows[jj].active;
@@ -271,9 +306,15 @@ __device__ void search_pass_update(const BlockScratch& sc, int base, volatile Ro
     const float lk = bc->pts[jj][k];
     // r_k = S_k - b - reg t_k
     const float pr = reg * lk;
-    DF rk = df_add(sc.tot[base + 2 * K * jj + k], df_neg(b));
+    DF rk = df_add(sc.tot[base + stride * jj + k], df_neg(b));
     rk = df_add(rk, DF{-pr, -fmaf(reg, lk, -pr)});
-    const float Sk = sc.tot[base + 2 * K * jj + K + k].hi + reg;
+    float Sk = sc.tot[base + stride * jj + K + k].hi + reg;
+    if (CMP) {
+        float ch, cl;
+        split_double(rows[jj].cC - (double)lk * rows[jj].cAA, ch, cl);
+        rk = df_add(rk, DF{ch, cl});
+        Sk += (float)rows[jj].cAA;
+    }
     // new lower end: the largest point with r > 0; new upper end: the smallest point above
     // it with r <= 0 (points the rounding noise puts out of order are ignored)
     const unsigned pos = (__ballot_sync(kFull, row && df_pos(rk) && lk > L && lk < H) >> g0) & 0xffu;
@@ -332,6 +373,12 @@ __device__ void search_pass_update(const BlockScratch& sc, int base, volatile Ro
         r->rH_hi = rH.hi;
         r->rH_lo = rH.lo;
         r->passes = passes;
+        if (CMP) {
+            const int o = base + stride * j + 2 * K;
+            r->cC = r->cC + df_to_double(sc.tot[o]) + df_to_double(sc.tot[o + 1]);
+            r->cAA = r->cAA + df_to_double(sc.tot[o + 2]);
+            r->visited = r->visited + df_to_double(sc.tot[o + 3]);
+        }
         if (done) {
             // the root, once, in FP64: the midpoint of the two Newton predictions, in [L, H]
             double root = (kH >= 0 && rH.hi == 0.0f && rH.lo == 0.0f)
@@ -378,13 +425,16 @@ struct Acc {
     }
 };
 
-// Accumulators whose first NP entries (residual sums, whose rounding moves the dual root)
-// fold into double-float after every float4 group, and whose other NQ entries (slopes and
-// magnitudes, which only scale a Newton correction) after every kFoldSlow groups.
+// Accumulators whose first NP entries fold into double-float after every PF float4
+// groups and whose other NQ entries after every PS groups.  The defaults (1, 4) serve the
+// single passes whose sums enter the result (b, the final residual); the root-search passes
+// only steer the search (the final pass recomputes r exactly and refines the root), so
+// they fold less often.
 constexpr int kFoldSlow = 4;
 
-template <int NP, int NQ>
+template <int NP, int NQ, int PF = 1, int PS = kFoldSlow>
 struct AccSplit {
+    static_assert(PS % PF == 0, "the slow fold period must be a multiple of the fast one");
     static constexpr int N = NP + NQ;
     float f[N];
     DF d[N];
@@ -406,12 +456,15 @@ struct AccSplit {
         cnt = 0;
     }
     __device__ __forceinline__ void tick() {
+        ++cnt;
+        if (cnt % PF == 0) {
 #pragma unroll
-        for (int i = 0; i < NP; ++i) {
-            d[i] = df_add_f(d[i], f[i]);
-            f[i] = 0.0f;
+            for (int i = 0; i < NP; ++i) {
+                d[i] = df_add_f(d[i], f[i]);
+                f[i] = 0.0f;
+            }
         }
-        if (++cnt == kFoldSlow) {
+        if (cnt == PS) {
 #pragma unroll
             for (int i = NP; i < N; ++i) {
                 d[i] = df_add_f(d[i], f[i]);

@@ -205,9 +205,11 @@ def compare_step(cfg, info, x_dev, mode):
     else:
         err = parity_errors(x_dev, lam, ref["x_new"], ref["lam"], cfg["A"], ref["b"], C, 0.0, 1.0)
     check(err, cfg["name"])
-    # the stopping ratio of Alg. 3; its error is bounded by ||x_dev - x_ref|| / ||x_ref||
+    # the stopping ratio of Alg. 3; its error is bounded by ||x_dev - x_ref|| / ||x_ref|| plus
+    # the rounding of the two norms, which the device forms from FP32 partial sums
     nrm = float(np.linalg.norm(ref["x_new"]))
-    slack = max(1e-5 * ref["rel_change"], float(np.linalg.norm(x_dev - ref["x_new"])) / max(nrm, 1e-30) + 1e-12)
+    slack = max(1e-5 * ref["rel_change"],
+                float(np.linalg.norm(x_dev - ref["x_new"])) / max(nrm, 1e-30) + 1e-6 * ref["rel_change"] + 1e-12)
     assert abs(info.rel_change - ref["rel_change"]) <= slack
     assert np.allclose(np.array(list(info.b)[:m]), ref["b"], rtol=1e-7)
     return ref, err

@@ -48,7 +48,9 @@ def test_noalloc_matches_project_on_two_calls_in_a_row(dev):
         zt = torch.from_numpy(z).to(dev)
         at = torch.from_numpy(np.ascontiguousarray(a)).to(dev)
         x_ref = torch.empty_like(zt)
-        h = binding.Handle(z.size, m, seg=seg)
+        # the allocation-free entry is the grid engine without compaction lists: compare
+        # with a handle running the same form
+        h = binding.Handle(z.size, m, seg=seg, engine=1, compaction=0)
         st, lam_ref, info_ref = h.project(zt, at, b, x_ref)
         assert st == binding.PGDTO_OK
         h.close()
