@@ -92,10 +92,11 @@ typedef struct {
     int eq_mask;            /* bit j set: row j is an equality g_j(x) = G_j (Sec. 3.2.4), always
                                active, lambda_j of either sign, and its violation for the
                                fallback rule is |g_j - G_j|; bits at or above m must be 0 */
-    int compaction;         /* single/independent rows: 1 (default) free-set compaction (Sec. 4.2.1)
-                               -- from the second root-search pass on, elements whose clip state
-                               the bracket has fixed are summed once and later passes visit the
-                               rest; 0: every pass visits every element */
+    int compaction;         /* single/independent rows: 1 = free-set compaction (Sec. 4.2.1) -- once
+                               the bracket is within 10% of the root, elements whose clip state it
+                               fixes are summed once and later passes visit the rest (shares that
+                               stream from global memory only); 0 (default) = every pass visits
+                               every element, which measured faster on the shipped workloads */
 } pgdto_params;
 
 /* Per-call report. */

@@ -117,7 +117,7 @@ extern "C" pgdto_status pgdto_params_default(pgdto_params* p) {
     p->engine = 0;
     p->cluster_elems = 0;
     p->eq_mask = 0;
-    p->compaction = 1;
+    p->compaction = 0;
     return PGDTO_OK;
 }
 
@@ -456,7 +456,8 @@ static pgdto_status launch(pgdto_handle* h, bool proj, float* x, const float* g,
         if (h->engine == 2 && !h->p.fault_inject) {
             a.sm_elems = h->res_cluster;
             if (a.sm_elems > 0) a.cidx = nullptr;
-            e = launch_seg_clusters(a, nullptr, 1, 1, h->cl_size, seg_args_aligned(a), h->stream, a.sm_elems);
+            e = launch_seg_clusters(a, nullptr, 1, 1, h->cl_size, seg_args_aligned(a), h->stream, a.sm_elems,
+                                    a.cidx != nullptr);
         } else {
             a.sm_elems = h->res_grid;
             if (a.sm_elems > 0) a.cidx = nullptr;
@@ -588,7 +589,8 @@ static pgdto_status launch_many(int count, pgdto_handle* const* hs, SegArgs* arg
         if (args[k].sm_elems > 0) args[k].cidx = nullptr;  // resident: no compaction (see launch)
     }
     if (count == 1) {
-        cudaError_t e = launch_seg_clusters(args[0], nullptr, 1, 1, h0->cl_size, vec, h0->stream, args[0].sm_elems);
+        cudaError_t e = launch_seg_clusters(args[0], nullptr, 1, 1, h0->cl_size, vec, h0->stream, args[0].sm_elems,
+                                            args[0].cidx != nullptr);
         if (e != cudaSuccess) return cuda_fail(e);
         h0->launches += 1;
         return PGDTO_OK;
@@ -628,8 +630,10 @@ static pgdto_status launch_many(int count, pgdto_handle* const* hs, SegArgs* arg
         cudaStream_t st = g == 0 ? h0->stream : h0->aux[g - 1];
         if (g > 0 && (e = cudaStreamWaitEvent(st, h0->fork_ev, 0)) != cudaSuccess) return cuda_fail(e);
         const int cnt = starts[g + 1] - starts[g];
+        bool cmp = false;
+        for (int k = starts[g]; k < starts[g + 1]; ++k) cmp = cmp || h0->items_host[k].cidx != nullptr;
         e = launch_seg_clusters(h0->items_host[starts[g]], h0->items + starts[g], cnt, cnt, sizes[g], vec, st,
-                                smem[g]);
+                                smem[g], cmp);
         if (e != cudaSuccess) return cuda_fail(e);
         if (g > 0) {
             if ((e = cudaEventRecord(h0->join_ev[g - 1], st)) != cudaSuccess ||

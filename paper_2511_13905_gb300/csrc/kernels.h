@@ -166,9 +166,10 @@ size_t coupled_work_ctrl_bytes();
 cudaError_t launch_seg(const SegArgs& a, int blocks, cudaStream_t stream);
 // Cluster engine: `items` (device array of `nitems` problems) on `nclusters` clusters of
 // `cluster` CTAs each.  vec: every pointer of every item is 16-byte aligned.  sm_elems:
-// residency floats per array, at least every item's sm_elems (a multiple of 4).
+// residency floats per array, at least every item's sm_elems (a multiple of 4).  cmp: some
+// item brings compaction lists (the compaction variant of the kernel runs).
 cudaError_t launch_seg_clusters(const SegArgs& first, const SegArgs* items, int nitems, int nclusters, int cluster,
-                                bool vec, cudaStream_t stream, int sm_elems);
+                                bool vec, cudaStream_t stream, int sm_elems, bool cmp);
 bool seg_args_aligned(const SegArgs& a);
 // Largest cluster size (<= 16) the cluster engine can use, and how many such clusters fit.
 int seg_cluster_shape(int device, int* cluster, int* max_clusters);

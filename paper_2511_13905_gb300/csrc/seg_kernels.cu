@@ -328,7 +328,7 @@ struct BoolC {
     static constexpr bool value = B;
 };
 
-template <bool VEC, class Sync>
+template <bool VEC, bool CMP, class Sync>
 __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, SegBcast& bc, float* sm) {
     const int nb = sy.size(), blk = sy.rank();
     const float lo = a.lo, hi = a.hi;
@@ -564,161 +564,266 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
     // evaluate alone, filtering the list as they go.  The row update adds the decided part
     // back (search_pass_update with CMP).  A margin of a few ulp keeps elements within
     // rounding of a bound undecided.
-    const float* zsrc = a.proj ? a.z_in : a.z;
-    const bool has_lo = !a.proj;
-    const bool cmp = a.cidx != nullptr;
-    const int nthr = blockDim.x, tid = threadIdx.x;
-    const int64_t lstride = cmp ? seg_list_cta(a.seg, a.nrows, nb, nthr) : 0;
-    while (bc.any_active) {
-        int roff = 0;
-        for (int j = 0; j < a.nrows; ++j) {
-            int64_t cb, ce;
-            block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
-            const int64_t rb = cb & ~int64_t(3);
-            const int off = roff;
-            roff += seg_res_span(cb, ce);
-            if (!bc.active[j]) continue;
-            float p[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) p[k] = bc.pts[j][k];
-            const int mode = cmp ? bc.cmode[j] : 0;
-            const float bl = bc.brL[j], bu = bc.brH[j];
-            int* lst = cmp ? a.cidx + (int64_t)blk * lstride + seg_list_row_off(a.seg, j, nb, nthr) : nullptr;
-            int* cntp = cmp ? a.ccnt + ((int64_t)blk * kMaxRows + j) * nthr + tid : nullptr;
-            int nkeep = 0;
-            // acc.f[0, K): r sums at the points; [K, K + 3): the elements this pass decides
-            // (sum a*bound, sum a z, sum a^2; these steer the search only, the final pass
-            // recomputes r exactly); [K + 3, 2K + 3): free-set curvature at the points
-            AccSplit<K + 3, K, 2, 8> acc;
-            acc.init();
-            int nvis = 0;  // elements this thread evaluates in this pass
-            auto e = [&](float z, float zl, float av) {
-                const float aa = av * av;
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    const float w = __fadd_rn(fmaf(-p[k], av, z), zl);
-                    acc.f[k] = fmaf(av, clampf(w, lo, hi), acc.f[k]);
-                    acc.f[K + 3 + k] += (w >= lo && w <= hi) ? aa : 0.0f;
-                }
-            };
-            // the K points, then (when classifying) the state at both bracket ends
-            auto visit = [&](int i, float z, float zl, float av) {
-                e(z, zl, av);
-                ++nvis;
-                if (mode == 0) return;
-                const float wl = __fadd_rn(fmaf(-bl, av, z), zl);
-                const float wu = __fadd_rn(fmaf(-bu, av, z), zl);
-                const float mg = 4e-7f * (fabsf(z) + fabsf(bl * av) + fabsf(bu * av) + (hi - lo));
-                const int sl = wl < lo - mg ? 0 : (wl > hi + mg ? 2 : (wl > lo + mg && wl < hi - mg ? 1 : 3));
-                const int su = wu < lo - mg ? 0 : (wu > hi + mg ? 2 : (wu > lo + mg && wu < hi - mg ? 1 : 3));
-                if (sl == su && sl != 3) {
-                    if (sl == 1) {
-                        acc.f[K + 1] = fmaf(av, z, fmaf(av, zl, acc.f[K + 1]));
-                        acc.f[K + 2] = fmaf(av, av, acc.f[K + 2]);
+    if constexpr (CMP) {
+        const float* zsrc = a.proj ? a.z_in : a.z;
+        const bool has_lo = !a.proj;
+        const bool cmp = a.cidx != nullptr;
+        const int nthr = blockDim.x, tid = threadIdx.x;
+        const int64_t lstride = cmp ? seg_list_cta(a.seg, a.nrows, nb, nthr) : 0;
+        while (bc.any_active) {
+            int roff = 0;
+            for (int j = 0; j < a.nrows; ++j) {
+                int64_t cb, ce;
+                block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
+                const int64_t rb = cb & ~int64_t(3);
+                const int off = roff;
+                roff += seg_res_span(cb, ce);
+                if (!bc.active[j]) continue;
+                float p[K];
+    #pragma unroll
+                for (int k = 0; k < K; ++k) p[k] = bc.pts[j][k];
+                const int mode = cmp ? bc.cmode[j] : 0;
+                const float bl = bc.brL[j], bu = bc.brH[j];
+                int* lst = cmp ? a.cidx + (int64_t)blk * lstride + seg_list_row_off(a.seg, j, nb, nthr) : nullptr;
+                int* cntp = cmp ? a.ccnt + ((int64_t)blk * kMaxRows + j) * nthr + tid : nullptr;
+                int nkeep = 0;
+                // acc.f[0, K): r sums at the points; [K, K + 3): the elements this pass decides
+                // (sum a*bound, sum a z, sum a^2; these steer the search only, the final pass
+                // recomputes r exactly); [K + 3, 2K + 3): free-set curvature at the points
+                AccSplit<K + 3, K, 2, 8> acc;
+                acc.init();
+                int nvis = 0;  // elements this thread evaluates in this pass
+                auto e = [&](float z, float zl, float av) {
+                    const float aa = av * av;
+    #pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        const float w = __fadd_rn(fmaf(-p[k], av, z), zl);
+                        acc.f[k] = fmaf(av, clampf(w, lo, hi), acc.f[k]);
+                        acc.f[K + 3 + k] += (w >= lo && w <= hi) ? aa : 0.0f;
+                    }
+                };
+                // the K points, then (when classifying) the state at both bracket ends
+                auto visit = [&](int i, float z, float zl, float av) {
+                    e(z, zl, av);
+                    ++nvis;
+                    if (mode == 0) return;
+                    const float wl = __fadd_rn(fmaf(-bl, av, z), zl);
+                    const float wu = __fadd_rn(fmaf(-bu, av, z), zl);
+                    const float mg = 4e-7f * (fabsf(z) + fabsf(bl * av) + fabsf(bu * av) + (hi - lo));
+                    const int sl = wl < lo - mg ? 0 : (wl > hi + mg ? 2 : (wl > lo + mg && wl < hi - mg ? 1 : 3));
+                    const int su = wu < lo - mg ? 0 : (wu > hi + mg ? 2 : (wu > lo + mg && wu < hi - mg ? 1 : 3));
+                    if (sl == su && sl != 3) {
+                        if (sl == 1) {
+                            acc.f[K + 1] = fmaf(av, z, fmaf(av, zl, acc.f[K + 1]));
+                            acc.f[K + 2] = fmaf(av, av, acc.f[K + 2]);
+                        } else {
+                            acc.f[K] = fmaf(av, sl == 0 ? lo : hi, acc.f[K]);
+                        }
                     } else {
-                        acc.f[K] = fmaf(av, sl == 0 ? lo : hi, acc.f[K]);
+                        lst[nkeep * nthr + tid] = i;
+                        ++nkeep;
+                    }
+                };
+                // one element loop per source (shared or global memory), per trial point form
+                // (with or without z_lo) and per kind of pass (with or without classification),
+                // fixed at compile time: a pass before the lists exist runs the plain loop
+                auto run = [&](auto rc, auto lc, auto cc) {
+                    constexpr bool R = decltype(rc)::value;
+                    constexpr bool HL = decltype(lc)::value;
+                    constexpr bool CL = decltype(cc)::value;
+                    auto vis = [&](int i, float z, float zl, float av) {
+                        if constexpr (CL) {
+                            visit(i, z, zl, av);
+                        } else {
+                            e(z, zl, av);
+                            ++nvis;
+                        }
+                    };
+                    if (CL && mode == 2) {
+                        const int cnt = *cntp;
+                        int q4 = 0;
+                        for (int q = 0; q < cnt; ++q) {
+                            const int i = lst[q * nthr + tid];
+                            if constexpr (R) {
+                                const int li = off + (int)(i - rb);
+                                vis(i, smz[li], HL ? sml[li] : 0.0f, sma[li]);
+                            } else {
+                                vis(i, zsrc[i], HL ? a.zlo[i] : 0.0f, a.A[i]);
+                            }
+                            if (++q4 == 4) {
+                                acc.tick();
+                                q4 = 0;
+                            }
+                        }
+                        return;
+                    }
+                    for_chunk<VEC>(
+                        cb, ce,
+                        [&](int64_t v) {
+                            float4 z, zl = make_float4(0.f, 0.f, 0.f, 0.f), av;
+                            if constexpr (R) {
+                                const int q = (off >> 2) + (int)(v - (rb >> 2));
+                                z = reinterpret_cast<const float4*>(smz)[q];
+                                if constexpr (HL) zl = reinterpret_cast<const float4*>(sml)[q];
+                                av = reinterpret_cast<const float4*>(sma)[q];
+                            } else {
+                                z = LD4L2(zsrc, v);
+                                if constexpr (HL) zl = LD4L2(a.zlo, v);
+                                av = LD4L2(a.A, v);
+                            }
+                            const int i0 = (int)(4 * v);
+                            vis(i0, z.x, zl.x, av.x);
+                            vis(i0 + 1, z.y, zl.y, av.y);
+                            vis(i0 + 2, z.z, zl.z, av.z);
+                            vis(i0 + 3, z.w, zl.w, av.w);
+                            acc.tick();
+                        },
+                        [&](int64_t i) {
+                            if constexpr (R) {
+                                const int q = off + (int)(i - rb);
+                                vis((int)i, smz[q], HL ? sml[q] : 0.0f, sma[q]);
+                            } else {
+                                vis((int)i, zsrc[i], HL ? a.zlo[i] : 0.0f, a.A[i]);
+                            }
+                            acc.tick();
+                        });
+                };
+                if (mode == 0) {
+                    if (res) {
+                        if (has_lo) run(BoolC<true>{}, BoolC<true>{}, BoolC<false>{});
+                        else run(BoolC<true>{}, BoolC<false>{}, BoolC<false>{});
+                    } else {
+                        if (has_lo) run(BoolC<false>{}, BoolC<true>{}, BoolC<false>{});
+                        else run(BoolC<false>{}, BoolC<false>{}, BoolC<false>{});
                     }
                 } else {
-                    lst[nkeep * nthr + tid] = i;
-                    ++nkeep;
+                    if (res) {
+                        if (has_lo) run(BoolC<true>{}, BoolC<true>{}, BoolC<true>{});
+                        else run(BoolC<true>{}, BoolC<false>{}, BoolC<true>{});
+                    } else {
+                        if (has_lo) run(BoolC<false>{}, BoolC<true>{}, BoolC<true>{});
+                        else run(BoolC<false>{}, BoolC<false>{}, BoolC<true>{});
+                    }
                 }
-            };
-            // one element loop per source (shared or global memory) and per trial point form
-            // (with or without z_lo), fixed at compile time
-            auto run = [&](auto rc, auto lc) {
-                constexpr bool R = decltype(rc)::value;
-                constexpr bool HL = decltype(lc)::value;
-                if (mode == 2) {
-                    const int cnt = *cntp;
-                    int q4 = 0;
-                    for (int q = 0; q < cnt; ++q) {
-                        const int i = lst[q * nthr + tid];
-                        if constexpr (R) {
-                            const int li = off + (int)(i - rb);
-                            visit(i, smz[li], HL ? sml[li] : 0.0f, sma[li]);
-                        } else {
-                            visit(i, zsrc[i], HL ? a.zlo[i] : 0.0f, a.A[i]);
-                        }
-                        if (++q4 == 4) {
-                            acc.tick();
-                            q4 = 0;
+                if (mode != 0) *cntp = nkeep;
+                acc.fold();
+                DF v[2 * K + 4];
+    #pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    v[k] = acc.d[k];
+                    v[K + k] = acc.d[K + 3 + k];
+                }
+                v[2 * K] = acc.d[K];
+                v[2 * K + 1] = acc.d[K + 1];
+                v[2 * K + 2] = acc.d[K + 2];
+                v[2 * K + 3] = DF{(float)nvis, 0.0f};
+                block_reduce<2 * K + 4, 0>(v, nullptr, sc, (2 * K + 4) * j, 0);
+            }
+            if (!sy.reduce(sc, (2 * K + 4) * a.nrows, 0, [&](BlockScratch& s, SegState* st) {
+                    search_pass_update<SegBcast, true>(s, 0, st->rows, &st->bc, a.nrows, a.tol_lambda, a.max_passes);
+                    __syncwarp();
+                    // the next pass classifies against the bracket its points will lie in.  The
+                    // lists are built once the bracket is within 10% of the root (the share of
+                    // elements it leaves undecided follows its width) and used from then on
+                    if (threadIdx.x < a.nrows) {
+                        const int r = threadIdx.x;
+                        volatile SegBcast* vb = &st->bc;
+                        if (vb->active[r]) {
+                            const float L = st->rows[r].fL, H = st->rows[r].fH;
+                            const int cm = vb->cmode[r];
+                            const bool narrow = (H - L) <= 0.1f * fmaxf(fabsf(L), fabsf(H));
+                            vb->cmode[r] = !a.cidx ? 0 : (cm >= 1 ? 2 : (narrow ? 1 : 0));
+                            vb->brL[r] = L;
+                            vb->brH[r] = H;
                         }
                     }
-                    return;
-                }
-                for_chunk<VEC>(
-                    cb, ce,
-                    [&](int64_t v) {
-                        float4 z, zl = make_float4(0.f, 0.f, 0.f, 0.f), av;
-                        if constexpr (R) {
-                            const int q = (off >> 2) + (int)(v - (rb >> 2));
-                            z = reinterpret_cast<const float4*>(smz)[q];
-                            if constexpr (HL) zl = reinterpret_cast<const float4*>(sml)[q];
-                            av = reinterpret_cast<const float4*>(sma)[q];
-                        } else {
-                            z = LD4L2(zsrc, v);
-                            if constexpr (HL) zl = LD4L2(a.zlo, v);
-                            av = LD4L2(a.A, v);
-                        }
-                        const int i0 = (int)(4 * v);
-                        visit(i0, z.x, zl.x, av.x);
-                        visit(i0 + 1, z.y, zl.y, av.y);
-                        visit(i0 + 2, z.z, zl.z, av.z);
-                        visit(i0 + 3, z.w, zl.w, av.w);
-                        acc.tick();
-                    },
-                    [&](int64_t i) {
-                        if constexpr (R) {
-                            const int q = off + (int)(i - rb);
-                            visit((int)i, smz[q], HL ? sml[q] : 0.0f, sma[q]);
-                        } else {
-                            visit((int)i, zsrc[i], HL ? a.zlo[i] : 0.0f, a.A[i]);
-                        }
-                        acc.tick();
-                    });
-            };
-            if (res) {
-                if (has_lo) run(BoolC<true>{}, BoolC<true>{});
-                else run(BoolC<true>{}, BoolC<false>{});
-            } else {
-                if (has_lo) run(BoolC<false>{}, BoolC<true>{});
-                else run(BoolC<false>{}, BoolC<false>{});
-            }
-            if (mode != 0) *cntp = nkeep;
-            acc.fold();
-            DF v[2 * K + 4];
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                v[k] = acc.d[k];
-                v[K + k] = acc.d[K + 3 + k];
-            }
-            v[2 * K] = acc.d[K];
-            v[2 * K + 1] = acc.d[K + 1];
-            v[2 * K + 2] = acc.d[K + 2];
-            v[2 * K + 3] = DF{(float)nvis, 0.0f};
-            block_reduce<2 * K + 4, 0>(v, nullptr, sc, (2 * K + 4) * j, 0);
+                }))
+                return;
+            sy.fetch(bc);
         }
-        if (!sy.reduce(sc, (2 * K + 4) * a.nrows, 0, [&](BlockScratch& s, SegState* st) {
-                search_pass_update<SegBcast, true>(s, 0, st->rows, &st->bc, a.nrows, a.tol_lambda, a.max_passes);
-                __syncwarp();
-                // the next pass classifies against the bracket its points will lie in.  The
-                // lists are built once the bracket is within 10% of the root (the share of
-                // elements it leaves undecided follows its width) and used from then on
-                if (threadIdx.x < a.nrows) {
-                    const int r = threadIdx.x;
-                    volatile SegBcast* vb = &st->bc;
-                    if (vb->active[r]) {
-                        const float L = st->rows[r].fL, H = st->rows[r].fH;
-                        const int cm = vb->cmode[r];
-                        const bool narrow = (H - L) <= 0.1f * fmaxf(fabsf(L), fabsf(H));
-                        vb->cmode[r] = !a.cidx ? 0 : (cm >= 1 ? 2 : (narrow ? 1 : 0));
-                        vb->brL[r] = L;
-                        vb->brH[r] = H;
+    } else {
+        // without compaction every pass visits every element (compile-time variant: none of
+        // the list bookkeeping in the loop, 2K sums per row)
+        const float* zsrc = a.proj ? a.z_in : a.z;
+        const bool has_lo = !a.proj;
+        while (bc.any_active) {
+            int roff = 0;
+            for (int j = 0; j < a.nrows; ++j) {
+                int64_t cb, ce;
+                block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
+                const int64_t rb = cb & ~int64_t(3);
+                const int off = roff;
+                roff += seg_res_span(cb, ce);
+                if (!bc.active[j]) continue;
+                float p[K];
+#pragma unroll
+                for (int k = 0; k < K; ++k) p[k] = bc.pts[j][k];
+                AccSplit<K, K, 2, 8> acc;
+                acc.init();
+                auto e = [&](float z, float zl, float av) {
+                    const float aa = av * av;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        const float w = __fadd_rn(fmaf(-p[k], av, z), zl);
+                        acc.f[k] = fmaf(av, clampf(w, lo, hi), acc.f[k]);
+                        acc.f[K + k] += (w >= lo && w <= hi) ? aa : 0.0f;
                     }
+                };
+                auto run = [&](auto rc, auto lc) {
+                    constexpr bool R = decltype(rc)::value;
+                    constexpr bool HL = decltype(lc)::value;
+                    for_chunk<VEC>(
+                        cb, ce,
+                        [&](int64_t v) {
+                            float4 z, zl = make_float4(0.f, 0.f, 0.f, 0.f), av;
+                            if constexpr (R) {
+                                const int q = (off >> 2) + (int)(v - (rb >> 2));
+                                z = reinterpret_cast<const float4*>(smz)[q];
+                                if constexpr (HL) zl = reinterpret_cast<const float4*>(sml)[q];
+                                av = reinterpret_cast<const float4*>(sma)[q];
+                            } else {
+                                z = LD4L2(zsrc, v);
+                                if constexpr (HL) zl = LD4L2(a.zlo, v);
+                                av = LD4L2(a.A, v);
+                            }
+                            e(z.x, zl.x, av.x);
+                            e(z.y, zl.y, av.y);
+                            e(z.z, zl.z, av.z);
+                            e(z.w, zl.w, av.w);
+                            acc.tick();
+                        },
+                        [&](int64_t i) {
+                            if constexpr (R) {
+                                const int q = off + (int)(i - rb);
+                                e(smz[q], HL ? sml[q] : 0.0f, sma[q]);
+                            } else {
+                                e(zsrc[i], HL ? a.zlo[i] : 0.0f, a.A[i]);
+                            }
+                            acc.tick();
+                        });
+                };
+                if (res) {
+                    if (has_lo) run(BoolC<true>{}, BoolC<true>{});
+                    else run(BoolC<true>{}, BoolC<false>{});
+                } else {
+                    if (has_lo) run(BoolC<false>{}, BoolC<true>{});
+                    else run(BoolC<false>{}, BoolC<false>{});
                 }
-            }))
-            return;
-        sy.fetch(bc);
+                acc.fold();
+                block_reduce<2 * K, 0>(acc.d, nullptr, sc, 2 * K * j, 0);
+            }
+            if (!sy.reduce(sc, 2 * K * a.nrows, 0, [&](BlockScratch& s, SegState* st) {
+                    // every element of each active row was visited
+                    if (threadIdx.x < a.nrows && st->bc.active[threadIdx.x])
+                        st->rows[threadIdx.x].visited =
+                            st->rows[threadIdx.x].visited + (double)(a.seg[threadIdx.x + 1] - a.seg[threadIdx.x]);
+                    __syncwarp();
+                    search_pass_update<SegBcast, false>(s, 0, st->rows, &st->bc, a.nrows, a.tol_lambda,
+                                                        a.max_passes);
+                }))
+                return;
+            sy.fetch(bc);
+        }
     }
 
     // ---------------------------------------------------------------- phase D
@@ -850,7 +955,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
     }
 }
 
-template <bool VEC>
+template <bool VEC, bool CMP>
 __global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
     __shared__ BlockScratch sc;
     __shared__ SegBcast bc;
@@ -865,13 +970,13 @@ __global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
     // test hook: block 0 never arrives, so every other block's first wait runs out its budget
     if (a.fault_inject == 1 && blockIdx.x == 0) return;
     GridSyncSeg sy{ws, a.timeout_cycles};
-    seg_body<VEC>(a, sy, sc, bc, a.sm_elems > 0 ? reinterpret_cast<float*>(seg_dyn_sm) : nullptr);
+    seg_body<VEC, CMP>(a, sy, sc, bc, a.sm_elems > 0 ? reinterpret_cast<float*>(seg_dyn_sm) : nullptr);
 }
 
 // Cluster engine over a list of problems: cluster c takes problems c, c + nclusters, ...
 // Problem 0 travels in the launch parameters (a single problem needs no upload), the rest
 // in `items`.  Each problem's report goes to its info_out.
-template <bool VEC>
+template <bool VEC, bool CMP>
 __global__ void __launch_bounds__(kThreads, 1) seg_cluster_kernel(SegArgs first, const SegArgs* __restrict__ items,
                                                                   int nitems) {
     __shared__ BlockScratch sc;
@@ -889,7 +994,7 @@ __global__ void __launch_bounds__(kThreads, 1) seg_cluster_kernel(SegArgs first,
             vc->ntrace = 0;
         }
         ClusterSyncSeg sy{&st, tr};
-        seg_body<VEC>(a, sy, sc, bc, a.sm_elems > 0 ? reinterpret_cast<float*>(seg_dyn_sm) : nullptr);
+        seg_body<VEC, CMP>(a, sy, sc, bc, a.sm_elems > 0 ? reinterpret_cast<float*>(seg_dyn_sm) : nullptr);
         if (cl.block_rank() == 0 && threadIdx.x == 0 && a.info_out) {
             const unsigned* src = reinterpret_cast<const unsigned*>(&st.info);
             unsigned* dst = reinterpret_cast<unsigned*>(a.info_out);
@@ -907,33 +1012,35 @@ static void allow_res_smem(K kernel) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_bytes(kResMaxElems));
 }
 
-template <bool VEC>
+template <bool VEC, bool CMP>
 static cudaError_t launch_seg_t(const SegArgs& a, int blocks, cudaStream_t stream) {
     static bool attr_set = false;
     if (!attr_set) {
-        allow_res_smem(seg_kernel<VEC>);
+        allow_res_smem(seg_kernel<VEC, CMP>);
         attr_set = true;
     }
     void* args[] = {const_cast<SegArgs*>(&a)};
-    return cudaLaunchCooperativeKernel((void*)seg_kernel<VEC>, dim3(blocks), dim3(kThreads), args,
+    return cudaLaunchCooperativeKernel((void*)seg_kernel<VEC, CMP>, dim3(blocks), dim3(kThreads), args,
                                        res_bytes(a.sm_elems), stream);
 }
 
+// The compaction variant runs when the problem brings its lists (a.cidx).
 cudaError_t launch_seg(const SegArgs& a, int blocks, cudaStream_t stream) {
     bool vec = true;
     auto al = [](const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
     vec = al(a.x) && al(a.g) && al(a.A) && al(a.x_prev) && al(a.g_prev) && al(a.d_prev) && al(a.d_new) &&
           al(a.z) && al(a.zlo) && al(a.z_in) && al(a.x_out);
-    return vec ? launch_seg_t<true>(a, blocks, stream) : launch_seg_t<false>(a, blocks, stream);
+    if (a.cidx) return vec ? launch_seg_t<true, true>(a, blocks, stream) : launch_seg_t<false, true>(a, blocks, stream);
+    return vec ? launch_seg_t<true, false>(a, blocks, stream) : launch_seg_t<false, false>(a, blocks, stream);
 }
 
-template <bool VEC>
+template <bool VEC, bool CMP>
 static cudaError_t launch_clusters_t(const SegArgs& first, const SegArgs* items, int nitems, int ncl, int S,
                                      int sm_elems, cudaStream_t stream) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(seg_cluster_kernel<VEC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        allow_res_smem(seg_cluster_kernel<VEC>);
+        cudaFuncSetAttribute(seg_cluster_kernel<VEC, CMP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        allow_res_smem(seg_cluster_kernel<VEC, CMP>);
         attr_set = true;
     }
     cudaLaunchConfig_t cfg = {};
@@ -948,15 +1055,18 @@ static cudaError_t launch_clusters_t(const SegArgs& first, const SegArgs* items,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, seg_cluster_kernel<VEC>, first, items, nitems);
+    return cudaLaunchKernelEx(&cfg, seg_cluster_kernel<VEC, CMP>, first, items, nitems);
 }
 
 cudaError_t launch_seg_clusters(const SegArgs& first, const SegArgs* items, int nitems, int nclusters, int cluster,
-                                bool vec, cudaStream_t stream, int sm_elems) {
+                                bool vec, cudaStream_t stream, int sm_elems, bool cmp) {
     if (nitems < 1 || nclusters < 1 || cluster < 1 || cluster > 16) return cudaErrorInvalidValue;
     if (sm_elems < 0 || sm_elems > kResMaxElems || (sm_elems & 3)) return cudaErrorInvalidValue;
-    return vec ? launch_clusters_t<true>(first, items, nitems, nclusters, cluster, sm_elems, stream)
-               : launch_clusters_t<false>(first, items, nitems, nclusters, cluster, sm_elems, stream);
+    if (cmp)
+        return vec ? launch_clusters_t<true, true>(first, items, nitems, nclusters, cluster, sm_elems, stream)
+                   : launch_clusters_t<false, true>(first, items, nitems, nclusters, cluster, sm_elems, stream);
+    return vec ? launch_clusters_t<true, false>(first, items, nitems, nclusters, cluster, sm_elems, stream)
+               : launch_clusters_t<false, false>(first, items, nitems, nclusters, cluster, sm_elems, stream);
 }
 
 bool seg_args_aligned(const SegArgs& a) {
@@ -972,13 +1082,13 @@ int seg_cluster_shape(int device, int* cluster, int* max_clusters) {
         *max_clusters = cached_n;
         return 0;
     }
-    cudaFuncSetAttribute(seg_cluster_kernel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    cudaFuncSetAttribute(seg_cluster_kernel<false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(seg_cluster_kernel<true, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaFuncSetAttribute(seg_cluster_kernel<false, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16);
     cfg.blockDim = dim3(kThreads);
     int s = 0;
-    if (cudaOccupancyMaxPotentialClusterSize(&s, seg_cluster_kernel<true>, &cfg) != cudaSuccess || s < 1) s = 8;
+    if (cudaOccupancyMaxPotentialClusterSize(&s, seg_cluster_kernel<true, false>, &cfg) != cudaSuccess || s < 1) s = 8;
     if (s > 16) s = 16;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -989,7 +1099,7 @@ int seg_cluster_shape(int device, int* cluster, int* max_clusters) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nc = 0;
-    if (cudaOccupancyMaxActiveClusters(&nc, seg_cluster_kernel<true>, &cfg) != cudaSuccess || nc < 1) nc = 1;
+    if (cudaOccupancyMaxActiveClusters(&nc, seg_cluster_kernel<true, false>, &cfg) != cudaSuccess || nc < 1) nc = 1;
     cached_dev = device;
     cached_s = s;
     cached_n = nc;
@@ -1002,12 +1112,16 @@ int max_blocks_seg(int device) {
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     // co-resident blocks with the largest residency (a cooperative launch needs them all)
-    allow_res_smem(seg_kernel<true>);
-    allow_res_smem(seg_kernel<false>);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, seg_kernel<true>, kThreads, res_bytes(kResMaxElems));
-    int per2 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, seg_kernel<false>, kThreads, res_bytes(kResMaxElems));
-    per = per < per2 ? per : per2;
+    // every variant must fit the same grid (the cooperative launch needs all blocks resident)
+    per = 1 << 30;
+    const void* ks[4] = {(const void*)seg_kernel<true, false>, (const void*)seg_kernel<false, false>,
+                         (const void*)seg_kernel<true, true>, (const void*)seg_kernel<false, true>};
+    for (const void* k : ks) {
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_bytes(kResMaxElems));
+        int v = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k, kThreads, res_bytes(kResMaxElems));
+        per = v < per ? v : per;
+    }
     if (per < 1) per = 1;
     int nb = sms * per;
     return nb > kMaxBlocks ? kMaxBlocks : nb;
