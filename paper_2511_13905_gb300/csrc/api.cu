@@ -447,6 +447,11 @@ static pgdto_status launch(pgdto_handle* h, bool proj, float* x, const float* g,
         a.timeout_cycles = h->timeout_cycles;
         a.ws = (CoupledWork*)h->work;
         a.eq_mask = h->p.eq_mask;
+        // warm start from the previous step's multipliers, still in the handle's report
+        a.lam_prev = (!proj && h->warm)
+                         ? reinterpret_cast<const double*>(reinterpret_cast<const char*>(h->dev_info) +
+                                                           offsetof(DeviceInfo, lambda))
+                         : nullptr;
         e = launch_coupled(a, h->blocks, h->stream);
     } else {
         SegArgs a;
@@ -487,7 +492,7 @@ extern "C" pgdto_status pgdto_step(pgdto_handle* h, float* x, const float* grad_
     h->cur = 1 - h->cur;  // d_t becomes d_prev
     h->t += 1;
     h->last_was_project = 0;
-    h->warm = h->mode != PGDTO_COUPLED;
+    h->warm = 1;
     if (info) return read_info(h, info, nullptr);
     return PGDTO_OK;
 }

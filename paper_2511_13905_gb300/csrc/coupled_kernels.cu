@@ -219,6 +219,26 @@ __device__ __forceinline__ void set_iterate(volatile CoupledBcast* bc, volatile 
     }
 }
 
+// Warm start: the session's previous step left its multipliers; a design's dual moves little
+// from one step to the next, so Newton starts there (stage 1's single-row candidates are
+// for a cold start).  Inequality multipliers are clamped at 0, equality ones are not.
+template <int M>
+__device__ void cupd_warm_start(const CoupledArgs& a, CoupledWork* ws) {
+    volatile CoupledBcast* bc = &ws->bc;
+    volatile NewtonState* nt = &ws->nt;
+    for (int j = 0; j < M; ++j) {
+        const double l = a.lam_prev[j];
+        nt->lam[j] = ((a.eq_mask >> j) & 1) ? (isfinite(l) ? l : 0.0) : (l > 0.0 ? l : 0.0);
+        bc->active[j] = 0;
+    }
+    bc->any_active = 0;
+    nt->stage = 2;
+    nt->trial = 0;
+    set_iterate(bc, nt, M);
+    bc->mode = kModeEval;
+}
+
+
 // Phase F: accept the first single-row candidate that every row admits (Alg. 2 stage 1);
 // otherwise start stage 2 from all candidates together.
 template <int M>
@@ -792,6 +812,7 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
                 if (threadIdx.x == 0) {
                     volatile CoupledBcast* vb = &ws->bc;
                     if (vb->status != kOk) vb->mode = kModeDone;
+                    else if (a.lam_prev) cupd_warm_start<M>(a, ws);
                     else if (vb->any_active) vb->mode = kModeStage1;
                     else cupd_plan_feasibility<M>(ws);
                     cfinish_if_done<M>(ws);

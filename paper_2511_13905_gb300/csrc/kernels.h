@@ -151,6 +151,7 @@ struct CoupledArgs {
     long long timeout_cycles;
     CoupledWork* ws;
     int eq_mask;          // bit j: row j is an equality (always active, lam_j of either sign)
+    const double* lam_prev;  // warm start: the previous step's lam (device), or null
 };
 
 // Workspace management (sizes in bytes, device-resident, zero-initialised by the host).

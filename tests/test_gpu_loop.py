@@ -194,3 +194,36 @@ def test_warm_started_steps_match_the_oracle(dev):
         passes.append(info.passes)
     h.close()
     assert max(passes) <= 20
+
+
+def test_warm_started_coupled_steps_match_the_oracle(dev):
+    """Consecutive coupled-row steps of one handle start Newton at the previous step's
+    multipliers (warm start); each step equals the oracle's step from the same state."""
+    import torch
+    from paper_2511_13905_gb300 import binding
+    cfg = inputs.config4(dims=(40, 20, 20))
+    n, m = cfg["n"], cfg["m"]
+    h = binding.Handle(n, m, mode="coupled")
+    h.set_state(T(cfg["x_prev"], dev), T(cfg["g_prev"], dev), T(cfg["d_prev"], dev), cfg["t"])
+    x = T(cfg["x"], dev)
+    A = T(cfg["A"], dev)
+    xp, gp, dp = (torch.empty(n, device=dev) for _ in range(3))
+    rng = np.random.default_rng(3)
+    s = rng.lognormal(0.0, 1.0, n)
+    passes = []
+    for k in range(8):
+        x_now = x.cpu().numpy()
+        t_now = h.get_state(xp, gp, dp)
+        g = (-3.0 * x_now.astype(np.float64) ** 2 * s).astype(np.float32)
+        gval = cfg["A"].astype(np.float64) @ x_now.astype(np.float64)
+        st, info = h.step(x, T(g, dev), A, gval, cfg["G"])
+        torch.cuda.synchronize()
+        assert st == 0, (k, info.as_dict(m))
+        ref = oracle_step(x_now, xp.cpu().numpy(), g, gp.cpu().numpy(), dp.cpu().numpy(), cfg["A"], gval, cfg["G"],
+                          t_now, mode="coupled")
+        lam = np.array(list(info.lambda_)[:m])
+        check(parity_errors(x.cpu().numpy(), lam, ref["x_new"], ref["lam"], cfg["A"], ref["b"], C, 0.0, 1.0),
+              "coupled warm k=%d" % k)
+        passes.append(info.passes)
+    h.close()
+    assert passes[-1] <= passes[0] + 2  # the warm start does not make the later steps longer
