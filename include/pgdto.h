@@ -88,7 +88,9 @@ typedef struct {
     int cluster_elems;      /* cluster engine: variables per thread block; a problem's cluster
                                has ceil(n / cluster_elems) blocks rounded up to a power of two,
                                at most 16.  It depends on n alone, so a problem's result is the
-                               same alone and in any batch.  0 = 16384 */
+                               same alone and in any batch.  0 = 8192 (the cluster engine runs
+                               two 256-thread blocks per SM; 8192 variables of a block fit its
+                               share of shared memory) */
     int eq_mask;            /* bit j set: row j is an equality g_j(x) = G_j (Sec. 3.2.4), always
                                active, lambda_j of either sign, and its violation for the
                                fallback rule is |g_j - G_j|; bits at or above m must be 0 */

@@ -61,13 +61,13 @@ struct pgdto_handle {
     cudaEvent_t fork_ev, join_ev[4];
 };
 
-static const int64_t kClusterElemsDefault = 16384;
+static const int64_t kClusterElemsDefault = 8192;
 
 // Residency floats per array for a problem split over nb blocks (0 when a block's share
 // does not fit the shared memory).
-static int res_elems(const int64_t* seg, int m, int nb) {
+static int res_elems(const int64_t* seg, int m, int nb, int cap) {
     const int need = seg_res_need_max(seg, m, nb);
-    return need <= kResMaxElems ? ((need + 3) & ~3) : 0;
+    return need <= cap ? ((need + 3) & ~3) : 0;
 }
 
 // Blocks of a problem's cluster: ceil(n / per_cta) rounded up to a power of two, at most
@@ -230,8 +230,8 @@ extern "C" pgdto_status pgdto_create(pgdto_handle** out, int64_t n, int m, const
         int s_max = 0;
         seg_cluster_shape(h->device, &s_max, &h->cl_max);
         h->cl_size = cluster_size_for(n, p.cluster_elems > 0 ? p.cluster_elems : kClusterElemsDefault, s_max);
-        h->res_grid = res_elems(h->seg, m, h->blocks);
-        h->res_cluster = res_elems(h->seg, m, h->cl_size);
+        h->res_grid = res_elems(h->seg, m, h->blocks, kResMaxElems);
+        h->res_cluster = res_elems(h->seg, m, h->cl_size, kResMaxElemsCluster);
         if (p.engine == 2 || (p.engine == 0 && n <= kClusterMaxN)) h->engine = 2;
     } else if (p.engine == 2) {
         delete h;
@@ -248,7 +248,7 @@ extern "C" pgdto_status pgdto_create(pgdto_handle** out, int64_t n, int m, const
     if (mode != PGDTO_COUPLED && p.compaction && n < (int64_t)0x7fffffff) {
         // compaction lists (32-bit element indices): room for the grid and the cluster layout
         const int64_t lg = (int64_t)h->blocks * seg_list_cta(h->seg, m, h->blocks, kThreads);
-        const int64_t lc = (int64_t)h->cl_size * seg_list_cta(h->seg, m, h->cl_size, kThreads);
+        const int64_t lc = (int64_t)h->cl_size * seg_list_cta(h->seg, m, h->cl_size, kClusterThreads);
         const int nbm = h->blocks > h->cl_size ? h->blocks : h->cl_size;
         if ((e = cudaMalloc(&h->cidx, (size_t)(lg > lc ? lg : lc) * sizeof(int))) != cudaSuccess ||
             (e = cudaMalloc(&h->ccnt, (size_t)nbm * kMaxRows * kThreads * sizeof(int))) != cudaSuccess) {

@@ -22,8 +22,12 @@ namespace pgdto {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
+// The cluster engine runs two 256-thread CTAs per SM: while one CTA's scalar update holds its
+// warps at a barrier, the other CTA's element pass keeps the SM busy.
+constexpr int kClusterThreads = 256;
 constexpr int kMaxBlocks = 1024;
 constexpr int kMaxVals = 136;   // DF values per grid reduction (4 rows x 2 x 16 points + spare)
+constexpr int kMaxBlockVals = 32;  // DF values one block_reduce call gathers per warp
 constexpr int kMaxMax = 8;      // float max values per grid reduction
 
 // status codes shared with include/pgdto.h
@@ -141,7 +145,7 @@ struct Partials {
 
 // Per-block scratch for reductions (shared memory).
 struct BlockScratch {
-    DF warp_vals[kMaxVals][kWarps];
+    DF warp_vals[kMaxBlockVals][kWarps];  // sized for the largest block (512 threads)
     float warp_max[kMaxMax][kWarps];
     DF tot[kMaxVals];
     float totmax[kMaxMax];
@@ -154,7 +158,8 @@ struct BlockScratch {
 template <int NV, int NM>
 __device__ __forceinline__ void block_reduce(const DF (&v)[NV], const float* mx, BlockScratch& sc, int voff = 0,
                                              int moff = 0) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    static_assert(NV <= kMaxBlockVals && NM <= kMaxMax, "block_reduce gathers at most kMaxBlockVals values");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
 #pragma unroll
     for (int i = 0; i < NV; ++i) {
         DF r = warp_reduce_df(v[i]);
@@ -166,13 +171,13 @@ __device__ __forceinline__ void block_reduce(const DF (&v)[NV], const float* mx,
         if (lane == 0) sc.warp_max[i][warp] = r;
     }
     __syncthreads();
-    for (int i = warp; i < NV; i += kWarps) {
-        DF r = lane < kWarps ? sc.warp_vals[i][lane] : df_zero();
+    for (int i = warp; i < NV; i += nw) {
+        DF r = lane < nw ? sc.warp_vals[i][lane] : df_zero();
         r = warp_reduce_df(r);
         if (lane == 0) sc.tot[voff + i] = r;
     }
-    for (int i = warp; i < NM; i += kWarps) {
-        float r = lane < kWarps ? sc.warp_max[i][lane] : -INFINITY;
+    for (int i = warp; i < NM; i += nw) {
+        float r = lane < nw ? sc.warp_max[i][lane] : -INFINITY;
         r = warp_reduce_max(r);
         if (lane == 0) sc.totmax[moff + i] = r;
     }
@@ -202,8 +207,8 @@ __device__ bool grid_reduce_update(GridCtrl* ctrl, Partials* part, BlockScratch&
     }
     __syncthreads();
     if (sc.flag) {
-        const int lane = tid & 31, warp = tid >> 5;
-        for (int i = warp; i < nv; i += kWarps) {
+        const int lane = tid & 31, warp = tid >> 5, nw = (int)(blockDim.x >> 5);
+        for (int i = warp; i < nv; i += nw) {
             DF acc = df_zero();
             // 8 independent loads in flight per lane before they are summed (fixed order)
             for (int b0 = 0; b0 < nb; b0 += 256) {
@@ -219,7 +224,7 @@ __device__ bool grid_reduce_update(GridCtrl* ctrl, Partials* part, BlockScratch&
             acc = warp_reduce_df(acc);
             if (lane == 0) sc.tot[i] = acc;
         }
-        for (int i = warp; i < nm; i += kWarps) {
+        for (int i = warp; i < nm; i += nw) {
             float acc = -INFINITY;
             for (int b = lane; b < nb; b += 32) acc = fmaxf(acc, __ldcg(&part->mx[i][b]));
             acc = warp_reduce_max(acc);
@@ -283,15 +288,15 @@ __device__ void cluster_reduce_update(BlockScratch& sc, int nv, int nm, Update&&
     cl.sync();
     if (cl.block_rank() == 0) {
         const int S = (int)cl.num_blocks();
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int i = warp; i < nv; i += kWarps) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+        for (int i = warp; i < nv; i += nw) {
             DF v = df_zero();
             if (lane < S) v = cl.map_shared_rank(&sc, lane)->tot[i];
             v = warp_reduce_df(v);
             __syncwarp();
             if (lane == 0) sc.tot[i] = v;
         }
-        for (int i = warp; i < nm; i += kWarps) {
+        for (int i = warp; i < nm; i += nw) {
             float v = -INFINITY;
             if (lane < S) v = cl.map_shared_rank(&sc, lane)->totmax[i];
             v = warp_reduce_max(v);

@@ -124,6 +124,8 @@ inline int seg_res_need_max(const int64_t* seg, int nrows, int nb) {
 // Residency capacity per array (floats): three arrays fit next to the static scratch in
 // the 227 KB a CTA may hold.
 constexpr int kResMaxElems = 16384 + 32;
+// The same for the cluster engine, whose two CTAs per SM share the SM's 228 KB.
+constexpr int kResMaxElemsCluster = 8192 + 32;
 
 // Arguments of the coupled-rows (Alg. 2) step / projection kernel.
 struct CoupledArgs {

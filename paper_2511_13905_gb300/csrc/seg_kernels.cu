@@ -977,7 +977,7 @@ __global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
 // Problem 0 travels in the launch parameters (a single problem needs no upload), the rest
 // in `items`.  Each problem's report goes to its info_out.
 template <bool VEC, bool CMP>
-__global__ void __launch_bounds__(kThreads, 1) seg_cluster_kernel(SegArgs first, const SegArgs* __restrict__ items,
+__global__ void __launch_bounds__(kClusterThreads, 2) seg_cluster_kernel(SegArgs first, const SegArgs* __restrict__ items,
                                                                   int nitems) {
     __shared__ BlockScratch sc;
     __shared__ SegBcast bc;
@@ -1006,10 +1006,10 @@ __global__ void __launch_bounds__(kThreads, 1) seg_cluster_kernel(SegArgs first,
 
 static size_t res_bytes(int sm_elems) { return (size_t)3 * (size_t)sm_elems * sizeof(float); }
 
-// Both kernels may take the largest residency; set once per kernel.
+// Each kernel may take its engine's largest residency; set once per kernel.
 template <class K>
-static void allow_res_smem(K kernel) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_bytes(kResMaxElems));
+static void allow_res_smem(K kernel, int cap = kResMaxElems) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_bytes(cap));
 }
 
 template <bool VEC, bool CMP>
@@ -1040,12 +1040,12 @@ static cudaError_t launch_clusters_t(const SegArgs& first, const SegArgs* items,
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(seg_cluster_kernel<VEC, CMP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        allow_res_smem(seg_cluster_kernel<VEC, CMP>);
+        allow_res_smem(seg_cluster_kernel<VEC, CMP>, kResMaxElemsCluster);
         attr_set = true;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ncl * S);
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(kClusterThreads);
     cfg.dynamicSmemBytes = res_bytes(sm_elems);
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
@@ -1061,7 +1061,7 @@ static cudaError_t launch_clusters_t(const SegArgs& first, const SegArgs* items,
 cudaError_t launch_seg_clusters(const SegArgs& first, const SegArgs* items, int nitems, int nclusters, int cluster,
                                 bool vec, cudaStream_t stream, int sm_elems, bool cmp) {
     if (nitems < 1 || nclusters < 1 || cluster < 1 || cluster > 16) return cudaErrorInvalidValue;
-    if (sm_elems < 0 || sm_elems > kResMaxElems || (sm_elems & 3)) return cudaErrorInvalidValue;
+    if (sm_elems < 0 || sm_elems > kResMaxElemsCluster || (sm_elems & 3)) return cudaErrorInvalidValue;
     if (cmp)
         return vec ? launch_clusters_t<true, true>(first, items, nitems, nclusters, cluster, sm_elems, stream)
                    : launch_clusters_t<false, true>(first, items, nitems, nclusters, cluster, sm_elems, stream);
@@ -1086,7 +1086,7 @@ int seg_cluster_shape(int device, int* cluster, int* max_clusters) {
     cudaFuncSetAttribute(seg_cluster_kernel<false, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16);
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(kClusterThreads);
     int s = 0;
     if (cudaOccupancyMaxPotentialClusterSize(&s, seg_cluster_kernel<true, false>, &cfg) != cudaSuccess || s < 1) s = 8;
     if (s > 16) s = 16;

@@ -213,7 +213,7 @@ def test_step_many_every_cluster_size(dev):
     import torch
     from paper_2511_13905_gb300 import binding
     cfgs = [inputs.config1(dims=d, seed_offset=k) for k, d in
-            enumerate([(50, 40), (250, 120), (300, 200), (400, 300), (512, 500), (61, 29), (128, 128)])]
+            enumerate([(50, 40), (120, 100), (250, 120), (300, 200), (400, 300), (61, 29), (128, 64)])]
     hs, xs = [], []
     for c in cfgs:
         h = binding.Handle(c["n"], 1)
