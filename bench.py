@@ -603,7 +603,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--serve-sessions", type=int, default=48)
-    ap.add_argument("--serve-waves", type=int, default=6)
+    ap.add_argument("--serve-waves", type=int, default=12)
     ap.add_argument("--serve-nmax", type=int, default=1 << 20)
     args = ap.parse_args()
     if args.warmup < 3:
