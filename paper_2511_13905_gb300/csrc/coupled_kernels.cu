@@ -713,8 +713,10 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
                 acc.f[5 * j + 3] += aj > 0.0f ? aj * lo : (aj < 0.0f ? aj * hi : 0.0f);
                 acc.f[5 * j + 4] += aj > 0.0f ? aj * hi : (aj < 0.0f ? aj * lo : 0.0f);
                 if (aj != 0.0f) {
-                    mx[2 * j] = fmaxf(mx[2 * j], (aj > 0.0f ? z - lo : z - hi) / aj);
-                    if ((eqm >> j) & 1) mx[2 * j + 1] = fmaxf(mx[2 * j + 1], -(aj > 0.0f ? z - hi : z - lo) / aj);
+                    // saturation bounds: only used widened by 1e-5, so a fast division will do
+                    const float ra = __fdividef(1.0f, aj);
+                    mx[2 * j] = fmaxf(mx[2 * j], (aj > 0.0f ? z - lo : z - hi) * ra);
+                    if ((eqm >> j) & 1) mx[2 * j + 1] = fmaxf(mx[2 * j + 1], -(aj > 0.0f ? z - hi : z - lo) * ra);
                 }
             }
         };

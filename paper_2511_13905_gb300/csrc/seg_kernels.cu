@@ -440,9 +440,10 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 acc.f[3] += av > 0.0f ? av * lo : (av < 0.0f ? av * hi : 0.0f);
                 acc.f[4] += av > 0.0f ? av * hi : (av < 0.0f ? av * lo : 0.0f);
                 if (av != 0.0f) {
-                    const float bp = (av > 0.0f ? z - lo : z - hi) / av;
-                    lsat = fmaxf(lsat, bp);
-                    if (eqj) lnegm = fmaxf(lnegm, -(av > 0.0f ? z - hi : z - lo) / av);
+                    // saturation bounds: only used widened by 1e-5, so a fast division will do
+                    const float ra = __fdividef(1.0f, av);
+                    lsat = fmaxf(lsat, (av > 0.0f ? z - lo : z - hi) * ra);
+                    if (eqj) lnegm = fmaxf(lnegm, -(av > 0.0f ? z - hi : z - lo) * ra);
                 }
             };
             if (a.proj) {
