@@ -849,8 +849,9 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
                         const float w = __fadd_rn(fmaf(-p[k], av, z), zl);
-                        acc.f[k] = fmaf(av, clampf(w, lo, hi), acc.f[k]);
-                        acc.f[K + k] += (w >= lo && w <= hi) ? aa : 0.0f;
+                        const float x = clampf(w, lo, hi);  // free exactly when the clip leaves w
+                        acc.f[k] = fmaf(av, x, acc.f[k]);
+                        acc.f[K + k] += (x == w) ? aa : 0.0f;
                     }
                 };
                 for_chunk<VEC>(
@@ -1042,8 +1043,9 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
 #pragma unroll
                 for (int k = 0; k < K; ++k) {
                     const float wk = fmaf(-p[k], u, w);
-                    acc.f[k] = fmaf(u, clampf(wk, lo, hi), acc.f[k]);
-                    acc.f[K + k] += (wk >= lo && wk <= hi) ? uu : 0.0f;
+                    const float xk = clampf(wk, lo, hi);
+                    acc.f[k] = fmaf(u, xk, acc.f[k]);
+                    acc.f[K + k] += (xk == wk) ? uu : 0.0f;
                 }
             };
             for_chunk<VEC>(

@@ -599,8 +599,9 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
     #pragma unroll
                     for (int k = 0; k < K; ++k) {
                         const float w = __fadd_rn(fmaf(-p[k], av, z), zl);
-                        acc.f[k] = fmaf(av, clampf(w, lo, hi), acc.f[k]);
-                        acc.f[K + 3 + k] += (w >= lo && w <= hi) ? aa : 0.0f;
+                        const float x = clampf(w, lo, hi);  // free exactly when the clip leaves w
+                        acc.f[k] = fmaf(av, x, acc.f[k]);
+                        acc.f[K + 3 + k] += (x == w) ? aa : 0.0f;
                     }
                 };
                 // the K points, then (when classifying) the state at both bracket ends
@@ -766,8 +767,9 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
                         const float w = __fadd_rn(fmaf(-p[k], av, z), zl);
-                        acc.f[k] = fmaf(av, clampf(w, lo, hi), acc.f[k]);
-                        acc.f[K + k] += (w >= lo && w <= hi) ? aa : 0.0f;
+                        const float x = clampf(w, lo, hi);  // free exactly when the clip leaves w
+                        acc.f[k] = fmaf(av, x, acc.f[k]);
+                        acc.f[K + k] += (x == w) ? aa : 0.0f;
                     }
                 };
                 auto run = [&](auto rc, auto lc) {
