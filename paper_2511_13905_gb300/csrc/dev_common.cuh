@@ -275,6 +275,97 @@ __device__ bool grid_reduce_update(GridCtrl* ctrl, Partials* part, BlockScratch&
     return sc.flag != 0;
 }
 
+// Grid-wide all-reduce of sc.tot[0..nv) / sc.totmax[0..nm) followed by the scalar update,
+// which every block runs on its own copy of the state.  Each block publishes its totals in
+// the round's partials buffer and arrives; the last to arrive resets the count and
+// releases the round.  Every block then sums all partials in block order and runs
+// update(sc) on its warp 0: every block computes the same totals and, with the same code
+// on the same inputs, the same state, so no result has to be broadcast.  Rounds alternate
+// between two buffers: a block cannot pass the next round before every block has arrived
+// there, after reading this round's partials, so it is never more than one round ahead.
+// Returns false if the wait was abandoned (timeout or abort); the caller must then return.
+// Block 0 appends the round's completion time to ctrl->trace.
+template <class Update>
+__device__ bool grid_allreduce_update(GridCtrl* ctrl, Partials* part2, BlockScratch& sc, int nv, int nm,
+                                      long long timeout_cycles, Update&& update) {
+    const int tid = threadIdx.x;
+    const int nb = gridDim.x;
+    Partials* part = part2 + (sc.gen & 1u);
+    for (int i = tid; i < nv; i += blockDim.x) part->v[i][blockIdx.x] = make_float2(sc.tot[i].hi, sc.tot[i].lo);
+    for (int i = tid; i < nm; i += blockDim.x) part->mx[i][blockIdx.x] = sc.totmax[i];
+    __syncthreads();
+    if (tid == 0) {
+        // release: the block's partials are visible to whoever observes this arrival
+        fence_acq_rel_gpu();
+        const unsigned old = atom_add_relaxed_u32(&ctrl->count, 1u);
+        const unsigned target = sc.gen + 1u;
+        int ok = 1;
+        if (old == (unsigned)(nb - 1)) {
+            fence_acq_rel_gpu();  // acquire: every other block's partials
+            ctrl->count = 0u;
+            st_release_u32(&ctrl->gen, target);  // orders the reset before the next round's arrivals
+        } else {
+            long long t0 = clock64();
+            unsigned spins = 0;
+            while (ld_acquire_u32(&ctrl->gen) != target) {
+                if (((++spins) & 63u) == 0u) {
+                    if (ld_volatile_i32(&ctrl->abort)) {
+                        ok = 0;
+                        break;
+                    }
+                    if (clock64() - t0 > timeout_cycles) {
+                        atomicExch(&ctrl->status, kErrTimeout);
+                        atomicExch(&ctrl->abort, 1);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        sc.gen = target;
+        sc.flag = ok;
+    }
+    __syncthreads();
+    if (!sc.flag) return false;
+    const int lane = tid & 31, warp = tid >> 5, nw = (int)(blockDim.x >> 5);
+    for (int i = warp; i < nv; i += nw) {
+        DF acc = df_zero();
+        for (int b0 = 0; b0 < nb; b0 += 256) {
+            float2 buf[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int b = b0 + lane + 32 * k;
+                buf[k] = b < nb ? __ldcg(&part->v[i][b]) : make_float2(0.0f, 0.0f);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc = df_add(acc, DF{buf[k].x, buf[k].y});
+        }
+        acc = warp_reduce_df(acc);
+        if (lane == 0) sc.tot[i] = acc;
+    }
+    for (int i = warp; i < nm; i += nw) {
+        float acc = -INFINITY;
+        for (int b = lane; b < nb; b += 32) acc = fmaxf(acc, __ldcg(&part->mx[i][b]));
+        acc = warp_reduce_max(acc);
+        if (lane == 0) sc.totmax[i] = acc;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        update(sc);
+        __syncwarp();
+    }
+    if (tid == 0 && blockIdx.x == 0) {
+        volatile GridCtrl* vc = ctrl;
+        const int k = vc->ntrace;
+        if (k >= 0 && k < 62) {
+            vc->trace[k] = globaltimer_ns();
+            vc->ntrace = k + 1;
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
 // Cluster-wide reduction of sc.tot / sc.totmax followed by the scalar update, for the CTAs
 // of one thread-block cluster.  After a cluster barrier the first CTA reads every CTA's
 // block totals through distributed shared memory (lane r of a warp reads rank r, fixed

@@ -51,8 +51,8 @@ struct SegState {
 
 struct SegWork {
     GridCtrl ctrl;
-    SegState st;
-    Partials part;
+    SegState st;       // the grid engine's report (info) after a launch
+    Partials part[2];  // block partials of alternate rounds
 };
 
 size_t seg_work_bytes() { return sizeof(SegWork); }
@@ -264,21 +264,38 @@ __device__ void report_status_only(SegState* ws, int* sticky, unsigned long long
 // ----------------------------------------------------------------------- element passes
 
 // Grid engine: the CTAs of one cooperative launch share one problem; phases end in a
-// grid-wide reduction through global memory (dev_common.cuh).
+// grid-wide all-reduce through global memory after which every CTA runs the scalar
+// update on its own copy of the search state in shared memory (dev_common.cuh).  Block 0
+// owns the side effects: the sticky status, the launch count and the report, which it
+// copies to global memory when the step ends (publish).
 struct GridSyncSeg {
     SegWork* ws;
     long long timeout;
+    SegState* st;  // this CTA's copy of the search state
     __device__ int rank() const { return blockIdx.x; }
     __device__ int size() const { return gridDim.x; }
-    __device__ SegState* state() const { return &ws->st; }
-    __device__ int* sticky() const { return &ws->ctrl.status; }
-    __device__ unsigned long long* launches() const { return &ws->ctrl.launches; }
+    __device__ SegState* state() const { return st; }
+    __device__ int* sticky() const { return blockIdx.x == 0 ? &ws->ctrl.status : nullptr; }
+    __device__ unsigned long long* launches() const { return blockIdx.x == 0 ? &ws->ctrl.launches : nullptr; }
     template <class F>
     __device__ bool reduce(BlockScratch& sc, int nv, int nm, F&& f) const {
-        SegState* st = &ws->st;
-        return grid_reduce_update(&ws->ctrl, &ws->part, sc, nv, nm, timeout, [&](BlockScratch& s) { f(s, st); });
+        SegState* s0 = st;
+        return grid_allreduce_update(&ws->ctrl, ws->part, sc, nv, nm, timeout, [&](BlockScratch& s) { f(s, s0); });
     }
-    __device__ void fetch(SegBcast& bc) const { load_cg(bc, &ws->st.bc); }
+    __device__ void fetch(SegBcast& bc) const {
+        const unsigned* src = reinterpret_cast<const unsigned*>(&st->bc);
+        unsigned* d = reinterpret_cast<unsigned*>(&bc);
+        for (int i = threadIdx.x; i < (int)(sizeof(SegBcast) / 4); i += blockDim.x) d[i] = src[i];
+        __syncthreads();
+    }
+    // Every thread of every CTA calls this at the end of the step.
+    __device__ void publish() const {
+        if (blockIdx.x != 0) return;
+        __syncthreads();
+        const unsigned* src = reinterpret_cast<const unsigned*>(&st->info);
+        unsigned* d = reinterpret_cast<unsigned*>(&ws->st.info);
+        for (int i = threadIdx.x; i < (int)(sizeof(DeviceInfo) / 4); i += blockDim.x) d[i] = src[i];
+    }
 };
 
 // Cluster engine: the CTAs of one thread-block cluster share one problem; phases end in a
@@ -310,6 +327,7 @@ struct ClusterSyncSeg {
         });
         return true;
     }
+    __device__ void publish() const {}  // the kernel copies the first CTA's report
     __device__ void fetch(SegBcast& bc) const {
         const SegBcast* src = cg::this_cluster().map_shared_rank(&st->bc, 0);
         const unsigned* sw = reinterpret_cast<const unsigned*>(src);
@@ -395,6 +413,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
         sy.fetch(bc);
         if (bc.status != kOk) {
             if (blk == 0 && threadIdx.x == 0) report_status_only(sy.state(), sy.sticky(), sy.launches(), bc.status);
+            sy.publish();
             return;
         }
     }
@@ -551,6 +570,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
         sy.fetch(bc);
         if (bc.status != kOk) {
             if (blk == 0 && threadIdx.x == 0) report_status_only(sy.state(), sy.sticky(), sy.launches(), bc.status);
+            sy.publish();
             return;
         }
     }
@@ -956,12 +976,14 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
         sy.fetch(bc);
         if (!bc.refine) break;
     }
+    sy.publish();
 }
 
 template <bool VEC, bool CMP>
 __global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
     __shared__ BlockScratch sc;
     __shared__ SegBcast bc;
+    __shared__ SegState st;
     SegWork* ws = a.ws;
     if (ld_volatile_i32(&ws->ctrl.abort)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -972,7 +994,12 @@ __global__ void __launch_bounds__(kThreads, 1) seg_kernel(SegArgs a) {
     grid_sync_init(&ws->ctrl, sc);
     // test hook: block 0 never arrives, so every other block's first wait runs out its budget
     if (a.fault_inject == 1 && blockIdx.x == 0) return;
-    GridSyncSeg sy{ws, a.timeout_cycles};
+    {
+        unsigned* w = reinterpret_cast<unsigned*>(&st.info);  // every report field starts defined
+        for (int i = threadIdx.x; i < (int)(sizeof(DeviceInfo) / 4); i += blockDim.x) w[i] = 0u;
+        __syncthreads();
+    }
+    GridSyncSeg sy{ws, a.timeout_cycles, &st};
     seg_body<VEC, CMP>(a, sy, sc, bc, a.sm_elems > 0 ? reinterpret_cast<float*>(seg_dyn_sm) : nullptr);
 }
 
