@@ -388,6 +388,7 @@ static void fill_seg_args(pgdto_handle* h, bool proj, float* x, const float* g, 
     a.x_out = x_out;
     for (int j = 0; j < h->m; ++j) a.bconst[j] = bconst[j];
     a.C = h->p.C;
+    a.two_c = 2.0 / h->p.C;
     a.alpha_max = h->p.alpha_max;
     a.alpha_fb = h->p.alpha_fallback;
     a.eps_alpha = h->p.eps_alpha;
@@ -434,6 +435,7 @@ static pgdto_status launch(pgdto_handle* h, bool proj, float* x, const float* g,
         a.x_out = x_out;
         for (int j = 0; j < h->m; ++j) a.bconst[j] = bconst[j];
         a.C = h->p.C;
+        a.two_c = 2.0 / h->p.C;
         a.alpha_max = h->p.alpha_max;
         a.alpha_fb = h->p.alpha_fallback;
         a.eps_alpha = h->p.eps_alpha;

@@ -107,7 +107,7 @@ __device__ void cupd_after_trial(const CoupledArgs& a, const BlockScratch& sc, C
     volatile RowState* rows = ws->rows;
     const bool row = j < M;
     const int jj = row ? j : 0;
-    const double two_c = 2.0 / a.C;
+    const double two_c = a.two_c;
     const double ax = a.proj ? 0.0 : df_to_double(sc.tot[5 * jj + 0]);
     const double r0s = df_to_double(sc.tot[5 * jj + 1]);
     const double sf = df_to_double(sc.tot[5 * jj + 2]);
@@ -247,7 +247,7 @@ __device__ void cupd_after_feasibility(const CoupledArgs& a, const BlockScratch&
     volatile CoupledBcast* bc = &ws->bc;
     volatile RowState* rows = ws->rows;
     volatile NewtonState* nt = &ws->nt;
-    const double two_c = 2.0 / a.C;
+    const double two_c = a.two_c;
     const int nc = bc->ncand;
     int accepted = -1;
     for (int c = 0; c < nc && accepted < 0; ++c) {
@@ -329,7 +329,7 @@ __device__ void cupd_after_eval(const CoupledArgs& a, const BlockScratch& sc, Co
     volatile CoupledBcast* bc = &ws->bc;
     volatile RowState* rows = ws->rows;
     volatile NewtonState* nt = &ws->nt;
-    const double two_c = 2.0 / a.C;
+    const double two_c = a.two_c;
     double h[M], scale[M];
     bool conv = true;
     for (int j = 0; j < M; ++j) {

@@ -153,6 +153,43 @@ struct BlockScratch {
     unsigned gen;
 };
 
+__host__ __device__ constexpr int pow2_ceil(int n) { return n <= 1 ? 1 : 2 * pow2_ceil((n + 1) / 2); }
+
+// Warp sums of P values per lane by recursive halving: at each of the first log2(P)
+// butterfly steps a lane keeps one half of its values (the upper one when its lane bit
+// for that step is set), sends the other half to its partner and adds the partner's copy
+// of the half it keeps; the remaining steps are plain butterfly additions.  Every value is
+// summed over all 32 lanes by the same fixed tree, with P - 1 + (5 - log2 P) exchanges
+// instead of 5 P.  On return w[0] holds the warp total of value `idx`.
+template <int P, int N, int O>
+struct WarpHalving {
+    __device__ static __forceinline__ void run(DF (&w)[P], int lane, int& idx) {
+        if constexpr (O > 0) {
+            if constexpr (N > 1) {
+                constexpr int H = N / 2;
+                const bool up = (lane & O) != 0;
+#pragma unroll
+                for (int i = 0; i < H; ++i) {
+                    const DF send = up ? w[i] : w[H + i];
+                    const DF keep = up ? w[H + i] : w[i];
+                    DF r;
+                    r.hi = __shfl_xor_sync(0xffffffffu, send.hi, O);
+                    r.lo = __shfl_xor_sync(0xffffffffu, send.lo, O);
+                    w[i] = df_add(keep, r);
+                }
+                if (up) idx += H;
+                WarpHalving<P, H, O / 2>::run(w, lane, idx);
+            } else {
+                DF r;
+                r.hi = __shfl_xor_sync(0xffffffffu, w[0].hi, O);
+                r.lo = __shfl_xor_sync(0xffffffffu, w[0].lo, O);
+                w[0] = df_add(w[0], r);
+                WarpHalving<P, 1, O / 2>::run(w, lane, idx);
+            }
+        }
+    }
+};
+
 // Reduce NV per-thread DF values and NM per-thread maxima (mx may be null when NM == 0);
 // the block totals land in sc.tot[voff + i] and sc.totmax[moff + i].
 template <int NV, int NM>
@@ -160,10 +197,16 @@ __device__ __forceinline__ void block_reduce(const DF (&v)[NV], const float* mx,
                                              int moff = 0) {
     static_assert(NV <= kMaxBlockVals && NM <= kMaxMax, "block_reduce gathers at most kMaxBlockVals values");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+    if constexpr (NV > 0) {
+        constexpr int P = pow2_ceil(NV);
+        static_assert(P <= 32, "one warp sums at most 32 values at once");
+        DF w[P];
 #pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        DF r = warp_reduce_df(v[i]);
-        if (lane == 0) sc.warp_vals[i][warp] = r;
+        for (int i = 0; i < P; ++i) w[i] = i < NV ? v[i] : df_zero();
+        int idx = 0;
+        WarpHalving<P, P, 16>::run(w, lane, idx);
+        // lanes that differ only in the bits of the plain steps hold the same total
+        if (idx < NV && (lane & (32 / P - 1)) == 0) sc.warp_vals[idx][warp] = w[0];
     }
 #pragma unroll
     for (int i = 0; i < NM; ++i) {

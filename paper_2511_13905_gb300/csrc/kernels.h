@@ -42,6 +42,7 @@ struct SegArgs {
     float* x_out;        // projection output
     double bconst[kMaxRows];  // step: G_j - g_j(x_t); projection: b_j
     double C, alpha_max, alpha_fb, eps_alpha, omega, tol_lambda;
+    double two_c;         // 2 / C, the slope of the regulariser term (computed by the host)
     int max_passes;
     int fault_inject;
     long long timeout_cycles;
@@ -148,6 +149,7 @@ struct CoupledArgs {
     float* x_out;
     double bconst[kMaxRows];
     double C, alpha_max, alpha_fb, eps_alpha, omega, tol_lambda, tol_N, c1;
+    double two_c;         // 2 / C (computed by the host)
     int max_passes, maxiter_newton;
     int fault_inject;
     long long timeout_cycles;

@@ -92,7 +92,7 @@ __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, Seg
     volatile RowState* rows = ws->rows;
     const bool row = j < a.nrows;
     const int jj = row ? j : 0;
-    const double two_c = 2.0 / a.C;  // one division, shared by every lane
+    const double two_c = a.two_c;
     const double ax = a.proj ? 0.0 : df_to_double(sc.tot[5 * jj + 0]);
     const double r0s = df_to_double(sc.tot[5 * jj + 1]);
     const double sf = df_to_double(sc.tot[5 * jj + 2]);
@@ -128,14 +128,18 @@ __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, Seg
     }
     const bool closed = down ? rL < 0.0 : (up && rH > 0.0);
     const bool search = row && finite && (up || down) && !closed;
-    // every lane of the group computes the row's first Newton quotients
-    double q = 0.0;
-    if (k == 0) q = rL / SLs;
-    else if (k == 1) q = rH / SHs;
-    const double NL = L + __shfl_sync(kFull, q, lane & ~7);
-    const double NH = H + __shfl_sync(kFull, q, (lane & ~7) + 1);
+    // the row's first Newton quotients and secant offset in one warp-wide division (FP64
+    // issues slowly here; divergent divisions would run one after another): lane k = 0 of
+    // the group divides for the Newton point from L, k = 1 from H, the others the secant
+    const double num = k == 0 ? rL : k == 1 ? rH : rL * (H - L);
+    const double den = k == 0 ? SLs : k == 1 ? SHs : rL - rH;
+    const double q = num / den;
+    const int g0 = lane & ~7;
+    const double NL = L + __shfl_sync(kFull, q, g0);
+    const double NH = H + __shfl_sync(kFull, q, g0 + 1);
+    const double sec = L + __shfl_sync(kFull, q, g0 + 2);
     const double lp = a.lam_prev ? a.lam_prev[jj] : (down ? 1.0 : -1.0);
-    const float p = next_point_warm(lane, L, rL, H, rH, NL, NH, lp);
+    const float p = next_point_warm(lane, L, H, NL, NH, sec, lp);
     if (row && k == 0) {
         ws->info.b[j] = b;
         rows[j].reg = two_c;
@@ -165,72 +169,71 @@ __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, Seg
     }
 }
 
-// After phase D: the report.
+// After phase D: the report.  Lane j < nrows refines row j; lane kMaxRows computes the
+// relative change; both divisions are one warp-wide division (FP64 issues slowly here).
 __device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegState* ws, int* sticky,
                              unsigned long long* launches) {
     const int lane = threadIdx.x;
+    const int nr = a.nrows;
     volatile DeviceInfo* inf = &ws->info;
     volatile RowState* rows = ws->rows;
     volatile SegBcast* bc = &ws->bc;
-    double rc = 0.0;
-    if (lane == 1 && !a.proj) {
-        const double dd = df_to_double(sc.tot[2 * a.nrows]);
-        const double nn = df_to_double(sc.tot[2 * a.nrows + 1]);
-        rc = nn > 0.0 ? sqrt(dd / nn) : INFINITY;
-    }
-    rc = __shfl_sync(kFull, rc, 1);
-    if (lane != 0) return;
+    const bool rl = lane < nr;
+    const int j = rl ? lane : 0;
+    const double ax = df_to_double(sc.tot[j]);
+    const double reg = rows[j].reg, bj = rows[j].b;
+    double lam = rows[j].lam;
+    const double S = df_to_double(sc.tot[nr + j]) + reg;
+    const double r = ax - bj - reg * lam;
+    const double dd = a.proj ? 0.0 : df_to_double(sc.tot[2 * nr]);
+    const double nn = a.proj ? 1.0 : df_to_double(sc.tot[2 * nr + 1]);
+    const bool rcl = lane == kMaxRows;
+    const double q = (rcl ? dd : r) / (rcl ? nn : S);
+    const double rq = sqrt(q);
+    const double rc = __shfl_sync(kFull, a.proj ? 0.0 : (nn > 0.0 ? rq : INFINITY), kMaxRows);
     // One Newton step per searched row on the accurate residual of this pass.  The
     // search's FP32 trial sums carry rounding noise (well under 1e-6 (|b| + |a^T x|)),
     // which can leave its root outside its last bracket by up to that noise over the
     // slope, on a neighbouring linear piece.  A correction within four bracket widths or
     // that noise scale is taken; one larger than 1e-7 lam (the estimate was on another
     // piece) runs this pass again at the corrected lam, at most eight times.
-    int again = 0;
-    double lam_out[kMaxRows];
-    for (int j = 0; j < a.nrows; ++j) {
-        const double ax = df_to_double(sc.tot[j]);
-        double lam = rows[j].lam;
-        const bool eqj = (a.eq_mask >> j) & 1;
-        if (rows[j].how == 2 && (lam > 0.0 || eqj)) {
-            const double reg = rows[j].reg;
-            const double S = df_to_double(sc.tot[a.nrows + j]) + reg;
-            const double r = ax - rows[j].b - reg * lam;
-            const double dl = S > 0.0 ? r / S : 0.0;
-            const double w = (double)rows[j].fH - (double)rows[j].fL;
-            const double noise = S > 0.0 ? 1e-6 * (fabs(rows[j].b) + fabs(ax)) / S : 0.0;
-            if (fabs(dl) <= fmax(4.0 * w, noise) && (lam + dl > 0.0 || eqj)) {
-                lam += dl;
-                if (fabs(dl) > 1e-7 * fabs(lam) && rows[j].nrefine < 8) {
-                    rows[j].nrefine = rows[j].nrefine + 1;
-                    rows[j].lam = lam;
-                    publish_lambda(bc, j, lam);
-                    again = 1;
-                }
+    const bool eqj = (a.eq_mask >> j) & 1;
+    bool again = false;
+    if (rl && rows[j].how == 2 && (lam > 0.0 || eqj)) {
+        const double dl = S > 0.0 ? q : 0.0;
+        const double w = (double)rows[j].fH - (double)rows[j].fL;
+        const bool near = fabs(dl) <= 4.0 * w || (S > 0.0 && fabs(dl) * S <= 1e-6 * (fabs(bj) + fabs(ax)));
+        if (near && (lam + dl > 0.0 || eqj)) {
+            lam += dl;
+            if (fabs(dl) > 1e-7 * fabs(lam) && rows[j].nrefine < 8) {
+                rows[j].nrefine = rows[j].nrefine + 1;
+                rows[j].lam = lam;
+                publish_lambda(bc, j, lam);
+                again = true;
             }
         }
-        lam_out[j] = lam;
     }
-    bc->refine = again;
-    if (again) return;
+    const unsigned again_m = __ballot_sync(kFull, again);
+    if (lane == 0) bc->refine = again_m ? 1 : 0;
+    if (again_m) return;
+    if (lane < kMaxRows) {
+        inf->lambda[lane] = rl ? lam : 0.0;
+        inf->viol[lane] = rl ? ax - bj : 0.0;
+        inf->b[lane] = rl ? bj : 0.0;
+    }
+    const unsigned nconv = __ballot_sync(kFull, rl && rows[j].how == 3);
+    const unsigned nfin = __ballot_sync(kFull, rl && !isfinite(ax));
+    if (lane != 0) return;
     int status = bc->status;
     int passes = 0;
-    double phi = 0.0;
-    for (int j = 0; j < a.nrows; ++j) {
-        const double ax = df_to_double(sc.tot[j]);
-        inf->lambda[j] = lam_out[j];
-        inf->viol[j] = ax - rows[j].b;
-        inf->b[j] = rows[j].b;
-        passes = max(passes, rows[j].passes + rows[j].nrefine);
-        phi = fmax(phi, fabs(rows[j].rlast));
-        if (rows[j].how == 3 && status == kOk) status = kNotConverged;
-        if (!isfinite(ax) && status == kOk) status = kErrNonfinite;
+    double phi = 0.0, vis = 0.0;
+    for (int i = 0; i < nr; ++i) {
+        passes = max(passes, rows[i].passes + rows[i].nrefine);
+        phi = fmax(phi, fabs(rows[i].rlast));
+        vis += rows[i].visited;
     }
-    for (int j = a.nrows; j < kMaxRows; ++j) {
-        inf->lambda[j] = 0.0;
-        inf->viol[j] = 0.0;
-        inf->b[j] = 0.0;
-    }
+    // the first row (in row order) that did not converge or is not finite names the status
+    if ((nconv | nfin) && status == kOk) status = (nconv >> (__ffs(nconv | nfin) - 1)) & 1u ? kNotConverged : kErrNonfinite;
     if (!a.proj) {
         inf->rel_change = rc;
     } else {
@@ -242,8 +245,6 @@ __device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegState*
     }
     inf->phi_inf = phi;
     inf->passes = passes;
-    double vis = 0.0;
-    for (int j = 0; j < a.nrows; ++j) vis += rows[j].visited;
     inf->visited = vis;
     inf->newton_iters = 0;
     inf->stage = 0;
@@ -1241,6 +1242,7 @@ extern "C" pgdto_status pgdto_project_noalloc(int64_t n, int m, const int64_t* s
     a.z_in = z;
     a.x_out = x_out;
     a.C = C;
+    a.two_c = 2.0 / C;
     a.tol_lambda = p.tol_lambda;
     a.max_passes = p.max_passes;
     a.timeout_cycles = (long long)clock_khz * (long long)p.barrier_timeout_ms;

@@ -46,11 +46,16 @@ __device__ void update_step_scalars(const Args& a, const BlockScratch& sc, volat
     const double ss = df_to_double(sc.tot[0]), sy = df_to_double(sc.tot[1]), yy = df_to_double(sc.tot[2]);
     const double gy = df_to_double(sc.tot[3]), pp = df_to_double(sc.tot[4]), gg = df_to_double(sc.tot[5]);
     const double gmax = (double)sc.totmax[0];
-    double q = 0.0;
-    if (lane == 0) q = ss / sy;                                      // BB1 ratio s's / s'y
-    else if (lane == 1) q = yy > 0.0 ? sqrt(ss / yy) : INFINITY;     // ||s|| / ||y||
-    else if (lane == 2) q = pp > 0.0 ? gy / pp : 0.0;                // PR coefficient
-    else if (lane == 3) q = gmax > 0.0 ? a.alpha_fb / gmax : INFINITY;  // fallback alpha_fb / ||g||_inf
+    // the four quotients in one warp-wide division (each lane its own operands): lane 0 the
+    // BB1 ratio s's / s'y, lane 1 s's / y'y (||s|| / ||y|| after the root), lane 2 the PR
+    // coefficient g'y / ||g_prev||^2, lane 3 the fallback alpha_fb / ||g||_inf
+    const double num = lane == 0 ? ss : lane == 1 ? ss : lane == 2 ? gy : a.alpha_fb;
+    const double den = lane == 0 ? sy : lane == 1 ? yy : lane == 2 ? pp : gmax;
+    double q = num / den;
+    const double rq = sqrt(q);
+    if (lane == 1) q = yy > 0.0 ? rq : INFINITY;
+    else if (lane == 2) q = pp > 0.0 ? q : 0.0;
+    else if (lane == 3) q = gmax > 0.0 ? q : INFINITY;
     const double bb = __shfl_sync(kFull, q, 0), lip = __shfl_sync(kFull, q, 1);
     const double pr = __shfl_sync(kFull, q, 2), fbq = __shfl_sync(kFull, q, 3);
     if (lane != 0) return;
@@ -152,18 +157,19 @@ __device__ __forceinline__ float next_point(int lane, double L, double rL, doubl
 // both ends, the secant, the midpoint, and a ladder lp (1 -+ 0.003), lp (1 -+ 0.03) around
 // it, since a design's dual moves little from one step to the next.  Without a usable lp
 // (outside (L, H)) the points are next_point's.  Either way any lp only changes where the
-// first pass looks.  Every lane reaches the one group8_sort (full-warp shuffles).
-__device__ __forceinline__ float next_point_warm(int lane, double L, double rL, double H, double rH, double NL,
-                                                 double NH, double lp) {
+// first pass looks.  Every lane reaches the one group8_sort (full-warp shuffles).  The
+// caller passes the Newton points NL, NH and the secant point sec = L + rL (H - L) / (rL -
+// rH), so that no lane divides here.
+__device__ __forceinline__ float next_point_warm(int lane, double L, double H, double NL, double NH, double sec,
+                                                 double lp) {
     const int k = lane & 7;
     const bool warm = lp > L && lp < H;
     const double w = H - L;
     double v;
     if (k == 0) v = NL;
     else if (k == 1) v = NH;
-    else if (k == 2) v = L + rL * w / (rL - rH);
+    else if (k == 2) v = sec;
     else if (!warm && wide_bracket(L, H)) {
-        const double sec = L + rL * w / (rL - rH);
         const double base = (L == 0.0 && NL > L && NL < H) ? NL : (H == 0.0 && NH > L && NH < H) ? NH : sec;
         v = base * (k == 3 ? 0.125 : k == 4 ? 0.25 : k == 5 ? 0.5 : k == 6 ? 2.0 : 4.0);
     } else if (!warm) v = L + w * (double)(k - 2) * (1.0 / 6.0);
