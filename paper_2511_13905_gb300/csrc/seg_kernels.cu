@@ -424,6 +424,9 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
     // trial point (z_hi, z_lo) and the coefficients there and phases C and D read them
     // back from it instead of global memory (z is then not written to global memory).
     const bool res = sm != nullptr && a.sm_elems > 0 && seg_res_need(a.seg, a.nrows, blk, nb) <= a.sm_elems;
+    // warm start: the first search pass evaluates the ladder around the previous root and
+    // shares phase B's reduction (the lean variant; the compaction variant keeps them apart)
+    const bool ladder = !CMP && !a.proj && a.lam_prev != nullptr;
     float* const smz = sm;
     float* const sml = sm + a.sm_elems;
     float* const sma = sm + 2 * a.sm_elems;
@@ -566,13 +569,16 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
             float mx[2] = {lsat, lnegm};
             block_reduce<5, 2>(acc.d, mx, sc, 5 * j, 2 * j);
         }
-        if (!sy.reduce(sc, 5 * a.nrows, 2 * a.nrows, [&](BlockScratch& s, SegState* st) { update_after_trial(a, s, st); }))
-            return;
-        sy.fetch(bc);
-        if (bc.status != kOk) {
-            if (blk == 0 && threadIdx.x == 0) report_status_only(sy.state(), sy.sticky(), sy.launches(), bc.status);
-            sy.publish();
-            return;
+        if (!ladder) {
+            if (!sy.reduce(sc, 5 * a.nrows, 2 * a.nrows,
+                           [&](BlockScratch& s, SegState* st) { update_after_trial(a, s, st); }))
+                return;
+            sy.fetch(bc);
+            if (bc.status != kOk) {
+                if (blk == 0 && threadIdx.x == 0) report_status_only(sy.state(), sy.sticky(), sy.launches(), bc.status);
+                sy.publish();
+                return;
+            }
         }
     }
 
@@ -769,18 +775,27 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
         // the list bookkeeping in the loop, 2K sums per row)
         const float* zsrc = a.proj ? a.z_in : a.z;
         const bool has_lo = !a.proj;
-        while (bc.any_active) {
+        const int nr = a.nrows;
+        bool lad = ladder;  // this pass evaluates the ladder and completes phase B's round
+        while (lad || bc.any_active) {
             int roff = 0;
-            for (int j = 0; j < a.nrows; ++j) {
+            for (int j = 0; j < nr; ++j) {
                 int64_t cb, ce;
                 block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
                 const int64_t rb = cb & ~int64_t(3);
                 const int off = roff;
                 roff += seg_res_span(cb, ce);
-                if (!bc.active[j]) continue;
                 float p[K];
+                if (lad) {
+                    const float lp = (float)a.lam_prev[j];
+                    if (!ladder_usable(lp)) continue;
 #pragma unroll
-                for (int k = 0; k < K; ++k) p[k] = bc.pts[j][k];
+                    for (int k = 0; k < K; ++k) p[k] = ladder_point(lp, k);
+                } else {
+                    if (!bc.active[j]) continue;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) p[k] = bc.pts[j][k];
+                }
                 AccSplit<K, K, 2, 8> acc;
                 acc.init();
                 auto e = [&](float z, float zl, float av) {
@@ -834,7 +849,41 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                     else run(BoolC<false>{}, BoolC<false>{});
                 }
                 acc.fold();
-                block_reduce<2 * K, 0>(acc.d, nullptr, sc, 2 * K * j, 0);
+                block_reduce<2 * K, 0>(acc.d, nullptr, sc, (lad ? 5 * nr : 0) + 2 * K * j, 0);
+            }
+            if (lad) {
+                // phase B's update, then the ladder pass's: rows that search and had no
+                // usable previous root keep the first points update_after_trial gave them
+                if (!sy.reduce(sc, (5 + 2 * K) * nr, 2 * nr, [&](BlockScratch& s, SegState* st) {
+                        update_after_trial(a, s, st);
+                        __syncwarp();
+                        volatile SegBcast* vb = &st->bc;
+                        volatile RowState* vr = st->rows;
+                        if (vb->status != kOk) return;
+                        const int lane = threadIdx.x, jr = lane >> 3, k = lane & 7;
+                        const int jj = jr < nr ? jr : 0;
+                        const float lp = (float)a.lam_prev[jj];
+                        const bool ev = jr < nr && ladder_usable(lp);
+                        const bool act = jr < nr && vr[jj].active;
+                        if (act && ev) vb->pts[jr][k] = ladder_point(lp, k);
+                        if (ev && k == 0) vr[jr].visited = vr[jr].visited + (double)(a.seg[jr + 1] - a.seg[jr]);
+                        const unsigned hb = __ballot_sync(kFull, k == 0 && act && !ev);
+                        unsigned held = 0u;
+#pragma unroll
+                        for (int r = 0; r < kMaxRows; ++r) held |= ((hb >> (8 * r)) & 1u) << r;
+                        __syncwarp();
+                        search_pass_update<SegBcast, false>(s, 5 * nr, vr, vb, nr, a.tol_lambda, a.max_passes, held);
+                    }))
+                    return;
+                sy.fetch(bc);
+                if (bc.status != kOk) {
+                    if (blk == 0 && threadIdx.x == 0)
+                        report_status_only(sy.state(), sy.sticky(), sy.launches(), bc.status);
+                    sy.publish();
+                    return;
+                }
+                lad = false;
+                continue;
             }
             if (!sy.reduce(sc, 2 * K * a.nrows, 0, [&](BlockScratch& s, SegState* st) {
                     // every element of each active row was visited

@@ -153,6 +153,26 @@ __device__ __forceinline__ float next_point(int lane, double L, double rL, doubl
     return group8_sort(f, lane);
 }
 
+// Warm-start ladder: K points around the previous step's root lp in ascending order,
+// lp (1 -+ 0.003), (1 -+ 0.01), (1 -+ 0.03), (1 -+ 0.1).  They need no bracket, so a step
+// with a usable lp evaluates them in the same pass that forms the trial point (the search's
+// first pass then costs no round of its own).  Computed in FP32 from the rounded lp, the
+// same way by every CTA and by the update that reads the sums.
+__device__ __forceinline__ bool ladder_usable(float lp) { return lp != 0.0f && isfinite(lp); }
+
+__device__ __forceinline__ float ladder_point(float lp, int k) {
+    const int i = lp > 0.0f ? k : K - 1 - k;
+    const float f = i == 0 ? 0.9f
+                  : i == 1 ? 0.97f
+                  : i == 2 ? 0.99f
+                  : i == 3 ? 0.997f
+                  : i == 4 ? 1.003f
+                  : i == 5 ? 1.01f
+                  : i == 6 ? 1.03f
+                  : 1.1f;
+    return lp * f;
+}
+
 // First points of a search that has the previous step's root lp (warm start): Newton from
 // both ends, the secant, the midpoint, and a ladder lp (1 -+ 0.003), lp (1 -+ 0.03) around
 // it, since a design's dual moves little from one step to the next.  Without a usable lp
@@ -297,13 +317,17 @@ __device__ __forceinline__ float next_point_f(int lane, float L, float rL, float
 // CMP: the pass summed only the elements not yet decided (free-set compaction); each row
 // then adds the decided elements' part, C + sum a z - t_k sum a^2, from its row state,
 // and the pass's three extra sums (the elements it decided) join that state.
+// Searches in `held` (bit j) were not evaluated in this pass: they keep their bracket and
+// points and stay active.
 template <class Bcast, bool CMP = false>
 __device__ void search_pass_update(const BlockScratch& sc, int base, volatile RowState* rows, volatile Bcast* bc,
-                                   int nsearch, double tol_lambda, int max_passes) {
+                                   int nsearch, double tol_lambda, int max_passes, unsigned held = 0u) {
     constexpr int stride = CMP ? 2 * K + 4 : 2 * K;
     const int lane = threadIdx.x, j = lane >> 3, k = lane & 7, g0 = lane & ~7;
     const int jj = j < nsearch ? j : 0;
-    const bool row = j < nsearch && rows[jj].active;
+    const bool act = j < nsearch && rows[jj].active;
+    const bool hold = act && ((held >> jj) & 1u);
+    const bool row = act && !hold;
     const float reg = rows[jj].freg;
     const DF b = DF{rows[jj].b_hi, rows[jj].b_lo};
     float L = rows[jj].fL, H = rows[jj].fH, SL = rows[jj].fSL, SH = rows[jj].fSH;
@@ -399,7 +423,7 @@ __device__ void search_pass_update(const BlockScratch& sc, int base, volatile Ro
         }
     }
     if (row && !done) bc->pts[j][k] = p;
-    const unsigned still = __ballot_sync(kFull, row && !done);
+    const unsigned still = __ballot_sync(kFull, (row && !done) || hold);
     if (lane == 0) bc->any_active = still ? 1 : 0;
 }
 
