@@ -69,19 +69,26 @@ struct NewtonState {
     int pad;
 };
 
-struct CoupledWork {
-    GridCtrl ctrl;
+// Search state of one problem.  Every CTA keeps its own copy in shared memory and runs the
+// scalar updates on it after each grid all-reduce (identical totals, identical code, so
+// identical copies); block 0 writes the report to the workspace at the end.
+struct CoupledState {
     CoupledBcast bc;
     RowState rows[kMaxRows];  // stage-1 searches
     RowState ls;              // the line search
     NewtonState nt;
     DeviceInfo info;
-    Partials part;
+};
+
+struct CoupledWork {
+    GridCtrl ctrl;
+    CoupledState st;   // st.info: the report after a launch
+    Partials part[2];  // block partials of alternate rounds
 };
 
 size_t coupled_work_bytes() { return sizeof(CoupledWork); }
 size_t coupled_work_ctrl_bytes() { return sizeof(GridCtrl); }
-DeviceInfo* coupled_work_info(CoupledWork* ws) { return &ws->info; }
+DeviceInfo* coupled_work_info(CoupledWork* ws) { return &ws->st.info; }
 
 // sc.tot layout of each pass
 //   B:   5 per row (a^T x_t, a^T clip(z), free curvature at 0, S_min, S_max), 2 maxima
@@ -101,7 +108,7 @@ __device__ __forceinline__ int jidx(int j, int k) {  // row-major upper-triangle
 // Phase B: inputs of the single-row searches (Alg. 2 stage 1), as for a single row; an
 // equality row (Sec. 3.2.4) with r(0) < 0 searches below 0 (see the single-row kernel).
 template <int M>
-__device__ void cupd_after_trial(const CoupledArgs& a, const BlockScratch& sc, CoupledWork* ws) {
+__device__ void cupd_after_trial(const CoupledArgs& a, const BlockScratch& sc, CoupledState* ws) {
     const int lane = threadIdx.x, j = lane >> 3, k = lane & 7;
     volatile CoupledBcast* bc = &ws->bc;
     volatile RowState* rows = ws->rows;
@@ -187,7 +194,7 @@ __device__ void cupd_after_trial(const CoupledArgs& a, const BlockScratch& sc, C
 
 // Candidates of stage 1 are known: set up the feasibility pass (or finish at lam = 0).
 template <int M>
-__device__ void cupd_plan_feasibility(CoupledWork* ws) {
+__device__ void cupd_plan_feasibility(CoupledState* ws) {
     volatile CoupledBcast* bc = &ws->bc;
     volatile RowState* rows = ws->rows;
     if (threadIdx.x != 0) return;
@@ -223,7 +230,7 @@ __device__ __forceinline__ void set_iterate(volatile CoupledBcast* bc, volatile 
 // from one step to the next, so Newton starts there (stage 1's single-row candidates are
 // for a cold start).  Inequality multipliers are clamped at 0, equality ones are not.
 template <int M>
-__device__ void cupd_warm_start(const CoupledArgs& a, CoupledWork* ws) {
+__device__ void cupd_warm_start(const CoupledArgs& a, CoupledState* ws) {
     volatile CoupledBcast* bc = &ws->bc;
     volatile NewtonState* nt = &ws->nt;
     for (int j = 0; j < M; ++j) {
@@ -242,7 +249,7 @@ __device__ void cupd_warm_start(const CoupledArgs& a, CoupledWork* ws) {
 // Phase F: accept the first single-row candidate that every row admits (Alg. 2 stage 1);
 // otherwise start stage 2 from all candidates together.
 template <int M>
-__device__ void cupd_after_feasibility(const CoupledArgs& a, const BlockScratch& sc, CoupledWork* ws) {
+__device__ void cupd_after_feasibility(const CoupledArgs& a, const BlockScratch& sc, CoupledState* ws) {
     if (threadIdx.x != 0) return;
     volatile CoupledBcast* bc = &ws->bc;
     volatile RowState* rows = ws->rows;
@@ -279,7 +286,7 @@ __device__ void cupd_after_feasibility(const CoupledArgs& a, const BlockScratch&
 // Line search along nt->d from nt->base (nt->lam is reset to base): first points
 // around the Newton step g = 1; phi'(0) = d^T h(base) = d^T J d > 0.
 template <int M>
-__device__ void cstart_line_search(CoupledWork* ws) {
+__device__ void cstart_line_search(CoupledState* ws) {
     volatile CoupledBcast* bc = &ws->bc;
     volatile NewtonState* nt = &ws->nt;
     volatile RowState* ls = &ws->ls;
@@ -324,7 +331,7 @@ __device__ void cstart_line_search(CoupledWork* ws) {
 // At an accepted point: KKT test, then the Newton direction on the working set and the
 // next full step max(lam + d, 0) as the new trial.
 template <int M>
-__device__ void cupd_after_eval(const CoupledArgs& a, const BlockScratch& sc, CoupledWork* ws) {
+__device__ void cupd_after_eval(const CoupledArgs& a, const BlockScratch& sc, CoupledState* ws) {
     if (threadIdx.x != 0) return;
     volatile CoupledBcast* bc = &ws->bc;
     volatile RowState* rows = ws->rows;
@@ -452,7 +459,7 @@ __device__ void cupd_after_eval(const CoupledArgs& a, const BlockScratch& sc, Co
 // takes the cap (closed bracket) or moves the bracket right (open bracket).  Later
 // passes are the shared root search.  When it ends, lam <- max(lam + g d, 0).
 template <int M>
-__device__ void cupd_after_line(const CoupledArgs& a, const BlockScratch& sc, CoupledWork* ws) {
+__device__ void cupd_after_line(const CoupledArgs& a, const BlockScratch& sc, CoupledState* ws) {
     const int lane = threadIdx.x;
     volatile CoupledBcast* bc = &ws->bc;
     volatile NewtonState* nt = &ws->nt;
@@ -533,7 +540,7 @@ __device__ void cupd_after_line(const CoupledArgs& a, const BlockScratch& sc, Co
 
 // When the projection is decided, publish lam for the final pass (thread 0).
 template <int M>
-__device__ __forceinline__ void cfinish_if_done(CoupledWork* ws) {
+__device__ __forceinline__ void cfinish_if_done(CoupledState* ws) {
     volatile CoupledBcast* bc = &ws->bc;
     volatile NewtonState* nt = &ws->nt;
     if (bc->mode != kModeDone) return;
@@ -547,7 +554,8 @@ __device__ __forceinline__ void cfinish_if_done(CoupledWork* ws) {
 
 // After phase D: the report.
 template <int M>
-__device__ void cupd_final(const CoupledArgs& a, const BlockScratch& sc, CoupledWork* ws) {
+__device__ void cupd_final(const CoupledArgs& a, const BlockScratch& sc, CoupledState* ws, int* sticky,
+                           unsigned long long* launches) {
     const int lane = threadIdx.x;
     volatile DeviceInfo* inf = &ws->info;
     volatile RowState* rows = ws->rows;
@@ -589,8 +597,8 @@ __device__ void cupd_final(const CoupledArgs& a, const BlockScratch& sc, Coupled
     inf->newton_iters = nt->iters;
     inf->stage = nt->stage;
     inf->status = status;
-    if (status != kOk) atomicCAS(&ws->ctrl.status, kOk, status);
-    ws->ctrl.launches += 1ull;
+    if (status != kOk && sticky) atomicCAS(sticky, kOk, status);
+    if (launches) *launches += 1ull;
 }
 
 // ----------------------------------------------------------------------- element passes
@@ -599,6 +607,8 @@ template <bool VEC, int M>
 __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
     __shared__ BlockScratch sc;
     __shared__ CoupledBcast bc;
+    __shared__ CoupledState cst;
+    CoupledState* const cs = &cst;
     CoupledWork* ws = a.ws;
     if (ld_volatile_i32(&ws->ctrl.abort)) return;
     const int nb = gridDim.x, blk = blockIdx.x;
@@ -612,6 +622,18 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
     grid_sync_init(&ws->ctrl, sc);
     // test hook: block 0 never arrives, so every other block's first wait runs out its budget
     if (a.fault_inject == 1 && blk == 0) return;
+    {
+        unsigned* w = reinterpret_cast<unsigned*>(&cs->info);  // every report field starts defined
+        for (int i = threadIdx.x; i < (int)(sizeof(DeviceInfo) / 4); i += blockDim.x) w[i] = 0u;
+        __syncthreads();
+    }
+    // the broadcast part of this CTA's state, for the element passes
+    auto fetch = [&]() {
+        const unsigned* src = reinterpret_cast<const unsigned*>(&cs->bc);
+        unsigned* d = reinterpret_cast<unsigned*>(&bc);
+        for (int i = threadIdx.x; i < (int)(sizeof(CoupledBcast) / 4); i += blockDim.x) d[i] = src[i];
+        __syncthreads();
+    };
     int64_t cb, ce;
     block_chunk(0, n, blk, nb, cb, ce);
     const float* zh_src = a.proj ? a.z_in : a.z;
@@ -672,13 +694,13 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
             float mx[1] = {gmax};
             block_reduce<6, 1>(acc.d, mx, sc);
         }
-        if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 6, 1, a.timeout_cycles,
-                                [&](BlockScratch& s) { update_step_scalars(a, s, &ws->bc, &ws->info); }))
+        if (!grid_allreduce_update(&ws->ctrl, ws->part, sc, 6, 1, a.timeout_cycles,
+                                [&](BlockScratch& s) { update_step_scalars(a, s, &cs->bc, &cs->info); }))
             return;
-        load_cg(bc, &ws->bc);
+        fetch();
         if (bc.status != kOk) {
             if (blk == 0 && threadIdx.x == 0) {
-                ws->info.status = bc.status;
+                ws->st.info.status = bc.status;
                 atomicCAS(&ws->ctrl.status, kOk, bc.status);
             }
             return;
@@ -808,23 +830,23 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
 #pragma unroll
         for (int j = 0; j < M; ++j) acc.d[5 * j] = df_add(acc.d[5 * j], fast_two_sum(bsh[j], bsl[j]));
         block_reduce<5 * M, 2 * M>(acc.d, mx, sc);
-        if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 5 * M, 2 * M, a.timeout_cycles, [&](BlockScratch& s) {
-                cupd_after_trial<M>(a, s, ws);
+        if (!grid_allreduce_update(&ws->ctrl, ws->part, sc, 5 * M, 2 * M, a.timeout_cycles, [&](BlockScratch& s) {
+                cupd_after_trial<M>(a, s, cs);
                 __syncwarp();
                 if (threadIdx.x == 0) {
-                    volatile CoupledBcast* vb = &ws->bc;
+                    volatile CoupledBcast* vb = &cs->bc;
                     if (vb->status != kOk) vb->mode = kModeDone;
-                    else if (a.lam_prev) cupd_warm_start<M>(a, ws);
+                    else if (a.lam_prev) cupd_warm_start<M>(a, cs);
                     else if (vb->any_active) vb->mode = kModeStage1;
-                    else cupd_plan_feasibility<M>(ws);
-                    cfinish_if_done<M>(ws);
+                    else cupd_plan_feasibility<M>(cs);
+                    cfinish_if_done<M>(cs);
                 }
             }))
             return;
-        load_cg(bc, &ws->bc);
+        fetch();
         if (bc.status != kOk) {
             if (blk == 0 && threadIdx.x == 0) {
-                ws->info.status = bc.status;
+                ws->st.info.status = bc.status;
                 atomicCAS(&ws->ctrl.status, kOk, bc.status);
             }
             return;
@@ -872,15 +894,15 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
                 acc.fold();
                 block_reduce<2 * K, 0>(acc.d, nullptr, sc, 2 * K * j, 0);
             }
-            if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 2 * K * M, 0, a.timeout_cycles,
+            if (!grid_allreduce_update(&ws->ctrl, ws->part, sc, 2 * K * M, 0, a.timeout_cycles,
                                     [&](BlockScratch& s) {
-                                        search_pass_update(s, 0, ws->rows, &ws->bc, M, a.tol_lambda, a.max_passes);
+                                        search_pass_update(s, 0, cs->rows, &cs->bc, M, a.tol_lambda, a.max_passes);
                                         __syncwarp();
                                         if (threadIdx.x == 0) {
-                                            volatile NewtonState* nt = &ws->nt;
+                                            volatile NewtonState* nt = &cs->nt;
                                             nt->passes = nt->passes + 1;
-                                            if (!ws->bc.any_active) cupd_plan_feasibility<M>(ws);
-                                            cfinish_if_done<M>(ws);
+                                            if (!cs->bc.any_active) cupd_plan_feasibility<M>(cs);
+                                            cfinish_if_done<M>(cs);
                                         }
                                     }))
                 return;
@@ -937,12 +959,12 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
                 });
             acc.fold();
             block_reduce<M * M, 0>(acc.d, nullptr, sc);
-            if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, M * M, 0, a.timeout_cycles, [&](BlockScratch& s) {
-                    cupd_after_feasibility<M>(a, s, ws);
+            if (!grid_allreduce_update(&ws->ctrl, ws->part, sc, M * M, 0, a.timeout_cycles, [&](BlockScratch& s) {
+                    cupd_after_feasibility<M>(a, s, cs);
                     if (threadIdx.x == 0) {
-                        volatile NewtonState* nt = &ws->nt;
+                        volatile NewtonState* nt = &cs->nt;
                         nt->passes = nt->passes + 1;
-                        cfinish_if_done<M>(ws);
+                        cfinish_if_done<M>(cs);
                     }
                 }))
                 return;
@@ -1007,13 +1029,13 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
                 });
             acc.fold();
             block_reduce<2 * M + NJ, 0>(acc.d, nullptr, sc);
-            if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 2 * M + NJ, 0, a.timeout_cycles,
+            if (!grid_allreduce_update(&ws->ctrl, ws->part, sc, 2 * M + NJ, 0, a.timeout_cycles,
                                     [&](BlockScratch& s) {
-                                        cupd_after_eval<M>(a, s, ws);
+                                        cupd_after_eval<M>(a, s, cs);
                                         if (threadIdx.x == 0) {
-                                            volatile NewtonState* nt = &ws->nt;
+                                            volatile NewtonState* nt = &cs->nt;
                                             nt->passes = nt->passes + 1;
-                                            cfinish_if_done<M>(ws);
+                                            cfinish_if_done<M>(cs);
                                         }
                                     }))
                 return;
@@ -1075,13 +1097,13 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
                 });
             acc.fold();
             block_reduce<2 * K, 0>(acc.d, nullptr, sc);
-            if (!grid_reduce_update(&ws->ctrl, &ws->part, sc, 2 * K, 0, a.timeout_cycles, [&](BlockScratch& s) {
-                    cupd_after_line<M>(a, s, ws);
-                    if (threadIdx.x == 0) cfinish_if_done<M>(ws);
+            if (!grid_allreduce_update(&ws->ctrl, ws->part, sc, 2 * K, 0, a.timeout_cycles, [&](BlockScratch& s) {
+                    cupd_after_line<M>(a, s, cs);
+                    if (threadIdx.x == 0) cfinish_if_done<M>(cs);
                 }))
                 return;
         }
-        load_cg(bc, &ws->bc);
+        fetch();
         if (bc.status != kOk) break;
     }
 
@@ -1147,8 +1169,16 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
             });
         acc.fold();
         block_reduce<M + 2, 0>(acc.d, nullptr, sc);
-        grid_reduce_update(&ws->ctrl, &ws->part, sc, M + 2, 0, a.timeout_cycles,
-                           [&](BlockScratch& s) { cupd_final<M>(a, s, ws); });
+        const bool fin = grid_allreduce_update(&ws->ctrl, ws->part, sc, M + 2, 0, a.timeout_cycles,
+                                               [&](BlockScratch& s) {
+                                                   cupd_final<M>(a, s, cs, blk == 0 ? &ws->ctrl.status : nullptr,
+                                                                 blk == 0 ? &ws->ctrl.launches : nullptr);
+                                               });
+        if (fin && blk == 0) {
+            const unsigned* src = reinterpret_cast<const unsigned*>(&cs->info);
+            unsigned* d = reinterpret_cast<unsigned*>(&ws->st.info);
+            for (int i = threadIdx.x; i < (int)(sizeof(DeviceInfo) / 4); i += blockDim.x) d[i] = src[i];
+        }
     }
 }
 

@@ -5,11 +5,12 @@
 //    so reductions over millions of FP32 terms keep ~44 bits without FP64 arithmetic
 //    (FP64 throughput is a small fraction of FP32 on this part);
 //  * warp / block reductions of DF values;
-//  * a grid-wide "last block reduces" step: every block writes its partial sums, arrives
-//    on a counter, and the last block to arrive reduces all partials in a fixed order,
-//    runs the scalar update and releases the others.  Waits are bounded: a block that has
-//    waited longer than its budget records PGDTO_ERR_TIMEOUT, raises an abort flag and
-//    returns, so a fault elsewhere never hangs the GPU.
+//  * a grid-wide all-reduce step: every block writes its partial sums and arrives on a
+//    counter; once all have arrived, every block sums all partials in a fixed order and
+//    runs the scalar update on its own copy of the search state, so no result is
+//    broadcast.  Waits are bounded: a block that has waited longer than its budget
+//    records PGDTO_ERR_TIMEOUT, raises an abort flag and returns, so a fault elsewhere
+//    never hangs the GPU.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -123,7 +124,7 @@ struct GridCtrl {
     int abort;         // raised by a block that gave up; every wait then returns
     unsigned long long launches;  // kernels that ran to completion (diagnostics)
     int pad1[26];
-    unsigned gen;      // round counter, bumped by the last block (own 128-byte line: the
+    unsigned gen;      // round counter, bumped by the last block to arrive (own 128-byte line: the
     int pad2[31];      // waiting blocks poll it while the others still arrive on `count`)
     unsigned long long trace_start;  // globaltimer at kernel entry (block 0)
     unsigned long long trace[62];    // globaltimer after each grid reduction's update
@@ -225,97 +226,6 @@ __device__ __forceinline__ void block_reduce(const DF (&v)[NV], const float* mx,
         if (lane == 0) sc.totmax[moff + i] = r;
     }
     __syncthreads();
-}
-
-// Grid-wide reduction of sc.tot[0..nv) / sc.totmax[0..nm) followed by a scalar update.
-// Every block calls it with its block totals in sc.  The last block to arrive reduces all
-// partials in block order (deterministic), calls update(sc) on its warp 0 with the grid
-// totals in sc.tot / sc.totmax, and releases the others.  Returns false if the wait
-// was abandoned (timeout or abort); the caller must then return.
-template <class Update>
-__device__ bool grid_reduce_update(GridCtrl* ctrl, Partials* part, BlockScratch& sc, int nv, int nm,
-                                   long long timeout_cycles, Update&& update) {
-    const int tid = threadIdx.x;
-    const int nb = gridDim.x;
-    for (int i = tid; i < nv; i += blockDim.x) part->v[i][blockIdx.x] = make_float2(sc.tot[i].hi, sc.tot[i].lo);
-    for (int i = tid; i < nm; i += blockDim.x) part->mx[i][blockIdx.x] = sc.totmax[i];
-    __syncthreads();
-    if (tid == 0) {
-        // release: the block's partials (ordered before by the barrier above) are visible to
-        // whoever observes this arrival; sc.gen is tracked by the block itself (grid_sync_init)
-        fence_acq_rel_gpu();
-        const unsigned old = atom_add_relaxed_u32(&ctrl->count, 1u);
-        sc.flag = (old == (unsigned)(nb - 1)) ? 1 : 0;
-        if (sc.flag) fence_acq_rel_gpu();  // acquire: every other block's partials
-    }
-    __syncthreads();
-    if (sc.flag) {
-        const int lane = tid & 31, warp = tid >> 5, nw = (int)(blockDim.x >> 5);
-        for (int i = warp; i < nv; i += nw) {
-            DF acc = df_zero();
-            // 8 independent loads in flight per lane before they are summed (fixed order)
-            for (int b0 = 0; b0 < nb; b0 += 256) {
-                float2 buf[8];
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int b = b0 + lane + 32 * k;
-                    buf[k] = b < nb ? __ldcg(&part->v[i][b]) : make_float2(0.0f, 0.0f);
-                }
-#pragma unroll
-                for (int k = 0; k < 8; ++k) acc = df_add(acc, DF{buf[k].x, buf[k].y});
-            }
-            acc = warp_reduce_df(acc);
-            if (lane == 0) sc.tot[i] = acc;
-        }
-        for (int i = warp; i < nm; i += nw) {
-            float acc = -INFINITY;
-            for (int b = lane; b < nb; b += 32) acc = fmaxf(acc, __ldcg(&part->mx[i][b]));
-            acc = warp_reduce_max(acc);
-            if (lane == 0) sc.totmax[i] = acc;
-        }
-        __syncthreads();
-        if (tid < 32) {
-            update(sc);  // warp 0: the scalar update spreads its work over the lanes
-            __syncwarp();
-        }
-        if (tid == 0) {
-            volatile GridCtrl* vc = ctrl;
-            const int k = vc->ntrace;
-            if (k >= 0 && k < 62) {
-                vc->trace[k] = globaltimer_ns();
-                vc->ntrace = k + 1;
-            }
-            ctrl->count = 0u;
-            st_release_u32(&ctrl->gen, sc.gen + 1u);  // orders the reset, the update and the trace
-            sc.gen = sc.gen + 1u;
-        }
-        __syncthreads();
-        return true;
-    }
-    if (tid == 0) {
-        const unsigned target = sc.gen + 1u;
-        long long t0 = clock64();
-        int ok = 1;
-        unsigned spins = 0;
-        while (ld_acquire_u32(&ctrl->gen) != target) {
-            if (((++spins) & 63u) == 0u) {
-                if (ld_volatile_i32(&ctrl->abort)) {
-                    ok = 0;
-                    break;
-                }
-                if (clock64() - t0 > timeout_cycles) {
-                    atomicExch(&ctrl->status, kErrTimeout);
-                    atomicExch(&ctrl->abort, 1);
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        sc.gen = target;
-        sc.flag = ok;
-    }
-    __syncthreads();
-    return sc.flag != 0;
 }
 
 // Grid-wide all-reduce of sc.tot[0..nv) / sc.totmax[0..nm) followed by the scalar update,
@@ -451,16 +361,6 @@ __device__ void cluster_reduce_update(BlockScratch& sc, int nv, int nm, Update&&
 // round counter is read while no round can have completed (this block has not arrived).
 __device__ __forceinline__ void grid_sync_init(GridCtrl* ctrl, BlockScratch& sc) {
     if (threadIdx.x == 0) sc.gen = ld_acquire_u32(&ctrl->gen);
-    __syncthreads();
-}
-
-// Copy a small struct written by the last block (global) into shared memory through L2.
-template <class T>
-__device__ __forceinline__ void load_cg(T& dst, const T* src) {
-    static_assert(sizeof(T) % 4 == 0, "word-sized struct expected");
-    const unsigned* s = reinterpret_cast<const unsigned*>(src);
-    unsigned* d = reinterpret_cast<unsigned*>(&dst);
-    for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x) d[i] = __ldcg(s + i);
     __syncthreads();
 }
 

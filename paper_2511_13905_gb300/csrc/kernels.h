@@ -8,7 +8,7 @@ namespace pgdto {
 
 constexpr int kMaxRows = 4;
 
-// Report written by the last block of a step or projection; same layout as pgdto_info.
+// Report of a step or projection (written by block 0 at the end); same layout as pgdto_info.
 struct DeviceInfo {
     double alpha, beta;
     double lambda[kMaxRows], b[kMaxRows], viol[kMaxRows];

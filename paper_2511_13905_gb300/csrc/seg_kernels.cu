@@ -9,13 +9,14 @@
 //            state copies; per row a^T x_t (for b), r(0) (Alg. 1 feasibility test), the
 //            free-set curvature at 0 and the saturation bound of Alg. 1's bracket
 //   phase C  root-search passes over z and a: r(lam_k) = a^T clip(z - lam_k a) - b - 2 lam_k/C
-//            and its slope at K points per pass; the last block moves the bracket, stops
+//            and its slope at K points per pass; the scalar update moves the bracket, stops
 //            when both ends lie on one linear piece, and picks the next points
 //   phase D  one pass: x_{t+1} = clip(x + c(beta d_prev - g) - lam a) evaluated in
 //            double-float arithmetic, a^T x_{t+1}, ||x_{t+1} - x_t||^2, ||x_{t+1}||^2
 //
 // The projection-only entry runs B (without the step part), C and D on a given z.
-// Each phase ends in one grid-wide reduction (dev_common.cuh).
+// Each phase ends in one grid-wide reduction (dev_common.cuh); with a warm start the first
+// search pass is evaluated right after phase B and shares its reduction.
 #include <float.h>
 #include <math.h>
 #include <string.h>
@@ -67,11 +68,12 @@ __device__ __forceinline__ bool all_finite(const BlockScratch& sc, int nv) {
 
 // ----------------------------------------------------------------------- scalar updates
 //
-// The updates run on warp 0 of the last block.  FP64 throughput is a small fraction of
-// FP32 on this part and a division is a long dependent sequence, so the work is spread
-// over lanes: lane 8j + k handles trial point k of row j (4 rows x 8 points = 32 lanes),
-// per-row quantities are computed redundantly by the 8 lanes of the row's group, and no
-// lane waits on more than one FP64 division per pass.
+// The updates run on warp 0 of every block (grid engine) or of the cluster's first block.
+// FP64 throughput is a small fraction of FP32 on this part, a division is a long
+// dependent sequence, and a warp instruction costs the same whatever its active lanes, so
+// the work is spread over lanes: lane 8j + k handles trial point k of row j (4 rows x 8
+// points = 32 lanes), per-row quantities are computed redundantly by the 8 lanes of the
+// row's group, and each update issues one warp-wide FP64 division.
 
 __device__ __forceinline__ void publish_lambda(volatile SegBcast* bc, int j, double lam) {
     float h, l;

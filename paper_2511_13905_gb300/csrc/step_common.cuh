@@ -32,11 +32,12 @@ __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fm
 
 // ----------------------------------------------------------------------- scalar updates
 //
-// The updates run on warp 0 of the last block.  FP64 throughput is a small fraction of
-// FP32 on this part and a division is a long dependent sequence, so the work is spread
-// over lanes: lane 8j + k handles trial point k of search j (4 searches x 8 points = 32
-// lanes), per-search quantities are computed redundantly by the 8 lanes of the group,
-// and no lane waits on more than one FP64 division per pass.
+// The updates run on warp 0 of every block (grid engine) or of the cluster's first block.
+// FP64 throughput is a small fraction of FP32 on this part, a division is a long
+// dependent sequence, and a warp instruction costs the same whatever its active lanes, so
+// the work is spread over lanes: lane 8j + k handles trial point k of search j (4
+// searches x 8 points = 32 lanes), per-search quantities are computed redundantly by the 8
+// lanes of the group, and each update issues one warp-wide FP64 division.
 
 // Step size and PR+ coefficient (Alg. 3; eq. final_alpha, eq. alpha, eq. CG).
 template <class Args, class Bcast>
