@@ -364,6 +364,15 @@ extern "C" pgdto_status pgdto_last_info(pgdto_handle* h, pgdto_info* info, doubl
     return read_info(h, info, lambda_out);
 }
 
+// The step parameters the device works with in double-float: (hi, lo) float pairs.
+static void fill_step_df(const pgdto_params& p, float* out) {
+    const double v[4] = {p.alpha_max, p.alpha_fallback, p.eps_alpha, p.omega};
+    for (int i = 0; i < 4; ++i) {
+        out[2 * i] = (float)v[i];
+        out[2 * i + 1] = (float)(v[i] - (double)out[2 * i]);
+    }
+}
+
 static void fill_seg_args(pgdto_handle* h, bool proj, float* x, const float* g, const float* A,
                           const double* bconst, const float* z_in, float* x_out, bool force_fallback, SegArgs& a) {
     memset(&a, 0, sizeof(a));
@@ -389,6 +398,7 @@ static void fill_seg_args(pgdto_handle* h, bool proj, float* x, const float* g, 
     for (int j = 0; j < h->m; ++j) a.bconst[j] = bconst[j];
     a.C = h->p.C;
     a.two_c = 2.0 / h->p.C;
+    fill_step_df(h->p, a.step_df);
     a.alpha_max = h->p.alpha_max;
     a.alpha_fb = h->p.alpha_fallback;
     a.eps_alpha = h->p.eps_alpha;
@@ -436,6 +446,7 @@ static pgdto_status launch(pgdto_handle* h, bool proj, float* x, const float* g,
         for (int j = 0; j < h->m; ++j) a.bconst[j] = bconst[j];
         a.C = h->p.C;
         a.two_c = 2.0 / h->p.C;
+        fill_step_df(h->p, a.step_df);
         a.alpha_max = h->p.alpha_max;
         a.alpha_fb = h->p.alpha_fallback;
         a.eps_alpha = h->p.eps_alpha;

@@ -32,8 +32,8 @@ namespace pgdto {
 enum CoupledMode : int { kModeDone = 0, kModeStage1 = 1, kModeFeas = 2, kModeEval = 3, kModeLine = 4 };
 
 struct CoupledBcast {
-    // step scalars (field names shared with the single-row kernel's templates)
-    double alpha, beta, c;
+    // step scalars c = omega alpha and beta as float pairs (field names shared with the
+    // single-row kernel's templates)
     float c_hi, c_lo, beta_hi, beta_lo;
     int branch, status;
     int any_active;  // root searches still running (stage 1 or line search)

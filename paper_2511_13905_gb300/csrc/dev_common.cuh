@@ -68,6 +68,35 @@ __device__ __forceinline__ DF df_add_f(DF a, float b) {
 
 __device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
 
+// a * b to double-float accuracy (the product of the hi parts exact via FMA).
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    const float p = a.hi * b.hi;
+    const float e = fmaf(a.hi, b.hi, -p);
+    return fast_two_sum(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
+}
+
+// a / b to double-float accuracy: q1 = a.hi / b.hi, then one correction from the exact
+// remainder a - q1 b.
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const float p = q1 * b.hi;
+    DF r = df_add(a, DF{-p, -fmaf(q1, b.hi, -p)});
+    r = df_add_f(r, -q1 * b.lo);
+    return fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+
+// sqrt(a) for a > 0 to double-float accuracy: s = sqrt(a.hi), then one Newton correction
+// (a - s^2) / (2 s) from the exact square.
+__device__ __forceinline__ DF df_sqrt(DF a) {
+    const float s = __fsqrt_rn(a.hi);
+    const float p = s * s;
+    const DF r = df_add(a, DF{-p, -fmaf(s, s, -p)});
+    return fast_two_sum(s, __fdiv_rn(r.hi, 2.0f * s));
+}
+
+__device__ __forceinline__ bool df_lt(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ DF df_min(DF a, DF b) { return df_lt(b, a) ? b : a; }
+
 // Split a double into hi + lo floats (hi = nearest float, lo = nearest float of the rest).
 __device__ __host__ __forceinline__ void split_double(double v, float& hi, float& lo) {
     hi = (float)v;

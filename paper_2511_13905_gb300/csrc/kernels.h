@@ -43,6 +43,7 @@ struct SegArgs {
     double bconst[kMaxRows];  // step: G_j - g_j(x_t); projection: b_j
     double C, alpha_max, alpha_fb, eps_alpha, omega, tol_lambda;
     double two_c;         // 2 / C, the slope of the regulariser term (computed by the host)
+    float step_df[8];     // alpha_max, alpha_fb, eps_alpha, omega as (hi, lo) float pairs
     int max_passes;
     int fault_inject;
     long long timeout_cycles;
@@ -150,6 +151,7 @@ struct CoupledArgs {
     double bconst[kMaxRows];
     double C, alpha_max, alpha_fb, eps_alpha, omega, tol_lambda, tol_N, c1;
     double two_c;         // 2 / C (computed by the host)
+    float step_df[8];     // alpha_max, alpha_fb, eps_alpha, omega as (hi, lo) float pairs
     int max_passes, maxiter_newton;
     int fault_inject;
     long long timeout_cycles;

@@ -32,8 +32,7 @@ namespace cg = cooperative_groups;
 namespace pgdto {
 
 struct SegBcast {
-    double alpha, beta, c;
-    float c_hi, c_lo, beta_hi, beta_lo;
+    float c_hi, c_lo, beta_hi, beta_lo;  // step scalars c = omega alpha and beta as float pairs
     int branch, any_active, status, refine;  // refine: phase D runs again at the refined lam
     float pts[kMaxRows][K];
     int active[kMaxRows];

@@ -39,59 +39,60 @@ __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fm
 // searches x 8 points = 32 lanes), per-search quantities are computed redundantly by the 8
 // lanes of the group, and each update issues one warp-wide FP64 division.
 
-// Step size and PR+ coefficient (Alg. 3; eq. final_alpha, eq. alpha, eq. CG).
+// Step size and PR+ coefficient (Alg. 3; eq. final_alpha, eq. alpha, eq. CG), in
+// double-float arithmetic (FP32 pipes; FP64 issues slowly here): the quotients to about
+// 1e-14, far below what the FP32 trial point z = x + omega alpha d resolves.
 template <class Args, class Bcast>
 __device__ void update_step_scalars(const Args& a, const BlockScratch& sc, volatile Bcast* bc,
                                     volatile DeviceInfo* inf) {
     const int lane = threadIdx.x;
-    const double ss = df_to_double(sc.tot[0]), sy = df_to_double(sc.tot[1]), yy = df_to_double(sc.tot[2]);
-    const double gy = df_to_double(sc.tot[3]), pp = df_to_double(sc.tot[4]), gg = df_to_double(sc.tot[5]);
-    const double gmax = (double)sc.totmax[0];
+    const DF ss = sc.tot[0], sy = sc.tot[1], yy = sc.tot[2], gy = sc.tot[3], pp = sc.tot[4], gg = sc.tot[5];
+    const float gmax = sc.totmax[0];
+    const DF amax = DF{a.step_df[0], a.step_df[1]}, afb = DF{a.step_df[2], a.step_df[3]};
+    const DF eps = DF{a.step_df[4], a.step_df[5]}, om = DF{a.step_df[6], a.step_df[7]};
     // the four quotients in one warp-wide division (each lane its own operands): lane 0 the
     // BB1 ratio s's / s'y, lane 1 s's / y'y (||s|| / ||y|| after the root), lane 2 the PR
     // coefficient g'y / ||g_prev||^2, lane 3 the fallback alpha_fb / ||g||_inf
-    const double num = lane == 0 ? ss : lane == 1 ? ss : lane == 2 ? gy : a.alpha_fb;
-    const double den = lane == 0 ? sy : lane == 1 ? yy : lane == 2 ? pp : gmax;
-    double q = num / den;
-    const double rq = sqrt(q);
-    if (lane == 1) q = yy > 0.0 ? rq : INFINITY;
-    else if (lane == 2) q = pp > 0.0 ? q : 0.0;
-    else if (lane == 3) q = gmax > 0.0 ? q : INFINITY;
-    const double bb = __shfl_sync(kFull, q, 0), lip = __shfl_sync(kFull, q, 1);
-    const double pr = __shfl_sync(kFull, q, 2), fbq = __shfl_sync(kFull, q, 3);
+    const DF num = lane == 0 ? ss : lane == 1 ? ss : lane == 2 ? gy : afb;
+    const DF den = lane == 0 ? sy : lane == 1 ? yy : lane == 2 ? pp : DF{gmax, 0.0f};
+    DF q = df_div(num, den);
+    const DF rq = df_sqrt(q);
+    const DF inf_df = DF{INFINITY, 0.0f};
+    if (lane == 1) q = yy.hi > 0.0f ? rq : inf_df;
+    else if (lane == 2) q = pp.hi > 0.0f ? q : df_zero();
+    else if (lane == 3) q = gmax > 0.0f ? q : inf_df;
+    const DF bb = DF{__shfl_sync(kFull, q.hi, 0), __shfl_sync(kFull, q.lo, 0)};
+    const DF lip = DF{__shfl_sync(kFull, q.hi, 1), __shfl_sync(kFull, q.lo, 1)};
+    const DF pr = DF{__shfl_sync(kFull, q.hi, 2), __shfl_sync(kFull, q.lo, 2)};
+    const DF fbq = DF{__shfl_sync(kFull, q.hi, 3), __shfl_sync(kFull, q.lo, 3)};
     if (lane != 0) return;
     int status = kOk;
-    if (!(isfinite(ss) && isfinite(sy) && isfinite(yy) && isfinite(gy) && isfinite(pp) && isfinite(gg)))
+    if (!(isfinite(ss.hi) && isfinite(sy.hi) && isfinite(yy.hi) && isfinite(gy.hi) && isfinite(pp.hi) &&
+          isfinite(gg.hi)))
         status = kErrNonfinite;
-    const double fb = fmin(a.alpha_max, fbq);
-    double alpha;
+    const DF fb = df_min(amax, fbq);
+    DF alpha;
     int branch;
-    if (a.force_fallback || a.t == 0 || ss == 0.0) {
+    if (a.force_fallback || a.t == 0 || (ss.hi == 0.0f && ss.lo == 0.0f)) {
         alpha = fb;
         branch = 0;
-    } else if (sy > a.eps_alpha) {
-        alpha = fmin(fmin(bb, 2.0 * lip), a.alpha_max);
+    } else if (df_lt(eps, sy)) {
+        alpha = df_min(df_min(bb, DF{2.0f * lip.hi, 2.0f * lip.lo}), amax);
         branch = 1;
     } else {
-        alpha = fmin(lip, a.alpha_max);
+        alpha = df_min(lip, amax);
         branch = 2;
     }
-    const double beta = a.t == 0 ? 0.0 : fmax(pr, 0.0);
-    const double c = a.omega * alpha;
-    float h, l;
-    bc->alpha = alpha;
-    bc->beta = beta;
-    bc->c = c;
-    split_double(c, h, l);
-    bc->c_hi = h;
-    bc->c_lo = l;
-    split_double(beta, h, l);
-    bc->beta_hi = h;
-    bc->beta_lo = l;
+    const DF beta = (a.t == 0 || !df_lt(df_zero(), pr)) ? df_zero() : pr;
+    const DF c = df_mul(om, alpha);
+    bc->c_hi = c.hi;
+    bc->c_lo = c.lo;
+    bc->beta_hi = beta.hi;
+    bc->beta_lo = beta.lo;
     bc->branch = branch;
     bc->status = status;
-    inf->alpha = alpha;
-    inf->beta = beta;
+    inf->alpha = df_to_double(alpha);
+    inf->beta = df_to_double(beta);
     inf->branch = branch;
     inf->t = a.t;
 }
