@@ -87,7 +87,10 @@ __device__ __forceinline__ void publish_lambda(volatile SegBcast* bc, int j, dou
 // An equality row (Sec. 3.2.4) with r(0) < 0 binds from below: its root is negative, in
 // [L, 0] with L the lowest breakpoint (every variable at its row-maximising bound below
 // it), or (C/2)(S_max - b) when even that point leaves r < 0.
-__device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, SegState* ws) {
+// ladder: the pass evaluated with phase B used the warm-start ladder; rows with a usable
+// previous root take their points from it, so the first points are computed only when
+// some row has none.
+__device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, SegState* ws, bool ladder = false) {
     const int lane = threadIdx.x, j = lane >> 3, k = lane & 7;
     volatile SegBcast* bc = &ws->bc;
     volatile RowState* rows = ws->rows;
@@ -129,18 +132,23 @@ __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, Seg
     }
     const bool closed = down ? rL < 0.0 : (up && rH > 0.0);
     const bool search = row && finite && (up || down) && !closed;
-    // the row's first Newton quotients and secant offset in one warp-wide division (FP64
-    // issues slowly here; divergent divisions would run one after another): lane k = 0 of
-    // the group divides for the Newton point from L, k = 1 from H, the others the secant
-    const double num = k == 0 ? rL : k == 1 ? rH : rL * (H - L);
-    const double den = k == 0 ? SLs : k == 1 ? SHs : rL - rH;
-    const double q = num / den;
-    const int g0 = lane & ~7;
-    const double NL = L + __shfl_sync(kFull, q, g0);
-    const double NH = H + __shfl_sync(kFull, q, g0 + 1);
-    const double sec = L + __shfl_sync(kFull, q, g0 + 2);
-    const double lp = a.lam_prev ? a.lam_prev[jj] : (down ? 1.0 : -1.0);
-    const float p = next_point_warm(lane, L, H, NL, NH, sec, lp);
+    const bool need = !ladder || __ballot_sync(kFull, row && !ladder_usable((float)a.lam_prev[jj])) != 0u;
+    float p = 0.0f;
+    if (need) {  // warp-uniform
+        // the row's first Newton quotients and secant offset in one warp-wide division
+        // (FP64 issues slowly here; divergent divisions would run one after another): lane
+        // k = 0 of the group divides for the Newton point from L, k = 1 from H, the others
+        // the secant
+        const double num = k == 0 ? rL : k == 1 ? rH : rL * (H - L);
+        const double den = k == 0 ? SLs : k == 1 ? SHs : rL - rH;
+        const double q = num / den;
+        const int g0 = lane & ~7;
+        const double NL = L + __shfl_sync(kFull, q, g0);
+        const double NH = H + __shfl_sync(kFull, q, g0 + 1);
+        const double sec = L + __shfl_sync(kFull, q, g0 + 2);
+        const double lp = a.lam_prev ? a.lam_prev[jj] : (down ? 1.0 : -1.0);
+        p = next_point_warm(lane, L, H, NL, NH, sec, lp);
+    }
     if (row && k == 0) {
         ws->info.b[j] = b;
         rows[j].reg = two_c;
@@ -159,7 +167,7 @@ __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, Seg
             publish_lambda(bc, j, 0.0);
         }
     }
-    if (search) bc->pts[j][k] = p;
+    if (search && need) bc->pts[j][k] = p;
     const unsigned any = __ballot_sync(kFull, search);
     const unsigned bad = __ballot_sync(kFull, row && !finite);
     if (lane == 0) {
@@ -856,7 +864,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 // phase B's update, then the ladder pass's: rows that search and had no
                 // usable previous root keep the first points update_after_trial gave them
                 if (!sy.reduce(sc, (5 + 2 * K) * nr, 2 * nr, [&](BlockScratch& s, SegState* st) {
-                        update_after_trial(a, s, st);
+                        update_after_trial(a, s, st, true);
                         __syncwarp();
                         volatile SegBcast* vb = &st->bc;
                         volatile RowState* vr = st->rows;
