@@ -395,9 +395,14 @@ static void fill_seg_args(pgdto_handle* h, bool proj, float* x, const float* g, 
     a.zlo = h->zlo;
     a.z_in = z_in;
     a.x_out = x_out;
-    for (int j = 0; j < h->m; ++j) a.bconst[j] = bconst[j];
+    for (int j = 0; j < h->m; ++j) {
+        a.bconst[j] = bconst[j];
+        split_to_floats(bconst[j], a.bconst_df + 2 * j);
+    }
     a.C = h->p.C;
     a.two_c = 2.0 / h->p.C;
+    split_to_floats(a.two_c, a.two_c_df);
+    split_to_floats(0.5 * h->p.C, a.half_c_df);
     fill_step_df(h->p, a.step_df);
     a.alpha_max = h->p.alpha_max;
     a.alpha_fb = h->p.alpha_fallback;

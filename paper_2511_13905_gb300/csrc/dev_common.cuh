@@ -91,7 +91,8 @@ __device__ __forceinline__ DF df_sqrt(DF a) {
     const float s = __fsqrt_rn(a.hi);
     const float p = s * s;
     const DF r = df_add(a, DF{-p, -fmaf(s, s, -p)});
-    return fast_two_sum(s, __fdiv_rn(r.hi, 2.0f * s));
+    const DF v = fast_two_sum(s, __fdiv_rn(r.hi, 2.0f * s));
+    return (a.hi > 0.0f && a.hi < INFINITY) ? v : DF{s, 0.0f};  // 0, inf and NaN as sqrtf gives them
 }
 
 __device__ __forceinline__ bool df_lt(DF a, DF b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }

@@ -44,6 +44,8 @@ struct SegArgs {
     double C, alpha_max, alpha_fb, eps_alpha, omega, tol_lambda;
     double two_c;         // 2 / C, the slope of the regulariser term (computed by the host)
     float step_df[8];     // alpha_max, alpha_fb, eps_alpha, omega as (hi, lo) float pairs
+    float bconst_df[2 * kMaxRows];  // bconst as (hi, lo) float pairs
+    float two_c_df[2], half_c_df[2];  // 2 / C and C / 2 as (hi, lo) float pairs
     int max_passes;
     int fault_inject;
     long long timeout_cycles;
@@ -159,6 +161,12 @@ struct CoupledArgs {
     int eq_mask;          // bit j: row j is an equality (always active, lam_j of either sign)
     const double* lam_prev;  // warm start: the previous step's lam (device), or null
 };
+
+// A double as an unevaluated sum hi + lo of two floats (host side).
+inline void split_to_floats(double v, float* out) {
+    out[0] = (float)v;
+    out[1] = (float)(v - (double)out[0]);
+}
 
 // Workspace management (sizes in bytes, device-resident, zero-initialised by the host).
 size_t seg_work_bytes();

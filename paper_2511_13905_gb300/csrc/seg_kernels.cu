@@ -74,14 +74,6 @@ __device__ __forceinline__ bool all_finite(const BlockScratch& sc, int nv) {
 // points = 32 lanes), per-row quantities are computed redundantly by the 8 lanes of the
 // row's group, and each update issues one warp-wide FP64 division.
 
-__device__ __forceinline__ void publish_lambda(volatile SegBcast* bc, int j, double lam) {
-    float h, l;
-    split_double(lam, h, l);
-    bc->lam_hi[j] = h;
-    bc->lam_lo[j] = l;
-    bc->active[j] = 0;
-}
-
 // After phase B: feasibility at lam = 0, bracket [0, H] (Alg. 1), closed form when the row
 // is violated even with every variable at its row-minimising bound (regularised root).
 // An equality row (Sec. 3.2.4) with r(0) < 0 binds from below: its root is negative, in
@@ -91,80 +83,83 @@ __device__ __forceinline__ void publish_lambda(volatile SegBcast* bc, int j, dou
 // previous root take their points from it, so the first points are computed only when
 // some row has none.
 __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, SegState* ws, bool ladder = false) {
+    // double-float throughout (FP32 pipes; FP64 issues slowly here), FP64 only for the
+    // values kept for the report and the final refinement
     const int lane = threadIdx.x, j = lane >> 3, k = lane & 7;
     volatile SegBcast* bc = &ws->bc;
     volatile RowState* rows = ws->rows;
     const bool row = j < a.nrows;
     const int jj = row ? j : 0;
-    const double two_c = a.two_c;
-    const double ax = a.proj ? 0.0 : df_to_double(sc.tot[5 * jj + 0]);
-    const double r0s = df_to_double(sc.tot[5 * jj + 1]);
-    const double sf = df_to_double(sc.tot[5 * jj + 2]);
-    const double smin = df_to_double(sc.tot[5 * jj + 3]);
-    const double smax = df_to_double(sc.tot[5 * jj + 4]);
-    const double lsat = (double)sc.totmax[2 * jj];
-    const double lneg = -(double)sc.totmax[2 * jj + 1];
+    const DF two_c = DF{a.two_c_df[0], a.two_c_df[1]};
+    const DF ax = a.proj ? df_zero() : sc.tot[5 * jj + 0];
+    const DF r0s = sc.tot[5 * jj + 1], sf = sc.tot[5 * jj + 2];
+    const DF smin = sc.tot[5 * jj + 3], smax = sc.tot[5 * jj + 4];
+    const float lsat = sc.totmax[2 * jj];
+    const float lneg = -sc.totmax[2 * jj + 1];
     const bool eq = (a.eq_mask >> jj) & 1;
-    const bool finite = isfinite(ax) && isfinite(r0s) && isfinite(sf) && isfinite(smin) && isfinite(smax);
-    const double b = a.bconst[jj] + ax;
-    const double r0 = r0s - b;
-    const bool up = r0 > 0.0;
-    const bool down = eq && r0 < 0.0;
-    double L, rL, SLs, H, rH, SHs;
+    const bool finite = isfinite(ax.hi) && isfinite(r0s.hi) && isfinite(sf.hi) && isfinite(smin.hi) &&
+                        isfinite(smax.hi);
+    const DF b = df_add(DF{a.bconst_df[2 * jj], a.bconst_df[2 * jj + 1]}, ax);
+    const DF r0 = df_add(r0s, df_neg(b));
+    const bool up = df_pos(r0);
+    const bool down = eq && df_pos(df_neg(r0));
+    float L, H;
+    DF rL, SLs, rH, SHs;
     if (down) {
-        float Lf = (float)(lneg * (1.0 + 1e-5) - 1e-30);
-        if (!((double)Lf < 0.0)) Lf = -FLT_MIN;
-        L = (double)Lf;
-        rL = smax - b - two_c * L;
+        // the saturation bounds are only used widened (by 1e-5 and a tiny absolute margin)
+        float Lf = fmaf(lneg, 1.00001f, -1e-30f);
+        if (!(Lf < 0.0f)) Lf = -FLT_MIN;
+        L = Lf;
+        rL = df_add(df_add(smax, df_neg(b)), df_neg(df_mul(two_c, DF{L, 0.0f})));
         SLs = two_c;
-        H = 0.0;
+        H = 0.0f;
         rH = r0;
-        SHs = sf + two_c;
+        SHs = df_add(sf, two_c);
     } else {
-        float Hf = (float)(lsat * (1.0 + 1e-5) + 1e-30);
-        if (!((double)Hf > 0.0)) Hf = FLT_MIN;
-        L = 0.0;
+        float Hf = fmaf(lsat, 1.00001f, 1e-30f);
+        if (!(Hf > 0.0f)) Hf = FLT_MIN;
+        L = 0.0f;
         rL = r0;
-        SLs = sf + two_c;
-        H = (double)Hf;
-        rH = smin - b - two_c * H;
+        SLs = df_add(sf, two_c);
+        H = Hf;
+        rH = df_add(df_add(smin, df_neg(b)), df_neg(df_mul(two_c, DF{H, 0.0f})));
         SHs = two_c;
     }
-    const bool closed = down ? rL < 0.0 : (up && rH > 0.0);
+    const bool closed = down ? df_pos(df_neg(rL)) : (up && df_pos(rH));
     const bool search = row && finite && (up || down) && !closed;
     const bool need = !ladder || __ballot_sync(kFull, row && !ladder_usable((float)a.lam_prev[jj])) != 0u;
     float p = 0.0f;
     if (need) {  // warp-uniform
-        // the row's first Newton quotients and secant offset in one warp-wide division
-        // (FP64 issues slowly here; divergent divisions would run one after another): lane
+        // the row's first Newton quotients and secant offset in one warp-wide division: lane
         // k = 0 of the group divides for the Newton point from L, k = 1 from H, the others
         // the secant
-        const double num = k == 0 ? rL : k == 1 ? rH : rL * (H - L);
-        const double den = k == 0 ? SLs : k == 1 ? SHs : rL - rH;
-        const double q = num / den;
+        const DF num = k == 0 ? rL : k == 1 ? rH : df_mul(rL, DF{H - L, 0.0f});
+        const DF den = k == 0 ? SLs : k == 1 ? SHs : df_add(rL, df_neg(rH));
+        const DF q = df_div(num, den);
         const int g0 = lane & ~7;
-        const double NL = L + __shfl_sync(kFull, q, g0);
-        const double NH = H + __shfl_sync(kFull, q, g0 + 1);
-        const double sec = L + __shfl_sync(kFull, q, g0 + 2);
-        const double lp = a.lam_prev ? a.lam_prev[jj] : (down ? 1.0 : -1.0);
-        p = next_point_warm(lane, L, H, NL, NH, sec, lp);
+        const float NL = (df_add_f(DF{__shfl_sync(kFull, q.hi, g0), __shfl_sync(kFull, q.lo, g0)}, L)).hi;
+        const float NH = (df_add_f(DF{__shfl_sync(kFull, q.hi, g0 + 1), __shfl_sync(kFull, q.lo, g0 + 1)}, H)).hi;
+        const float sec = (df_add_f(DF{__shfl_sync(kFull, q.hi, g0 + 2), __shfl_sync(kFull, q.lo, g0 + 2)}, L)).hi;
+        const float lp = a.lam_prev ? (float)a.lam_prev[jj] : (down ? 1.0f : -1.0f);
+        p = next_point_warm_f(lane, L, H, NL, NH, sec, lp);
     }
     if (row && k == 0) {
-        ws->info.b[j] = b;
-        rows[j].reg = two_c;
+        ws->info.b[j] = df_to_double(b);
+        rows[j].reg = a.two_c;
         if (search) {
-            store_row(&rows[j], b, L, rL, SLs, H, rH, SHs, 0.0, 0.0, 1, 0, 2);
+            store_row_df(&rows[j], b, L, rL, SLs, H, rH, SHs, df_zero(), 0.0, two_c.hi, 1, 2);
             bc->active[j] = 1;
             bc->cmode[j] = 0;
-            bc->brL[j] = rows[j].fL;
-            bc->brH[j] = rows[j].fH;
+            bc->brL[j] = L;
+            bc->brH[j] = H;
         } else if (closed) {
-            const double lam = 0.5 * a.C * ((down ? smax : smin) - b);
-            store_row(&rows[j], b, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, lam, 0.0, 0, 0, 1);
-            publish_lambda(bc, j, lam);
+            const DF lam = df_mul(DF{a.half_c_df[0], a.half_c_df[1]}, df_add(down ? smax : smin, df_neg(b)));
+            store_row_df(&rows[j], b, 0.0f, df_zero(), df_zero(), 0.0f, df_zero(), df_zero(), lam, 0.0, two_c.hi, 0, 1);
+            publish_lambda_df(bc, j, lam);
         } else {
-            store_row(&rows[j], b, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, r0, 0, 0, 0);
-            publish_lambda(bc, j, 0.0);
+            store_row_df(&rows[j], b, 0.0f, df_zero(), df_zero(), 0.0f, df_zero(), df_zero(), df_zero(),
+                         df_to_double(r0), two_c.hi, 0, 0);
+            publish_lambda_df(bc, j, df_zero());
         }
     }
     if (search && need) bc->pts[j][k] = p;
@@ -179,7 +174,8 @@ __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, Seg
 }
 
 // After phase D: the report.  Lane j < nrows refines row j; lane kMaxRows computes the
-// relative change; both divisions are one warp-wide division (FP64 issues slowly here).
+// relative change; both divisions are one warp-wide double-float division (FP32 pipes;
+// FP64 issues slowly here).
 __device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegState* ws, int* sticky,
                              unsigned long long* launches) {
     const int lane = threadIdx.x;
@@ -189,17 +185,19 @@ __device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegState*
     volatile SegBcast* bc = &ws->bc;
     const bool rl = lane < nr;
     const int j = rl ? lane : 0;
-    const double ax = df_to_double(sc.tot[j]);
-    const double reg = rows[j].reg, bj = rows[j].b;
-    double lam = rows[j].lam;
-    const double S = df_to_double(sc.tot[nr + j]) + reg;
-    const double r = ax - bj - reg * lam;
-    const double dd = a.proj ? 0.0 : df_to_double(sc.tot[2 * nr]);
-    const double nn = a.proj ? 1.0 : df_to_double(sc.tot[2 * nr + 1]);
+    const DF two_c = DF{a.two_c_df[0], a.two_c_df[1]};
+    const DF ax = sc.tot[j];
+    const DF bj = DF{rows[j].b_hi, rows[j].b_lo};
+    DF lam = DF{rows[j].lam_hi, rows[j].lam_lo};
+    const DF S = df_add(sc.tot[nr + j], two_c);
+    const DF r = df_add(df_add(ax, df_neg(bj)), df_neg(df_mul(two_c, lam)));
+    const DF dd = a.proj ? df_zero() : sc.tot[2 * nr];
+    const DF nn = a.proj ? DF{1.0f, 0.0f} : sc.tot[2 * nr + 1];
     const bool rcl = lane == kMaxRows;
-    const double q = (rcl ? dd : r) / (rcl ? nn : S);
-    const double rq = sqrt(q);
-    const double rc = __shfl_sync(kFull, a.proj ? 0.0 : (nn > 0.0 ? rq : INFINITY), kMaxRows);
+    const DF q = df_div(rcl ? dd : r, rcl ? nn : S);
+    const DF rq = df_sqrt(q);
+    const double rcl_v = a.proj ? 0.0 : (nn.hi > 0.0f ? df_to_double(rq) : INFINITY);
+    const double rc = __shfl_sync(kFull, rcl_v, kMaxRows);
     // One Newton step per searched row on the accurate residual of this pass.  The
     // search's FP32 trial sums carry rounding noise (well under 1e-6 (|b| + |a^T x|)),
     // which can leave its root outside its last bracket by up to that noise over the
@@ -208,16 +206,20 @@ __device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegState*
     // piece) runs this pass again at the corrected lam, at most eight times.
     const bool eqj = (a.eq_mask >> j) & 1;
     bool again = false;
-    if (rl && rows[j].how == 2 && (lam > 0.0 || eqj)) {
-        const double dl = S > 0.0 ? q : 0.0;
-        const double w = (double)rows[j].fH - (double)rows[j].fL;
-        const bool near = fabs(dl) <= 4.0 * w || (S > 0.0 && fabs(dl) * S <= 1e-6 * (fabs(bj) + fabs(ax)));
-        if (near && (lam + dl > 0.0 || eqj)) {
-            lam += dl;
-            if (fabs(dl) > 1e-7 * fabs(lam) && rows[j].nrefine < 8) {
+    if (rl && rows[j].how == 2 && (df_pos(lam) || eqj)) {
+        const bool spos = df_pos(S);
+        const DF dl = spos ? q : df_zero();
+        const float w = rows[j].fH - rows[j].fL;
+        const float adl = fabsf(dl.hi);
+        const bool near = adl <= 4.0f * w || (spos && adl * S.hi <= 1e-6f * (fabsf(bj.hi) + fabsf(ax.hi)));
+        const DF ln = df_add(lam, dl);
+        if (near && (df_pos(ln) || eqj)) {
+            lam = ln;
+            if (adl > 1e-7f * fabsf(lam.hi) && rows[j].nrefine < 8) {
                 rows[j].nrefine = rows[j].nrefine + 1;
-                rows[j].lam = lam;
-                publish_lambda(bc, j, lam);
+                rows[j].lam_hi = lam.hi;
+                rows[j].lam_lo = lam.lo;
+                publish_lambda_df(bc, j, lam);
                 again = true;
             }
         }
@@ -226,12 +228,12 @@ __device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegState*
     if (lane == 0) bc->refine = again_m ? 1 : 0;
     if (again_m) return;
     if (lane < kMaxRows) {
-        inf->lambda[lane] = rl ? lam : 0.0;
-        inf->viol[lane] = rl ? ax - bj : 0.0;
-        inf->b[lane] = rl ? bj : 0.0;
+        inf->lambda[lane] = rl ? df_to_double(lam) : 0.0;
+        inf->viol[lane] = rl ? df_to_double(df_add(ax, df_neg(bj))) : 0.0;
+        inf->b[lane] = rl ? rows[j].b : 0.0;
     }
     const unsigned nconv = __ballot_sync(kFull, rl && rows[j].how == 3);
-    const unsigned nfin = __ballot_sync(kFull, rl && !isfinite(ax));
+    const unsigned nfin = __ballot_sync(kFull, rl && !isfinite(ax.hi));
     if (lane != 0) return;
     int status = bc->status;
     int passes = 0;
@@ -1279,6 +1281,7 @@ extern "C" pgdto_status pgdto_project_noalloc(int64_t n, int m, const int64_t* s
     for (int j = 0; j < m; ++j) {
         if (!isfinite(b[j])) return PGDTO_ERR_NONFINITE;
         a.bconst[j] = b[j];
+        split_to_floats(b[j], a.bconst_df + 2 * j);
     }
     int device = 0;
     if (cudaGetDevice(&device) != cudaSuccess) return PGDTO_ERR_CUDA;
@@ -1301,6 +1304,8 @@ extern "C" pgdto_status pgdto_project_noalloc(int64_t n, int m, const int64_t* s
     a.x_out = x_out;
     a.C = C;
     a.two_c = 2.0 / C;
+    split_to_floats(a.two_c, a.two_c_df);
+    split_to_floats(0.5 * C, a.half_c_df);
     a.tol_lambda = p.tol_lambda;
     a.max_passes = p.max_passes;
     a.timeout_cycles = (long long)clock_khz * (long long)p.barrier_timeout_ms;

@@ -25,7 +25,8 @@ struct RowState {
     int active, passes, how, nrefine;  // nrefine: extra final passes at a refined root
     // the same bracket in float / double-float form: the per-pass update works on these
     // (FP64 issues at a small fraction of the FP32 rate here and sits on the critical path)
-    float b_hi, b_lo, fL, fH, rL_hi, rL_lo, rH_hi, rH_lo, fSL, fSH, freg, fpad;
+    float b_hi, b_lo, fL, fH, rL_hi, rL_lo, rH_hi, rH_lo, fSL, fSH, freg;
+    float lam_hi, lam_lo;  // lam as a float pair
 };
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
@@ -206,6 +207,32 @@ __device__ __forceinline__ float next_point_warm(int lane, double L, double H, d
     return group8_sort(fv, lane);
 }
 
+// next_point_warm in FP32 (the points are FP32 anyway), from the float bracket [L, H] and
+// the Newton points NL, NH and secant point sec already formed.
+__device__ __forceinline__ float next_point_warm_f(int lane, float L, float H, float NL, float NH, float sec,
+                                                   float lp) {
+    const int k = lane & 7;
+    const bool warm = lp > L && lp < H;
+    const float w = H - L;
+    const float am = fabsf(L), bm = fabsf(H);
+    float v;
+    if (k == 0) v = NL;
+    else if (k == 1) v = NH;
+    else if (k == 2) v = sec;
+    else if (!warm && (L * H <= 0.0f || fmaxf(am, bm) > 4.0f * fminf(am, bm))) {
+        const float base = (L == 0.0f && NL > L && NL < H) ? NL : (H == 0.0f && NH > L && NH < H) ? NH : sec;
+        v = base * (k == 3 ? 0.125f : k == 4 ? 0.25f : k == 5 ? 0.5f : k == 6 ? 2.0f : 4.0f);
+    } else if (!warm) v = fmaf(w, (float)(k - 2) * (1.0f / 6.0f), L);
+    else if (k == 3) v = fmaf(0.5f, w, L);
+    else v = lp * (k == 4 ? 0.97f : k == 5 ? 0.997f : k == 6 ? 1.003f : 1.03f);
+    if (!(v > L && v < H)) v = fmaf(w, ((float)k + 0.5f) * 0.125f, L);
+    if (!(v > L && v < H)) {
+        v = L + 0.5f * w;
+        if (!(v > L && v < H)) v = H;
+    }
+    return group8_sort(v, lane);
+}
+
 __device__ __forceinline__ void store_row(volatile RowState* r, double b, double L, double rL, double SL, double H,
                                           double rH, double SH, double lam, double rlast, int active, int passes,
                                           int how) {
@@ -217,6 +244,12 @@ __device__ __forceinline__ void store_row(volatile RowState* r, double b, double
     r->rH = rH;
     r->SH = SH;
     r->lam = lam;
+    {
+        float lh, ll;
+        split_double(lam, lh, ll);
+        r->lam_hi = lh;
+        r->lam_lo = ll;
+    }
     r->rlast = rlast;
     r->active = active;
     r->passes = passes;
@@ -271,6 +304,50 @@ __device__ __forceinline__ void publish_lambda(volatile Bcast* bc, int j, double
 }
 
 __device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+
+template <class Bcast>
+__device__ __forceinline__ void publish_lambda_df(volatile Bcast* bc, int j, DF lam) {
+    bc->lam_hi[j] = lam.hi;
+    bc->lam_lo[j] = lam.lo;
+    bc->active[j] = 0;
+}
+
+// store_row for a search formed in double-float (single and independent rows): the
+// bracket is kept in its float / double-float form only (what the passes' update reads);
+// b, lam and rlast also in FP64 for the final refinement and the report.
+__device__ __forceinline__ void store_row_df(volatile RowState* r, DF b, float L, DF rL, DF SL, float H, DF rH,
+                                             DF SH, DF lam, double rlast, float freg, int active, int how) {
+    r->b = df_to_double(b);
+    r->L = 0.0;
+    r->rL = 0.0;
+    r->SL = 0.0;
+    r->H = 0.0;
+    r->rH = 0.0;
+    r->SH = 0.0;
+    r->lam = df_to_double(lam);
+    r->lam_hi = lam.hi;
+    r->lam_lo = lam.lo;
+    r->rlast = rlast;
+    r->active = active;
+    r->passes = 0;
+    r->how = how;
+    r->nrefine = 0;
+    r->cC = 0.0;
+    r->cAA = 0.0;
+    r->visited = 0.0;
+    r->b_hi = b.hi;
+    r->b_lo = b.lo;
+    r->rL_hi = rL.hi;
+    r->rL_lo = rL.lo;
+    r->rH_hi = rH.hi;
+    r->rH_lo = rH.lo;
+    r->fL = L;
+    r->fH = H;
+    r->fSL = SL.hi;
+    r->fSH = SH.hi;
+    r->freg = freg;
+}
+
 
 // a / b for a double-float a and a float b, to double-float accuracy.
 __device__ __forceinline__ DF df_div_f(DF a, float b) {
@@ -412,16 +489,23 @@ __device__ void search_pass_update(const BlockScratch& sc, int base, volatile Ro
             r->visited = r->visited + df_to_double(sc.tot[o + 3]);
         }
         if (done) {
-            // the root, once, in FP64: the midpoint of the two Newton predictions, in [L, H]
-            double root = (kH >= 0 && rH.hi == 0.0f && rH.lo == 0.0f)
-                              ? (double)H
-                              : 0.5 * (((double)NL.hi + (double)NL.lo) + ((double)NH.hi + (double)NH.lo));
-            root = fmin(fmax(root, (double)L), (double)H);
-            r->lam = root;
-            r->rlast = fmax(fabs((double)rL.hi), fabs((double)rH.hi));
+            // the root: the midpoint of the two Newton predictions (double-float), in [L, H]
+            DF root;
+            if (kH >= 0 && rH.hi == 0.0f && rH.lo == 0.0f) {
+                root = DF{H, 0.0f};
+            } else {
+                const DF s2 = df_add(NL, NH);
+                root = DF{0.5f * s2.hi, 0.5f * s2.lo};
+            }
+            if (df_lt(root, DF{L, 0.0f})) root = DF{L, 0.0f};
+            if (df_lt(DF{H, 0.0f}, root)) root = DF{H, 0.0f};
+            r->lam = df_to_double(root);
+            r->lam_hi = root.hi;
+            r->lam_lo = root.lo;
+            r->rlast = (double)fmaxf(fabsf(rL.hi), fabsf(rH.hi));
             r->active = 0;
             r->how = how;
-            publish_lambda(bc, j, root);
+            publish_lambda_df(bc, j, root);
         }
     }
     if (row && !done) bc->pts[j][k] = p;
