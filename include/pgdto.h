@@ -305,9 +305,10 @@ int64_t pgdto_kernel_launches(const pgdto_handle* h);
  *   z, A, x_out: device, as for pgdto_project (x_out may alias z); b: host, m doubles.
  *   lambda_out / info: host or NULL; when either is non-NULL the call waits for the stream
  *     and reads the result back, otherwise it returns as soon as the work is enqueued.
- * Workspace: a file-scope device array of about 1.2 MB (the reduction partials for up to
- * 1024 blocks and 4 rows plus the control block) that every GPU loading the library holds
- * until the process exits.  Sizes beyond what it holds, m > 4, return PGDTO_ERR_ARG; n has
+ * Workspace: a file-scope device array of about 2.3 MB (the reduction partials of two
+ * alternating rounds for up to 1024 blocks and 4 rows, plus the control block and the
+ * report) that every GPU loading the library holds until the process exits.  Sizes
+ * beyond what it holds, m > 4, return PGDTO_ERR_ARG; n has
  * no limit of its own.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call before any stream
  * capture.  Every call shares the one array: calls whose device work overlaps (two streams,

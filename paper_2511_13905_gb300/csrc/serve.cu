@@ -88,7 +88,7 @@ int64_t clock_us(const pgdto_server* srv) {
 
 uint64_t session_bytes(int64_t n, int64_t a_len) {
     // handle: x_prev, g_prev, d[2], z, z_lo (6 n floats) + workspace; session: x, g, A
-    return (uint64_t)(6 * n + 2 * n + a_len) * sizeof(float) + (uint64_t)(2u << 20);
+    return (uint64_t)(6 * n + 2 * n + a_len) * sizeof(float) + (uint64_t)(3u << 20);
 }
 
 void free_session(Session* s) {
