@@ -68,6 +68,10 @@ __device__ __forceinline__ DF df_add_f(DF a, float b) {
 
 __device__ __forceinline__ double df_to_double(DF a) { return (double)a.hi + (double)a.lo; }
 
+// Double-float multiply, divide and square root after Dekker's double-length arithmetic
+// (T. J. Dekker, "A floating-point technique for extending the available precision",
+// 1971), with the exact products taken by FMA.
+//
 // a * b to double-float accuracy (the product of the hi parts exact via FMA).
 __device__ __forceinline__ DF df_mul(DF a, DF b) {
     const float p = a.hi * b.hi;
@@ -157,7 +161,7 @@ struct GridCtrl {
     unsigned gen;      // round counter, bumped by the last block to arrive (own 128-byte line: the
     int pad2[31];      // waiting blocks poll it while the others still arrive on `count`)
     unsigned long long trace_start;  // globaltimer at kernel entry (block 0)
-    unsigned long long trace[62];    // globaltimer after each grid reduction's update
+    unsigned long long trace[62];    // globaltimer after each grid round's update (block 0)
     int ntrace;
     int pad3[3];
 };
