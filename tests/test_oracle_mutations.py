@@ -48,7 +48,7 @@ def _pins(mod):
     try:
         for c in _golden("step_scalars.json")["cases"]:
             sc = S.step_scalars(c["x"], c["x_prev"], c["g"], c["g_prev"], c["t"], c["gval"], c["G"],
-                                S.StepParams())
+                                S.StepParams(), eq=c.get("eq"))
             ok = (sc["branch"] == c["branch"] and np.isclose(sc["alpha"], c["alpha"], rtol=1e-12)
                   and np.isclose(sc["beta"], c["beta"], rtol=1e-12, atol=1e-15))
             if not ok:
@@ -84,6 +84,15 @@ def _pins(mod):
             failed.append("golden_full_step")
     except Exception as e:
         failed.append("golden_full_step:exception:%s" % e)
+    try:
+        c = _golden("full_step_t1.json")
+        out = S.oracle_step(c["x"], c["x_prev"], c["g"], c["g_prev"], c["d_prev"], c["A"], c["gval"], c["G"],
+                            c["t"], S.StepParams(omega=c["omega"]), mode="single")
+        if not (np.allclose(out["d"], c["d"], atol=1e-15) and np.allclose(out["z"], c["z"], atol=1e-15)
+                and np.allclose(out["x_new"], c["x_new"], atol=1e-14)):
+            failed.append("golden_full_step_t1")
+    except Exception as e:
+        failed.append("golden_full_step_t1:exception:%s" % e)
     try:
         for seed, Cc in [(301, 3.0), (302, 3.0), (103, C), (107, C)]:
             z, A, b = inputs.random_projection(5, 2, seed, feasible=(Cc != 3.0))
@@ -148,6 +157,9 @@ MUTANTS = [
     ("step.py", "sty > p.eps_alpha", "sty > 0.0"),                                 # eps_alpha threshold ignored
     ("step.py", "b = G - gval + A2 @ x", "b = G - gval"),                          # linearisation point dropped
     ("step.py", "z = x + p.omega * alpha * d", "z = x - p.omega * alpha * d"),     # wrong sign of the step
+    ("step.py", "-g + beta * np.asarray(d_prev", "-g - beta * np.asarray(d_prev"),  # sign of the CG term
+    ("step.py", "z = x + p.omega * alpha * d", "z = x + alpha * d"),              # relaxation omega dropped
+    ("step.py", "np.where(E, np.abs(dg), np.maximum(dg, 0.0))", "np.maximum(dg, 0.0)"),  # equality trigger one-sided
     ("projection.py", "np.clip(z - lam * a, lo, hi) - b", "np.clip(z + lam * a, lo, hi) - b"),  # sign in r(lam)
     ("projection.py", "_piecewise_root(z, a, b, lo, hi, 2.0 / C)", "_piecewise_root(z, a, b, lo, hi, 1.0 / C)"),  # 2/C -> 1/C
     ("projection.py", "/ (float(u[free] @ u[free]) + reg)", "/ (float(u[free] @ u[free]) + 0.5 * reg)"),  # regulariser in the piece root

@@ -34,7 +34,7 @@ def _load(name):
 @pytest.mark.parametrize("case", _load("step_scalars.json")["cases"], ids=lambda c: c["name"])
 def test_step_scalars_golden(case):
     sc = step_scalars(case["x"], case["x_prev"], case["g"], case["g_prev"], case["t"],
-                      case["gval"], case["G"], StepParams())
+                      case["gval"], case["G"], StepParams(), eq=case.get("eq"))
     assert sc["branch"] == case["branch"]
     assert sc["alpha"] == pytest.approx(case["alpha"], rel=1e-12)
     assert sc["beta"] == pytest.approx(case["beta"], rel=1e-12, abs=1e-15)
@@ -72,6 +72,23 @@ def test_full_step_golden():
     assert np.allclose(out["lam"], c["lam"], rtol=1e-10)
     assert np.allclose(out["x_new"], c["x_new"], atol=1e-12)
     assert out["rel_change"] == pytest.approx(c["rel_change"], rel=1e-10)
+
+
+def test_full_step_t1_golden():
+    """t = 1: the PR+ direction d = -g + beta d_prev (eq. CG) with beta > 0 and the
+    relaxed trial point z = x + omega alpha d (Sec. 3.4) with omega = 0.5."""
+    c = _load("full_step_t1.json")
+    out = oracle_step(c["x"], c["x_prev"], c["g"], c["g_prev"], c["d_prev"], c["A"], c["gval"], c["G"],
+                      c["t"], StepParams(omega=c["omega"]), mode="single", lo=c["lo"], hi=c["hi"])
+    assert out["branch"] == c["branch"]
+    assert out["alpha"] == pytest.approx(c["alpha"], rel=1e-14)
+    assert out["beta"] == pytest.approx(c["beta"], rel=1e-14)
+    assert np.allclose(out["d"], c["d"], rtol=0, atol=1e-15)
+    assert np.allclose(out["z"], c["z"], rtol=0, atol=1e-15)
+    assert np.allclose(out["b"], c["b"], atol=1e-15)
+    assert np.allclose(out["lam"], c["lam"], rtol=1e-12)
+    assert np.allclose(out["x_new"], c["x_new"], atol=1e-14)
+    assert out["rel_change"] == pytest.approx(c["rel_change"], rel=1e-12)
 
 
 # ----------------------------------------------------------------- brute force
