@@ -294,30 +294,40 @@ int64_t pgdto_kernel_launches(const pgdto_handle* h);
 
 /*
  * pgdto_project_noalloc -- the projection of pgdto_project for callers that cannot
- * allocate device memory.  The paper has no counterpart; this is a deployment variant.  Callers that cannot call
- * cudaMalloc include code running while a CUDA graph it does not own is being captured,
- * processes whose device memory belongs to another allocator or is fixed at start-up, and
- * loops that must never block in the driver's allocator.  No handle is involved (creating
- * one allocates); the call allocates nothing and frees nothing.
+ * allocate device memory.  The paper has no counterpart; this is a deployment variant.
+ * Callers that cannot call cudaMalloc include processes whose device memory belongs to
+ * another allocator (a framework's caching allocator that has reserved the GPU's memory,
+ * or a pool fixed at start-up, where a cudaMalloc would fail or fragment it) and loops
+ * with a latency budget that must never block in the driver's allocator.  No handle is
+ * involved (creating one allocates); the call allocates nothing and frees nothing.
  *   n, m, seg_offsets, lo, hi as for pgdto_create (m > 1 needs the segmented layout:
  *     rows with disjoint supports; coupled rows are not served here); C > 0 the
  *     regularisation of eq. h (1e12 in the paper).  Other parameters are the defaults.
  *   z, A, x_out: device, as for pgdto_project (x_out may alias z); b: host, m doubles.
  *   lambda_out / info: host or NULL; when either is non-NULL the call waits for the stream
- *     and reads the result back, otherwise it returns as soon as the work is enqueued.
+ *     (cudaStreamSynchronize) and reads the result back, otherwise it returns as soon as
+ *     the work is enqueued and the result's status is not observed.
  * Workspace: a file-scope device array of about 2.3 MB (the reduction partials of two
  * alternating rounds for up to 1024 blocks and 4 rows, plus the control block and the
  * report) that every GPU loading the library holds until the process exits.  Sizes
- * beyond what it holds, m > 4, return PGDTO_ERR_ARG; n has
- * no limit of its own.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call before any stream
- * capture.  Every call shares the one array: calls whose device work overlaps (two streams,
- * two host threads) race and give wrong results, so serialise them.  Each call clears the
- * barrier counters and status it needs before its kernel runs.
+ * beyond what it holds, m > 4, return PGDTO_ERR_ARG; n has no limit of its own.  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture.  Every call
+ * shares the one array: calls whose device work overlaps (two streams, two host threads)
+ * race and give wrong results, so serialise them.  Before its kernel runs, each call
+ * clears the barrier counters, the sticky status and the abort flag, and marks the report
+ * unpublished, so a device wait that ran out returns PGDTO_ERR_TIMEOUT (lambda_out then
+ * NaN), never the previous call's result.
  */
 pgdto_status pgdto_project_noalloc(int64_t n, int m, const int64_t* seg_offsets, float lo, float hi, double C,
                                    const float* z, const float* A, const double* b, float* x_out,
                                    double* lambda_out, pgdto_info* info, void* cuda_stream);
+
+/* Tests only: make the following pgdto_project_noalloc calls leave block 0 before the first
+ * grid reduction (fault_inject = 1) with a device-wait budget of timeout_ms (0 = the
+ * default), so that the other blocks' waits run out and the call reports
+ * PGDTO_ERR_TIMEOUT; nothing faults, traps or hangs.  (0, 0) restores normal calls. */
+pgdto_status pgdto_noalloc_set_test_fault(int fault_inject, int timeout_ms);
 
 /* Library version string, e.g. "pgdto-gb300 0.1 sm_103a". */
 const char* pgdto_version(void);

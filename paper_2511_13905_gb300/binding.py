@@ -104,6 +104,7 @@ def load(path=None):
         "pgdto_project_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                                  ctypes.c_float, ctypes.c_float, ctypes.c_double, P, P, D, P, D,
                                                  ctypes.POINTER(Info), P]),
+        "pgdto_noalloc_set_test_fault": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
         "pgdto_version": (ctypes.c_char_p, []),
         "pgdto_server_create": (ctypes.c_int, [ctypes.POINTER(H), ctypes.c_uint64, ctypes.c_int,
                                                ctypes.POINTER(Params), P]),
@@ -257,6 +258,11 @@ def project_noalloc(z, A, b, x_out, m=1, seg=None, lo=0.0, hi=1.0, C=1e12, strea
                                    _darr(b, m), _dptr(x_out), lam, ctypes.byref(info) if info is not None else None,
                                    _stream_ptr(stream))
     return st, (list(lam) if lam is not None else None), info
+
+
+def noalloc_set_test_fault(fault_inject, timeout_ms):
+    """pgdto_noalloc_set_test_fault (tests only)."""
+    return load().pgdto_noalloc_set_test_fault(int(fault_inject), int(timeout_ms))
 
 
 def _ptrs(ts):

@@ -1222,10 +1222,10 @@ int max_blocks_seg(int device) {
 
 // ------------------------------------------------------------------ allocation-free projection
 //
-// pgdto_project_noalloc serves callers that cannot allocate device memory: code that runs
-// while a CUDA graph it does not own is being captured (cudaMalloc is not allowed there),
-// processes whose device memory is handed out by another allocator or fixed at start-up,
-// and loops that must never wait on the driver's allocator.  It runs the projection kernel
+// pgdto_project_noalloc serves callers that cannot allocate device memory: processes whose
+// device memory is handed out by another allocator or fixed at start-up (a cudaMalloc there
+// fails or fragments the pool), and loops that must never wait on the driver's allocator.
+// It runs the projection kernel
 // above with its workspace in the file-scope array below instead of a handle's allocation.
 // Every GPU that loads this library holds the array until the process exits.
 
@@ -1240,6 +1240,10 @@ namespace {
 constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 void* g_noalloc_addr[kNoallocMaxDevices];
+// tests only (pgdto_noalloc_set_test_fault): block 0 leaves before the first grid reduction
+// and every wait has this budget, so the other blocks' waits run out
+int g_noalloc_fault_inject = 0;
+int g_noalloc_timeout_ms = 0;
 
 // Device address of the array on `device`, looked up once per device with that device
 // current.  Host code only ever sees the array through this address: the symbol name
@@ -1308,20 +1312,46 @@ extern "C" pgdto_status pgdto_project_noalloc(int64_t n, int m, const int64_t* s
     split_to_floats(0.5 * C, a.half_c_df);
     a.tol_lambda = p.tol_lambda;
     a.max_passes = p.max_passes;
-    a.timeout_cycles = (long long)clock_khz * (long long)p.barrier_timeout_ms;
+    int timeout_ms = p.barrier_timeout_ms;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        a.fault_inject = g_noalloc_fault_inject;
+        if (g_noalloc_timeout_ms > 0) timeout_ms = g_noalloc_timeout_ms;
+    }
+    a.timeout_cycles = (long long)clock_khz * (long long)timeout_ms;
     a.ws = (SegWork*)ws;
-    // the barrier counters and the sticky status must start at zero; the rest of the array
-    // keeps whatever the last call left and is rewritten before it is read
+    DeviceInfo* report = seg_work_info((SegWork*)ws);
+    // The barrier counters, the sticky status and the abort flag must start at zero.  The
+    // report is filled with 0xff bytes (status -1, NaN values): a kernel whose blocks gave
+    // up waiting never publishes it, and what the last call left there must not read as
+    // this call's result.  The rest of the array is rewritten before it is read.
     if (cudaMemsetAsync(ws, 0, sizeof(GridCtrl), stream) != cudaSuccess) return PGDTO_ERR_CUDA;
+    if (cudaMemsetAsync(report, 0xff, sizeof(DeviceInfo), stream) != cudaSuccess) return PGDTO_ERR_CUDA;
     if (launch_seg(a, max_blocks_seg(device), stream) != cudaSuccess) return PGDTO_ERR_CUDA;
     if (!info && !lambda_out) return PGDTO_OK;
     DeviceInfo di;
-    if (cudaMemcpyAsync(&di, seg_work_info((SegWork*)ws), sizeof(di), cudaMemcpyDeviceToHost, stream) !=
-        cudaSuccess)
+    int ctrl[4];  // GridCtrl: count, pad, sticky status, abort flag
+    if (cudaMemcpyAsync(&di, report, sizeof(di), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaMemcpyAsync(ctrl, ws, sizeof(ctrl), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
         return PGDTO_ERR_CUDA;
     if (cudaStreamSynchronize(stream) != cudaSuccess) return PGDTO_ERR_CUDA;
-    if (info) memcpy(info, &di, sizeof(di));
+    int status = di.status;
+    if (ctrl[3]) status = ctrl[2] ? ctrl[2] : PGDTO_ERR_TIMEOUT;  // a wait was abandoned
+    else if (ctrl[2] && status == PGDTO_OK) status = ctrl[2];
+    else if (status < PGDTO_OK || status > PGDTO_ERR_UNSUPPORTED) status = PGDTO_ERR_TIMEOUT;  // never published
+    if (info) {
+        memcpy(info, &di, sizeof(di));
+        info->status = status;
+    }
     if (lambda_out)
         for (int j = 0; j < m; ++j) lambda_out[j] = di.lambda[j];
-    return (pgdto_status)di.status;
+    return (pgdto_status)status;
+}
+
+extern "C" pgdto_status pgdto_noalloc_set_test_fault(int fault_inject, int timeout_ms) {
+    if ((fault_inject != 0 && fault_inject != 1) || timeout_ms < 0) return PGDTO_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    g_noalloc_fault_inject = fault_inject;
+    g_noalloc_timeout_ms = timeout_ms;
+    return PGDTO_OK;
 }
