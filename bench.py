@@ -1,17 +1,24 @@
 """Benchmark of the PGD-TO optimizer step on GB300.
 
-Default workload (the one the metric is quoted on): min volume under the nonlinear
-compliance row, 3D 128x64x64 hex mesh, n = 524288, m = 1, a 50-step trajectory from t = 0.
-A "step" is one full optimizer step (step size, PR+ direction, trial point, projection,
-x_{t+1}) through pgdto_step.  Between timed steps the synthetic sensitivities for the new
-design are regenerated on the device (the stand-in for the finite-element solve, not timed)
-and L2 is flushed by writing a 256 MiB buffer, so every step starts from HBM.
+Headline (``value``, ``roofline``, ``e2e``, ``cpu_baseline``): the largest single-GPU
+workload, four materials on a 3D 192x96x96 mesh, n = 7,077,888 variables in four
+independent volume rows, one full optimizer step from the seeded state (t = 1).  A "step"
+is one pgdto_step: step size, PR+ direction, trial point, projection, x_{t+1}.  Between
+timed steps the handle's state is reset to the seeded one and L2 is flushed by writing a
+256 MiB buffer, so every step starts from HBM.
+
+``workloads`` carries the other configurations the same way: 1 (2D 256x128, n = 32768),
+2 (the 50-step min-volume run on 3D 128x64x64, n = 524288; the timed steps continue the
+run) and 4 (volume + centre of mass, 3D 256x128x128, n = 4194304, four coupled rows).
+Every workload states its error against the FP64 oracle per result (lambda relative,
+x absolute, scaled row residual), computed by the oracle leg in worker processes.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload 1..4]
 
 N > 1 (under torchrun): each rank runs its own independent replica (weak scaling, no data
 collective); the job value is the steps of all ranks over the slowest rank's time.
---impl reference times the FP64 CPU oracle (paper's Alg. 1/2 projection) on the host cores.
+--impl reference times the FP64 CPU oracle (the paper's Alg. 1/2 projection) on the host
+cores, on the same workload, metric and unit.
 """
 
 from __future__ import annotations
@@ -20,6 +27,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -29,15 +37,20 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+HEADLINE = 3
 WORKLOADS = {
-    1: "volume_2d_256x128 (n=32768, m=1, one step from a prior step)",
-    2: "min_volume_3d_128x64x64 (n=524288, m=1, 50-step trajectory)",
+    1: "volume_2d_256x128 (n=32768, m=1)",
+    2: "min_volume_3d_128x64x64 (n=524288, m=1, 50-step run)",
     3: "multimaterial_3d_192x96x96_x4 (n=7077888, m=4 independent)",
     4: "volume_com_3d_256x128x128 (n=4194304, m=4 coupled)",
 }
 KERNEL_SOURCES = ["paper_2511_13905_gb300/csrc/seg_kernels.cu", "paper_2511_13905_gb300/csrc/dev_common.cuh",
                   "paper_2511_13905_gb300/csrc/coupled_kernels.cu", "paper_2511_13905_gb300/csrc/step_common.cuh",
                   "paper_2511_13905_gb300/csrc/kernels.h"]
+DTYPE = ("f32 bulk streams; double-float (FP32 pairs) step scalars, brackets, roots and reductions; "
+         "f64 in the coupled m x m Newton solve and in the report")
+TOL = 1e-6
+L2_BYTES = 126.5e6   # GB300 L2 (about 126 MB usable of the 129 MB quoted)
 
 
 def kernel_hash():
@@ -57,14 +70,14 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def measured_traffic(workload):
-    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernel."""
+def measured_traffic(key):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernel sources."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    e = d.get(str(workload))
+    e = d.get(str(key))
     if not e or e.get("kernel_hash") != kernel_hash():
         return None
     return e.get("dram_bytes_per_launch")
@@ -141,28 +154,90 @@ def algorithmic_bytes(n, m_eff, passes):
     return n * (16 + (20 + 4 * m_eff) + 4 * (1 + m_eff) * passes + (12 + 4 * m_eff))
 
 
-# --------------------------------------------------------------------------- our arm
+def compulsory_bytes(n, m_eff):
+    """Read x, x_prev, g, g_prev, d_prev and A once, write d and x_{t+1} once: 4 (5 + m_eff) + 8 per element."""
+    return n * (4 * (5 + m_eff) + 8)
 
-def run_ours(args, rank, world, local_rank):
+
+def pass_bytes(n, m_eff):
+    """One projection pass reads the trial point and the coefficients: 4 (1 + m_eff) per element."""
+    return n * 4 * (1 + m_eff)
+
+
+def roofline(n, m_eff, passes, step_s, bw_hbm, bw_l2, traffic, kernel):
+    """Both roofline readings of one step (bytes per launch over the event-timed launch):
+    streaming = the streaming-byte count at the passes actually run, against the HBM peak;
+    split = (compulsory bytes at the HBM rate + passes x pass bytes at the L2 read rate when
+    a pass fits L2, else at the HBM rate) / step time; compulsory = compulsory bytes alone."""
+    alg = algorithmic_bytes(n, m_eff, passes)
+    comp = compulsory_bytes(n, m_eff)
+    pb = pass_bytes(n, m_eff)
+    bw_pass = bw_l2 if (bw_l2 and pb <= L2_BYTES) else bw_hbm
+    t_floor = comp / (bw_hbm * 1e9) + passes * pb / (bw_pass * 1e9)
+    achieved = alg / step_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": bw_hbm, "unit": "GB/s", "frac": achieved / bw_hbm,
+            "traffic": traffic, "kernel": kernel, "algorithmic_bytes_per_launch": alg,
+            "frac_split": t_floor / step_s, "split_floor_us": 1e6 * t_floor,
+            "pass_bw_gbs": bw_pass, "pass_bytes": pb, "compulsory_bytes": comp,
+            "frac_compulsory": comp / step_s / 1e9 / bw_hbm}
+
+
+def kernel_name(n, mode):
+    if mode == "coupled":
+        return "pgdto::coupled_kernel (grid engine, one CTA per SM, cooperative)"
+    if n <= (1 << 17):
+        return "pgdto::seg_cluster_kernel (cluster engine, one thread-block cluster)"
+    return "pgdto::seg_kernel (grid engine, one CTA per SM, cooperative)"
+
+
+def make_cfg(wl):
+    from paper_2511_13905_gb300 import inputs
+    return {1: inputs.config1, 2: inputs.config2, 3: inputs.config3, 4: inputs.config4}[wl]()
+
+
+# --------------------------------------------------------------------------- probes
+
+def run_probes(dev, stream):
+    """L2 and HBM read rates of a plain streaming read (pgdto_probe_read), CUDA-event timed:
+    a 48 MiB buffer read 200 times in place (L2-resident after the first read), and a
+    4 GiB buffer read 5 times (HBM)."""
+    import torch
+    from paper_2511_13905_gb300 import binding
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = 4 * sms
+    out = torch.empty(blocks, device=dev)
+    res = {}
+    for name, nbytes, reps in (("l2_read_gbs", 48 << 20, 200), ("hbm_read_gbs", 4 << 30, 5)):
+        buf = torch.ones(nbytes // 4, device=dev)
+        for _ in range(3):
+            if binding.probe_read(buf, out, blocks) != 0:
+                raise RuntimeError("pgdto_probe_read failed")
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            binding.probe_read(buf, out, blocks)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = nbytes * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        del buf
+    res["how"] = ("pgdto_probe_read: 128-bit streaming reads, %d blocks x 512 threads; 48 MiB x 200 reads in place "
+                  "(L2), 4 GiB x 5 reads (HBM); CUDA events around the repeated launches" % blocks)
+    return res
+
+
+# --------------------------------------------------------------------------- device-timed workloads
+
+def time_workload(wl, args, dev, stream, flush, probes, world=1, local_rank=0, e2e=False):
+    """Warm-up and K timed pgdto_step launches of workload `wl`; returns the result dict
+    and the device outputs of the last timed step (for the oracle errors)."""
     import numpy as np
     import torch
 
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_2511_13905_gb300 import binding, inputs
 
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    stream = torch.cuda.current_stream()
-    wl = args.workload
-    if wl == 2:
-        cfg = inputs.config2()
-    elif wl == 1:
-        cfg = inputs.config1()
-    elif wl == 3:
-        cfg = inputs.config3()
-    else:
-        cfg = inputs.config4()
+    cfg = make_cfg(wl)
     n, m = cfg["n"], cfg["m"]
     m_eff = m if cfg["mode"] == "coupled" else 1
 
@@ -174,7 +249,8 @@ def run_ours(args, rank, world, local_rank):
     x = x0.clone()
     g = T(cfg["g"])
     G = cfg["G"]
-    if wl == 2:
+    trajectory = wl == 2
+    if trajectory:
         s_dev = T(cfg["s"]).double()
 
         def sensitivities(xc):
@@ -187,12 +263,7 @@ def run_ours(args, rank, world, local_rank):
         A_fixed = T(cfg["A"])
 
         def sensitivities(xc):
-            if cfg["mode"] == "independent":
-                seg = cfg["seg"]
-                xd = xc.double()
-                return A_fixed, [float(xd[seg[j]:seg[j + 1]].sum().item()) for j in range(m)]
-            Ad = A_fixed.reshape(m, n).double()
-            return A_fixed, (Ad @ xc.double()).tolist()
+            return A_fixed, list(cfg["gval"])
 
     def reset():
         x.copy_(x0)
@@ -201,21 +272,16 @@ def run_ours(args, rank, world, local_rank):
         else:
             h.set_state(None, None, None, 0)
 
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    trajectory = wl == 2
-
-    # warm-up (also checks that the step succeeds)
     reset()
     for _ in range(args.warmup):
         A, gval = sensitivities(x)
         st, info = h.step(x, g, A, gval, G)
-        if st != 0:
+        if st not in (0, binding.PGDTO_NOT_CONVERGED):
             raise RuntimeError("pgdto_step failed: %s" % binding.STATUS_NAMES.get(st, st))
         if not trajectory:
             reset()
     torch.cuda.synchronize()
 
-    # timed steps (device time, CUDA events on the launching stream)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -223,14 +289,14 @@ def run_ours(args, rank, world, local_rank):
     clocks.start()
     torch.cuda.synchronize()
     launches0 = h.kernel_launches()
-    evs = []
-    passes = []
+    evs, passes, newton = [], [], []
+    info = None
     for k in range(args.steps):
         A, gval = sensitivities(x)
         flush.fill_(float(k))
         # a bounded spin (about 0.1 ms) keeps the device busy while the host enqueues the
-        # step (about 50 us through the Python binding), so the events bracket device work;
-        # the host path is what the end-to-end figure measures
+        # step (tens of microseconds through the Python binding), so the events bracket
+        # device work; the host path is what the end-to-end figure measures
         torch.cuda._sleep(200_000)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -242,75 +308,96 @@ def run_ours(args, rank, world, local_rank):
         if st != 0 or st2 not in (0, binding.PGDTO_NOT_CONVERGED):
             raise RuntimeError("step %d failed: %s / %s" % (k, st, st2))
         passes.append(info.passes)
-        if not trajectory:
+        newton.append(info.newton_iters)
+        if not trajectory and k < args.steps - 1:
             reset()
     torch.cuda.synchronize()
     launches = h.kernel_launches() - launches0
     clk = clocks.stop()
     times_ms = [a.elapsed_time(b) for a, b in evs]
     value, total_s = combine_ranks(sum(times_ms) / 1e3, args.steps, world, dev)
+    out_x = x.cpu().numpy()
+    out_lam = list(info.lambda_)[:m]
 
-    # end to end through the host-buffer entry point (pinned memory, copies inside the timing)
-    xh = torch.from_numpy(cfg["x"].copy()).pin_memory()
-    gh = g.cpu().pin_memory()
-    reset()
-    e2e_times = []
-    for k in range(args.warmup + args.steps):
-        A, gval = sensitivities(xh.to(dev))
-        Ah = A.cpu().pin_memory()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st, info = h.step_host(xh, gh, Ah, gval, G)
-        t1 = time.perf_counter()
-        if st not in (0, binding.PGDTO_NOT_CONVERGED):
-            raise RuntimeError("step_host failed: %s" % st)
-        if k >= args.warmup:
-            e2e_times.append(t1 - t0)
-        if not trajectory:
-            xh.copy_(torch.from_numpy(cfg["x"]))
-            reset()
-    e2e_value, e2e_total = combine_ranks(sum(e2e_times), len(e2e_times), world, dev)
-    a_bytes = 4 * (m * n if cfg["mode"] == "coupled" or wl in (1, 2) else n)
-    h2d = 4 * n * 2 + a_bytes
-    d2h = 4 * n
-
-    avg_passes = sum(passes) / len(passes)
     step_s = total_s / args.steps
-    alg_bytes = algorithmic_bytes(n, m_eff, avg_passes)
-    peak, peak_kind = peaks()
-    achieved = alg_bytes / step_s / 1e9
-    result = {
-        "metric": "PGD-TO optimizer steps/s",
-        "value": value,
-        "unit": "steps/s",
-        "n_gpus": world,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": 1e3 * step_s,
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f32 (compensated sums, f64 scalars)",
-        "data": "synthetic",
-        "config": {"workload": cfg["name"], "n": n, "m": m, "mode": cfg["mode"],
-                   "trajectory": "50-step run from t=0" if trajectory else "one step from the seeded state",
-                   "l2": "flushed between timed steps (256 MiB write)",
-                   "timing": "CUDA events on the launching stream; a bounded spin kernel ahead of the start "
-                             "event keeps the device busy while the host enqueues the step",
-                   "parallelism": "replicas" if world > 1
-                   else "single GPU", "avg_projection_passes": avg_passes},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": measured_traffic(wl),
-                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                     else "fallback", "kernel": "pgdto::seg_kernel (fused step)",
-                     "algorithmic_bytes_per_launch": alg_bytes},
-        "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "api": "pgdto_step_host (pinned host buffers)"},
+    avg_passes = sum(passes) / len(passes)
+    bw, peak_kind = peaks()
+    res = {
+        "workload": cfg["name"], "n": n, "m": m, "mode": cfg["mode"],
+        "steps_per_s": value, "ms_per_step": 1e3 * step_s,
+        "ms_per_step_median": statistics.median(times_ms), "ms_per_step_min": min(times_ms),
+        "avg_projection_passes": avg_passes, "newton_iters": sum(newton) / len(newton),
+        "trajectory": ("steps t = 0..%d of the run from t = 0; timed t = %d..%d" %
+                       (args.warmup + args.steps - 1, args.warmup, args.warmup + args.steps - 1)) if trajectory
+        else "one step from the seeded state (t = %d), the state reset before each timed step" % cfg["t"],
+        "roofline": roofline(n, m_eff, avg_passes, step_s, bw, probes.get("l2_read_gbs"),
+                             measured_traffic(wl), kernel_name(n, cfg["mode"])),
         "gpu_launches": launches,
         "clocks": clk,
     }
+    res["roofline"]["peak_source"] = ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                                      else "fallback")
+
+    if e2e:
+        # end to end through the host-buffer entry point: pinned host x, grad f and A copied in,
+        # rho_{t+1} copied out, inside the timing
+        xh = torch.from_numpy(cfg["x"].copy()).pin_memory()
+        gh = torch.from_numpy(cfg["g"].copy()).pin_memory()
+        reset()
+        e2e_times = []
+        for k in range(args.warmup + args.steps):
+            A, gval = sensitivities(xh.to(dev))
+            Ah = A.cpu().pin_memory()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, info_h = h.step_host(xh, gh, Ah, gval, G)
+            t1 = time.perf_counter()
+            if st not in (0, binding.PGDTO_NOT_CONVERGED):
+                raise RuntimeError("step_host failed: %s" % st)
+            if k >= args.warmup:
+                e2e_times.append(t1 - t0)
+            if not trajectory:
+                xh.copy_(torch.from_numpy(cfg["x"]))
+                reset()
+        e2e_value, _ = combine_ranks(sum(e2e_times), len(e2e_times), world, dev)
+        a_bytes = 4 * int(np.asarray(cfg["A"]).size) if not trajectory else 4 * n
+        res["e2e"] = {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": 8 * n + a_bytes,
+                      "d2h_bytes_per_step": 4 * n, "api": "pgdto_step_host (pinned host buffers)"}
+
+    # the GPU's steps from the oracle's own states for the trajectory workload (its timed
+    # steps continue the device's run, whose states the oracle must not take as inputs)
     h.close()
-    return result
+    return res, {"x": out_x, "lam": out_lam}
+
+
+def run_trajectory_from_states(states, dev):
+    """Workload 2: one device step from each of the oracle's states (outside any timing)."""
+    import numpy as np
+    import torch
+
+    from paper_2511_13905_gb300 import binding, inputs
+    cfg = inputs.config2()
+    n = cfg["n"]
+
+    def T(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    h = binding.Handle(n, 1)
+    g = T(cfg["g"])
+    outs = []
+    for s in states:
+        x = T(s["x"])
+        A, gval = inputs.config2_inputs(cfg, s["x"])
+        if s["t"] > 0:
+            h.set_state(T(s["x_prev"]), g, T(s["d_prev"]), s["t"])
+        else:
+            h.set_state(None, None, None, 0)
+        st, info = h.step(x, g, T(A), gval, cfg["G"])
+        if st not in (0, binding.PGDTO_NOT_CONVERGED):
+            raise RuntimeError("workload 2 step t=%d failed: %s" % (s["t"], st))
+        outs.append({"x": x.cpu().numpy(), "lam": [info.lambda_[0]]})
+    h.close()
+    return outs
 
 
 # --------------------------------------------------------------------------- batched
@@ -386,13 +473,14 @@ def run_batched(args, local_rank=0):
 
     t_b, passes_b, launches_b, info_b = timed(batched, args.steps)
     x_b = [x.cpu().numpy() for x in xs]
+    lam_b = [[i.lambda_[0]] for i in info_b]
     t_p, passes_p, launches_p, info_p = timed(plain, args.steps)
     diff = max(float(np.max(np.abs(a.astype(np.float64) - x.cpu().numpy()))) for a, x in zip(x_b, xs))
     bytes_b = sum(algorithmic_bytes(n, 1, i.passes) for i in info_b)
     peak, _ = peaks()
     for h in hs:
         h.close()
-    return {"workload": "%d x volume_2d_256x128 (n=%d, m=1, one step each)" % (B, n),
+    res = {"workload": "%d x volume_2d_256x128 (n=%d, m=1, one step each)" % (B, n),
             "batched": {"ms": t_b, "steps_per_s": B / (t_b / 1e3), "launches": launches_b,
                         "passes_per_instance": passes_b / B,
                         "roofline": {"bound": "hbm", "achieved": bytes_b / (t_b / 1e3) / 1e9, "peak": peak,
@@ -404,6 +492,7 @@ def run_batched(args, local_rank=0):
             "max_abs_diff_x_batched_vs_plain": diff,
             "timing": "median of %d CUDA-event-timed repetitions, L2 flushed (256 MiB write) before each; "
                       "the events bracket device work (the host marshals behind a spin kernel)" % args.steps}
+    return res, {"x": x_b, "lam": lam_b}
 
 
 # --------------------------------------------------------------------------- serving
@@ -524,21 +613,107 @@ def run_serving(args, local_rank=0):
             "latency": "wave start to rho_{t+1} in host memory; every session submits one step per wave"}
 
 
-# --------------------------------------------------------------------------- oracle
+# --------------------------------------------------------------------------- oracle leg
+#
+# Everything below that calls the FP64 oracle runs in worker processes (spawned before the
+# first CUDA call): the CPU baseline (the oracle timed on the host cores) and, on the same
+# inputs, the oracle's results that the device results are compared with.  Inputs come
+# from the seeded generators only; the device results travel to the workers, never the
+# other way round.
 
-def oracle_workload(wl):
+def _oracle_cfg(wl, seed_offset=0):
     from paper_2511_13905_gb300 import inputs
-    if wl == 2:
-        return inputs.config2()
-    return {1: inputs.config1, 3: inputs.config3, 4: inputs.config4}[wl]()
+    return {1: inputs.config1, 2: inputs.config2, 3: inputs.config3, 4: inputs.config4}[wl](seed_offset=seed_offset)
 
 
-def time_oracle_steps(wl, nsteps, budget_s):
-    """Oracle steps ('paper' projector: Alg. 1 bisection / Alg. 2) on the workload; (steps, seconds)."""
+def _errors(cfg, ref, dev_x, dev_lam):
+    import numpy as np
+    from oracle.checks import parity_errors
+    lam = np.asarray(dev_lam, dtype=np.float64)
+    if cfg["mode"] == "independent":
+        seg = [int(s) for s in cfg["seg"]]
+        a = np.asarray(cfg["A"], dtype=np.float64)
+
+        def matvec(xv):
+            return (np.array([a[seg[j]:seg[j + 1]] @ xv[seg[j]:seg[j + 1]] for j in range(len(seg) - 1)]),
+                    np.array([np.abs(a[seg[j]:seg[j + 1]]) @ np.abs(xv[seg[j]:seg[j + 1]])
+                              for j in range(len(seg) - 1)]))
+        amax = [float(np.max(np.abs(a[seg[j]:seg[j + 1]]))) for j in range(len(seg) - 1)]
+        err = parity_errors(dev_x, lam, ref["x_new"], ref["lam"], matvec, ref["b"], 1e12, 0.0, 1.0, amax=amax)
+    else:
+        err = parity_errors(dev_x, lam, ref["x_new"], ref["lam"], cfg["A"], ref["b"], 1e12, 0.0, 1.0)
+    return {k: err[k] for k in ("lam_rel", "x_abs", "viol_rel")}
+
+
+def oracle_errors_seeded(wl, dev_x, dev_lam, seed_offset=0):
+    """The oracle's step on the seeded state of workload wl, and the device result's error."""
+    from oracle.step import oracle_step
+    cfg = _oracle_cfg(wl, seed_offset)
+    t0 = time.perf_counter()
+    ref = oracle_step(cfg["x"], cfg["x_prev"], cfg["g"], cfg["g_prev"], cfg["d_prev"], cfg["A"], cfg["gval"],
+                      cfg["G"], cfg["t"], mode=cfg["mode"], seg=cfg.get("seg"))
+    err = _errors(cfg, ref, dev_x, dev_lam)
+    err["oracle_s"] = time.perf_counter() - t0
+    return err
+
+
+def oracle_errors_batch(seed_offsets, dev_xs, dev_lams):
+    worst = {"lam_rel": 0.0, "x_abs": 0.0, "viol_rel": 0.0}
+    for so, xv, lv in zip(seed_offsets, dev_xs, dev_lams):
+        e = oracle_errors_seeded(1, xv, lv, so)
+        for k in worst:
+            worst[k] = max(worst[k], e[k])
+    return worst
+
+
+def oracle_trajectory_states(steps):
+    """The oracle's own workload-2 run, t = 0..steps-1, as float32 states a caller would hold."""
     import numpy as np
     from oracle.step import oracle_step
     from paper_2511_13905_gb300 import inputs
-    cfg = oracle_workload(wl)
+    cfg = inputs.config2()
+    n = cfg["n"]
+    x = cfg["x"].astype(np.float32)
+    x_prev = np.zeros(n, np.float32)
+    d_prev = np.zeros(n, np.float32)
+    g_prev = np.zeros(n, np.float32)
+    out = []
+    for t in range(steps):
+        A, gval = inputs.config2_inputs(cfg, x)
+        out.append({"t": t, "x": x.copy(), "x_prev": x_prev.copy(), "d_prev": d_prev.copy()})
+        ref = oracle_step(x, x_prev, cfg["g"], g_prev, d_prev, A, gval, cfg["G"], t, mode="single")
+        x_prev, g_prev, d_prev = x.copy(), cfg["g"].copy(), ref["d"].astype(np.float32)
+        x = ref["x_new"].astype(np.float32)
+    return out
+
+
+def oracle_errors_trajectory(states, dev_outs):
+    """Workload 2: the oracle's step from each state against the device step from it."""
+    from oracle.step import oracle_step
+    from paper_2511_13905_gb300 import inputs
+    import numpy as np
+    cfg = inputs.config2()
+    worst = {"lam_rel": 0.0, "x_abs": 0.0, "viol_rel": 0.0}
+    for s, o in zip(states, dev_outs):
+        A, gval = inputs.config2_inputs(cfg, s["x"])
+        g_prev = cfg["g"] if s["t"] > 0 else np.zeros(cfg["n"], np.float32)
+        ref = oracle_step(s["x"], s["x_prev"], cfg["g"], g_prev, s["d_prev"], A, gval, cfg["G"], s["t"],
+                          mode="single")
+        c = dict(cfg)
+        c["A"] = A
+        e = _errors(c, ref, o["x"], o["lam"])
+        for k in worst:
+            worst[k] = max(worst[k], e[k])
+    return worst
+
+
+def time_oracle_steps(wl, nsteps, budget_s):
+    """Oracle steps ('paper' projector: Alg. 1 bisection / Alg. 2 as printed) on the workload;
+    returns (steps, seconds).  Workload 2 continues its run; the others repeat the seeded step."""
+    import numpy as np
+    from oracle.step import oracle_step
+    from paper_2511_13905_gb300 import inputs
+    cfg = _oracle_cfg(wl)
     n = cfg["n"]
     x = cfg["x"].astype(np.float32)
     xp = cfg.get("x_prev", np.zeros(n, np.float32))
@@ -563,35 +738,82 @@ def time_oracle_steps(wl, nsteps, budget_s):
     return done, spent
 
 
-def cpu_baseline_subprocess(wl, nsteps, budget_s):
-    """Run the oracle timing in a child pinned to one BLAS/OpenMP thread; returns the dict."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
-               CUDA_VISIBLE_DEVICES="")
-    code = ("import json,sys; sys.path.insert(0, %r); import bench; d, s = bench.time_oracle_steps(%d, %d, %f); "
-            "print(json.dumps([d, s]))" % (ROOT, wl, nsteps, budget_s))
-    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
-    if r.returncode != 0:
-        return {"error": r.stderr[-400:]}
-    done, spent = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": done / spent, "unit": "steps/s", "cores": 1, "kind": "oracle",
-            "sample": "%d oracle steps of the same workload (FP64 NumPy, Alg. 1 bisection / Alg. 2 as printed), "
-                      "%.1f s of CPU time" % (done, spent)}
+def _one_thread_env():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def _pool(procs):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(processes=procs, initializer=_one_thread_env)
+
+
+def host_identity():
+    model = platform.processor() or platform.machine()
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for ln in r.stdout.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"cpu_count": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
+def cpu_baseline(wl, budget_s):
+    """The oracle on one host thread, then on every host core at once (one process per core,
+    each running whole steps of the same workload); value = steps per second of the whole
+    host.  Each process holds one copy of the workload, so the process count is also capped
+    by host memory (3 GB per process)."""
+    ident = host_identity()
+    pool = _pool(1)
+    try:
+        done, spent = pool.apply(time_oracle_steps, (wl, 100000, budget_s))
+    finally:
+        pool.close()
+        pool.join()
+    single = done / spent
+    procs = os.cpu_count() or 1
+    try:
+        mem = os.sysconf("SC_PHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        procs = max(1, min(procs, int(mem // (3 << 30))))
+    except (ValueError, OSError, AttributeError):
+        pass
+    pool = _pool(procs)
+    try:
+        t0 = time.perf_counter()
+        res = pool.starmap(time_oracle_steps, [(wl, 100000, budget_s)] * procs)
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    total = sum(d for d, _ in res)
+    longest = max(s for _, s in res)
+    return {"value": total / longest, "unit": "steps/s", "cores": procs, "kind": "oracle",
+            "sample": "%d full oracle steps of the same workload (FP64 NumPy; Alg. 1 bisection / Alg. 2 as "
+                      "printed), %d processes x %.0f s of CPU time each on the host cores (wall %.1f s)"
+                      % (total, procs, budget_s, wall),
+            "single_thread": {"value": single, "unit": "steps/s", "cores": 1,
+                              "sample": "%d oracle steps, %.1f s on one thread" % (done, spent)},
+            "host": ident}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
+    _one_thread_env()
     wl = args.workload
     # warm-up steps untimed, then K timed steps, each a full oracle step on the whole workload
-    time_oracle_steps(wl, args.warmup, 60.0)
+    time_oracle_steps(wl, args.warmup, 120.0)
     done, spent = time_oracle_steps(wl, args.steps, 240.0)
     v = done / spent
-    cfg_name = WORKLOADS[wl]
+    ident = host_identity()
     return {
         "impl": "reference", "metric": "PGD-TO optimizer steps/s", "value": v, "unit": "steps/s",
         "n_gpus": 1, "steps": done, "warmup": args.warmup, "ms_per_step": 1e3 * spent / done,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": cfg_name, "runs_on": "host CPU, 1 thread"},
+        "config": {"workload": WORKLOADS[wl], "runs_on": "host CPU, 1 thread (%s)" % ident["model"]},
         "cpu_baseline": {"value": v, "unit": "steps/s", "cores": 1, "kind": "oracle",
                          "sample": "%d full oracle steps (FP64 NumPy, Alg. 1 / Alg. 2 as printed)" % done},
         "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -604,10 +826,13 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", type=int, default=2, choices=[1, 2, 3, 4])
+    ap.add_argument("--workload", type=int, default=HEADLINE, choices=[1, 2, 3, 4])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true", help="headline workload only")
+    ap.add_argument("--no-errors", action="store_true", help="skip the oracle errors")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--batch-instances", type=int, default=256)
     ap.add_argument("--serve-sessions", type=int, default=48)
     ap.add_argument("--serve-waves", type=int, default=12)
@@ -623,20 +848,123 @@ def main():
         if res is not None:
             print(json.dumps(res))
         return
+
+    lead = rank == 0 and world == 1
+    errors = lead and not args.no_errors
+    pool = _pool(min(8, os.cpu_count() or 1)) if errors else None  # spawned before any CUDA call
+    pending = {}
+    traj_steps = args.warmup + args.steps
+    others = [w for w in (1, 2, 4) if w != args.workload] if lead and not args.no_workloads else []
+    if errors and (2 in others or args.workload == 2):
+        pending["traj_states"] = pool.apply_async(oracle_trajectory_states, (traj_steps,))
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
     if world > 1:
-        import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    res = run_ours(args, rank, world, local_rank)
-    if rank == 0 and world == 1 and not args.no_batched:
-        res["batched"] = run_batched(args, local_rank)
-    if rank == 0 and world == 1 and not args.no_serving:
-        res["serving"] = run_serving(args, local_rank)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    probes = run_probes(dev, stream) if lead else {}
+
+    head, head_out = time_workload(args.workload, args, dev, stream, flush, probes, world, local_rank, e2e=True)
+    if errors and args.workload != 2:
+        pending["err_%d" % args.workload] = pool.apply_async(
+            oracle_errors_seeded, (args.workload, head_out["x"], head_out["lam"]))
+    subs = {}
+    for wl in others:
+        r, o = time_workload(wl, args, dev, stream, flush, probes)
+        subs[wl] = r
+        if errors and wl != 2:
+            pending["err_%d" % wl] = pool.apply_async(oracle_errors_seeded, (wl, o["x"], o["lam"]))
+    if errors and "traj_states" in pending:
+        states = pending.pop("traj_states").get()
+        outs = run_trajectory_from_states(states, dev)
+        pending["err_2"] = pool.apply_async(oracle_errors_trajectory, (states, outs))
+        del states, outs
+    batched = None
+    if lead and not args.no_batched:
+        batched, bouts = run_batched(args, local_rank)
+        if errors:
+            k = len(bouts["x"])
+            chunks = [list(range(i, k, 8)) for i in range(8)]
+            pending["err_batched"] = [pool.apply_async(oracle_errors_batch, ([i for i in c],
+                                                                             [bouts["x"][i] for i in c],
+                                                                             [bouts["lam"][i] for i in c]))
+                                      for c in chunks]
+    # the oracle results; host-timed measurements (serving, the CPU baseline) run after
+    # them so that the worker processes do not compete for the host
+    err = {}
+    for key, fut in pending.items():
+        if isinstance(fut, list):
+            parts = [f.get() for f in fut]
+            err[key] = {k: max(p[k] for p in parts) for k in parts[0]}
+        else:
+            err[key] = fut.get()
+    if pool is not None:
+        pool.close()
+        pool.join()
+
+    def attach(res, wl):
+        e = err.get("err_%d" % wl)
+        if e is not None:
+            e = dict(e)
+            e["tolerance"] = TOL
+            e["within_tolerance"] = all(e[k] <= TOL for k in ("lam_rel", "x_abs", "viol_rel"))
+            e["against"] = ("the oracle's step from its own state at each t = 0..%d" % (traj_steps - 1)
+                            if wl == 2 else "the oracle's step on the timed step's inputs")
+            res["oracle_errors"] = e
+
+    attach(head, args.workload)
+    for wl, r in subs.items():
+        attach(r, wl)
+    if batched is not None and "err_batched" in err:
+        batched["oracle_errors"] = dict(err["err_batched"], tolerance=TOL,
+                                        against="each instance against the oracle's step on its seeded state")
+
+    result = {
+        "metric": "PGD-TO optimizer steps/s",
+        "value": head["steps_per_s"],
+        "unit": "steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": DTYPE,
+        "data": "synthetic",
+        "config": {"workload": head["workload"], "n": head["n"], "m": head["m"], "mode": head["mode"],
+                   "trajectory": head["trajectory"],
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "timing": "CUDA events on the launching stream around each pgdto_step launch; a bounded "
+                             "spin kernel ahead of the start event keeps the device busy while the host enqueues",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "avg_projection_passes": head["avg_projection_passes"],
+                   "ms_per_step_median": head["ms_per_step_median"]},
+        "roofline": head["roofline"],
+        "e2e": head["e2e"],
+        "gpu_launches": head["gpu_launches"],
+        "clocks": head["clocks"],
+    }
+    if "oracle_errors" in head:
+        result["oracle_errors"] = head["oracle_errors"]
+    if probes:
+        result["probes"] = probes
+    if subs:
+        result["workloads"] = {str(wl): r for wl, r in subs.items()}
+    if batched is not None:
+        result["batched"] = batched
+    if lead and not args.no_serving:
+        result["serving"] = run_serving(args, local_rank)
+    if lead and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_budget)
     if rank == 0:
-        if not args.no_cpu_baseline and world == 1:
-            res["cpu_baseline"] = cpu_baseline_subprocess(args.workload, 1000, 20.0)
-        print(json.dumps(res))
+        print(json.dumps(result))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

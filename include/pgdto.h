@@ -329,6 +329,17 @@ pgdto_status pgdto_project_noalloc(int64_t n, int m, const int64_t* seg_offsets,
  * PGDTO_ERR_TIMEOUT; nothing faults, traps or hangs.  (0, 0) restores normal calls. */
 pgdto_status pgdto_noalloc_set_test_fault(int fault_inject, int timeout_ms);
 
+/*
+ * Read-bandwidth probe (measurement tooling; the paper has no counterpart).  Enqueues one
+ * kernel that reads the n floats at buf once with 128-bit loads (n a multiple of 4, buf
+ * 16-byte aligned, both device) and writes one partial sum per block to out (device,
+ * `blocks` floats).  Timing repeated launches with CUDA events gives the L2 read rate for
+ * a buffer well under the L2 size and the HBM read rate for one far above it: the two
+ * bounds of the projection passes.  PGDTO_ERR_ARG on bad arguments, PGDTO_ERR_CUDA if the
+ * launch fails.
+ */
+pgdto_status pgdto_probe_read(const float* buf, int64_t n, float* out, int blocks, void* cuda_stream);
+
 /* Library version string, e.g. "pgdto-gb300 0.1 sm_103a". */
 const char* pgdto_version(void);
 

@@ -83,7 +83,7 @@ def step_scalars(x, x_prev, g, g_prev, t, gval, G, p: StepParams, eq=None):
 
 
 def oracle_step(x, x_prev, g, g_prev, d_prev, A, gval, G, t, p: StepParams | None = None,
-                mode="single", seg=None, projector="exact", lo=0.0, hi=1.0, eq=None):
+                mode="single", seg=None, projector="exact", lo=0.0, hi=1.0, eq=None, lam_given=None):
     """One Alg. 3 iteration.  Returns a dict with x_new, d, z, lam, b, alpha, beta, ...
 
     mode: 'single' (A is one row), 'independent' (A holds one coefficient per variable
@@ -91,6 +91,9 @@ def oracle_step(x, x_prev, g, g_prev, d_prev, A, gval, G, t, p: StepParams | Non
     unique optimum (what parity is measured against); 'paper' runs Alg. 1 / Alg. 2 with
     the paper's tolerances (what the CPU baseline times).  eq: boolean mask of the
     equality rows g_j(x) = G_j (Sec. 3.2.4), linearised the same way.
+    lam_given: multipliers to use instead of solving (a stored result of the exact
+    projector for a problem too large to solve again in a test, written by a script under
+    tests/golden that calls this function); everything else is computed as above.
     """
     p = p or StepParams()
     x = np.asarray(x, dtype=np.float64)
@@ -107,7 +110,9 @@ def oracle_step(x, x_prev, g, g_prev, d_prev, A, gval, G, t, p: StepParams | Non
         seg = [int(s) for s in seg]
         ax = np.array([a[seg[j]:seg[j + 1]] @ x[seg[j]:seg[j + 1]] for j in range(len(seg) - 1)])
         b = G - gval + ax
-        if projector == "exact":
+        if lam_given is not None:
+            lam = np.asarray(lam_given, dtype=np.float64)
+        elif projector == "exact":
             lam = P.solve_independent_exact(z, a, seg, b, lo, hi, p.C, eq=eq)
         else:
             lam, _ = P.solve_independent_bisect(z, a, seg, b, lo, hi, p.C, p.tol_B, eq=eq)
@@ -117,7 +122,9 @@ def oracle_step(x, x_prev, g, g_prev, d_prev, A, gval, G, t, p: StepParams | Non
         A2 = np.atleast_2d(np.asarray(A, dtype=np.float64))
         b = G - gval + A2 @ x
         E = P.eq_mask(eq, A2.shape[0])
-        if A2.shape[0] == 1 or mode == "single":
+        if lam_given is not None:
+            lam = np.asarray(lam_given, dtype=np.float64)
+        elif A2.shape[0] == 1 or mode == "single":
             if projector == "exact":
                 lam = np.array([P.solve_single_exact(z, A2[0], b[0], lo, hi, p.C, equality=bool(E[0]))])
             else:

@@ -105,6 +105,7 @@ def load(path=None):
                                                  ctypes.c_float, ctypes.c_float, ctypes.c_double, P, P, D, P, D,
                                                  ctypes.POINTER(Info), P]),
         "pgdto_noalloc_set_test_fault": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+        "pgdto_probe_read": (ctypes.c_int, [P, ctypes.c_int64, P, ctypes.c_int, P]),
         "pgdto_version": (ctypes.c_char_p, []),
         "pgdto_server_create": (ctypes.c_int, [ctypes.POINTER(H), ctypes.c_uint64, ctypes.c_int,
                                                ctypes.POINTER(Params), P]),
@@ -263,6 +264,11 @@ def project_noalloc(z, A, b, x_out, m=1, seg=None, lo=0.0, hi=1.0, C=1e12, strea
 def noalloc_set_test_fault(fault_inject, timeout_ms):
     """pgdto_noalloc_set_test_fault (tests only)."""
     return load().pgdto_noalloc_set_test_fault(int(fault_inject), int(timeout_ms))
+
+
+def probe_read(buf, out, blocks, stream=None):
+    """pgdto_probe_read: one streaming read of the device tensor buf (measurement tooling)."""
+    return load().pgdto_probe_read(_dptr(buf), int(buf.numel()), _dptr(out), int(blocks), _stream_ptr(stream))
 
 
 def _ptrs(ts):

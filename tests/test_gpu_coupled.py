@@ -1,16 +1,21 @@
 """Parity of the coupled-row CUDA path (Alg. 2: single-row candidates, then Newton on the
 m x m Jacobian) with the FP64 oracle's exact optimum, through the C ABI."""
 
+import json
+import os
+
 import numpy as np
 import pytest
 
 from oracle import oracle_step
+from oracle.checks import kkt_report
 from oracle import projection as P
 from oracle.checks import parity_errors
 from paper_2511_13905_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 C = 1e12
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 TOL = {"lam_rel": 1e-6, "x_abs": 1e-6, "viol_rel": 1e-6}
 
 
@@ -108,7 +113,7 @@ def test_project_coupled_all_inactive(dev):
 
 
 @pytest.mark.parametrize("dims,infeasible", [((32, 16, 16), False), ((64, 32, 32), False),
-                                             ((32, 16, 16), True), (None, False)])
+                                             ((32, 16, 16), True), (None, False), (None, True)])
 def test_step_config4(dev, dims, infeasible):
     import torch
     from paper_2511_13905_gb300 import binding
@@ -120,11 +125,30 @@ def test_step_config4(dev, dims, infeasible):
     st, info = h.step(x, T(cfg["g"], dev), T(cfg["A"], dev), cfg["gval"], cfg["G"])
     torch.cuda.synchronize()
     assert st == 0, info.as_dict(m)
+    lam_given = None
+    if dims is None and infeasible:
+        # the exact coupled solve of this problem takes minutes of CPU time: its multipliers
+        # were stored by tests/golden/make_config4_infeasible.py (oracle only), and are
+        # checked here against the KKT conditions of the problem rebuilt from the seed
+        with open(os.path.join(GOLDEN, "config4_infeasible_full.json")) as f:
+            gold = json.load(f)
+        assert gold["n"] == n and gold["m"] == m
+        lam_given = gold["lam"]
     ref = oracle_step(cfg["x"], cfg["x_prev"], cfg["g"], cfg["g_prev"], cfg["d_prev"], cfg["A"], cfg["gval"],
-                      cfg["G"], cfg["t"], mode="coupled")
+                      cfg["G"], cfg["t"], mode="coupled", lam_given=lam_given)
+    if lam_given is not None:
+        A64 = np.asarray(cfg["A"], dtype=np.float64)
+        rep = kkt_report(ref["z"], A64, ref["b"], ref["lam"], ref["x_new"], 0.0, 1.0, C)
+        assert rep["worst"] <= 1e-9, rep
+        assert np.allclose(ref["b"], gold["b"], rtol=1e-12)
     assert info.alpha == pytest.approx(ref["alpha"], rel=1e-6)
     assert info.beta == pytest.approx(ref["beta"], rel=1e-6, abs=1e-12)
     lam = np.array(list(info.lambda_)[:m])
-    check(parity_errors(x.cpu().numpy(), lam, ref["x_new"], ref["lam"], cfg["A"], ref["b"], C, 0.0, 1.0),
-          cfg["name"])
+    err = parity_errors(x.cpu().numpy(), lam, ref["x_new"], ref["lam"], cfg["A"], ref["b"], C, 0.0, 1.0)
+    print("%s: lam %s (oracle %s), errors %s" % (cfg["name"], lam, ref["lam"],
+                                                {k: err[k] for k in ("lam_rel", "x_abs", "viol_rel")}))
+    check(err, cfg["name"])
+    if infeasible:
+        # the regularised branch (Sec. 3.2.3): the infeasible row's multiplier is of order C
+        assert np.max(ref["lam"]) > 1e9 and np.max(lam) > 1e9
     h.close()

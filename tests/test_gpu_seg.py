@@ -248,7 +248,7 @@ def _config2_state_sequence(cfg, steps):
     return seq
 
 
-@pytest.mark.parametrize("dims,steps", [((32, 16, 16), 50), (None, 4)])
+@pytest.mark.parametrize("dims,steps", [((32, 16, 16), 50), (None, 50)])
 def test_step_config2_trajectory(dev, dims, steps):
     """Every step of the workload-2 run, fed the oracle's state, against the oracle's step."""
     from paper_2511_13905_gb300 import binding
