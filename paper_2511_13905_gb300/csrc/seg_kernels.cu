@@ -202,8 +202,10 @@ __device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegState*
     // search's FP32 trial sums carry rounding noise (well under 1e-6 (|b| + |a^T x|)),
     // which can leave its root outside its last bracket by up to that noise over the
     // slope, on a neighbouring linear piece.  A correction within four bracket widths or
-    // that noise scale is taken; one larger than 1e-7 lam (the estimate was on another
-    // piece) runs this pass again at the corrected lam, at most eight times.
+    // that noise scale is taken.  The pass wrote x at the uncorrected lam, and a change dl
+    // of lam moves a free x_i by dl a_i: a correction larger than 1e-7 lam, or one that
+    // moves some free x_i by more than 1e-7 (max |a_i| over the free set), runs this pass
+    // again at the corrected lam, at most eight times.
     const bool eqj = (a.eq_mask >> j) & 1;
     bool again = false;
     if (rl && rows[j].how == 2 && (df_pos(lam) || eqj)) {
@@ -215,7 +217,7 @@ __device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegState*
         const DF ln = df_add(lam, dl);
         if (near && (df_pos(ln) || eqj)) {
             lam = ln;
-            if (adl > 1e-7f * fabsf(lam.hi) && rows[j].nrefine < 8) {
+            if ((adl > 1e-7f * fabsf(lam.hi) || adl * sc.totmax[j] > 1e-7f) && rows[j].nrefine < 8) {
                 rows[j].nrefine = rows[j].nrefine + 1;
                 rows[j].lam_hi = lam.hi;
                 rows[j].lam_lo = lam.lo;
@@ -919,6 +921,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
     for (;;) {
         AccSplit<2 * kMaxRows + 2, 0> acc;
         acc.init();
+        float amax_free[kMaxRows] = {0.0f, 0.0f, 0.0f, 0.0f};
         int roff = 0;
         for (int j = 0; j < a.nrows; ++j) {
             const float lh = bc.lam_hi[j], ll = bc.lam_lo[j];
@@ -928,6 +931,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
             const int off = roff;
             roff += seg_res_span(cb, ce);
             float sh = 0.0f, sl = 0.0f, sfree = 0.0f;  // a^T x as hi (TwoSum) + lo; slope
+            float amf = 0.0f;  // max |a| over the free set: how far a change of lam moves x
             int cnt = 0;
             auto e = [&](float x, float zh, float zl, float av) -> float {
                 const float p = lh * av;
@@ -945,6 +949,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 sh = t.hi;
                 sl = __fadd_rn(sl, __fadd_rn(t.lo, fmaf(av, xn, -ph) + av * xl));
                 sfree = fr ? fmaf(av, av, sfree) : sfree;
+                amf = fr ? fmaxf(amf, fabsf(av)) : amf;
                 const float dx = xn - x;
                 acc.f[2 * kMaxRows] = fmaf(dx, dx, acc.f[2 * kMaxRows]);
                 acc.f[2 * kMaxRows + 1] = fmaf(xn, xn, acc.f[2 * kMaxRows + 1]);
@@ -1017,6 +1022,9 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                     });
             }
             fold();
+#pragma unroll
+            for (int q = 0; q < kMaxRows; ++q)
+                if (q == j) amax_free[q] = amf;  // register select, no indexed local array
         }
         acc.fold();
         // pack: rows' a^T x, rows' slopes, then the two norms
@@ -1031,8 +1039,8 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
         packed[2 * nr] = acc.d[2 * kMaxRows];
         packed[2 * nr + 1] = acc.d[2 * kMaxRows + 1];
         const int nv = 2 * nr + (a.proj ? 0 : 2);
-        block_reduce<2 * kMaxRows + 2, 0>(packed, nullptr, sc);
-        if (!sy.reduce(sc, nv, 0, [&](BlockScratch& s, SegState* st) { update_final(a, s, st, sy.sticky(), sy.launches()); }))
+        block_reduce<2 * kMaxRows + 2, kMaxRows>(packed, amax_free, sc);
+        if (!sy.reduce(sc, nv, nr, [&](BlockScratch& s, SegState* st) { update_final(a, s, st, sy.sticky(), sy.launches()); }))
             return;
         sy.fetch(bc);
         if (!bc.refine) break;
