@@ -72,7 +72,11 @@ typedef struct {
     double eps_alpha;       /* BB1 threshold on s^T y, 1e-6 (Sec. 3.4) */
     double c1;              /* Armijo constant of the Newton line search, 1e-4 (App. A.3.3) */
     double c2;              /* curvature constant, 0.9 (App. A.3.3; recorded, not enforced) */
-    double tol_lambda;      /* relative width at which a dual root search stops, 1e-10 */
+    double tol_lambda;      /* relative width at which a dual root search stops, 1e-10; a row
+                               search also stops once both Newton predictions agree to 100
+                               tol_lambda and to 1e-8 / max_i |a_i| (the final pass takes one
+                               exact Newton step from there, and runs again if that step moves
+                               lam by more than 1e-7 lam or some free x_i by more than 1e-7) */
     int t_warmup;           /* steps before the fallback rule applies, 50 (Sec. 3.4) */
     int maxiter_newton;     /* Alg. 2 maxiter (the paper gives none), 50 */
     int max_passes;         /* cap on root-search passes per projection, 64 */
@@ -95,7 +99,7 @@ typedef struct {
                                active, lambda_j of either sign, and its violation for the
                                fallback rule is |g_j - G_j|; bits at or above m must be 0 */
     int compaction;         /* single/independent rows: 1 = free-set compaction (Sec. 4.2.1) -- once
-                               the bracket is within 10% of the root, elements whose clip state it
+                               the bracket is within 50% of the root, elements whose clip state it
                                fixes are summed once and later passes visit the rest (shares that
                                stream from global memory only); 0 (default) = every pass visits
                                every element, which measured faster on the shipped workloads */

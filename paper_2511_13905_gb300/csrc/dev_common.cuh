@@ -29,7 +29,7 @@ constexpr int kClusterThreads = 256;
 constexpr int kMaxBlocks = 1024;
 constexpr int kMaxVals = 136;   // DF values per grid reduction (4 rows x 2 x 16 points + spare)
 constexpr int kMaxBlockVals = 32;  // DF values one block_reduce call gathers per warp
-constexpr int kMaxMax = 8;      // float max values per grid reduction
+constexpr int kMaxMax = 12;     // float max values per grid reduction (3 per row of 4)
 
 // status codes shared with include/pgdto.h
 enum : int { kOk = 0, kErrNonfinite = 4, kErrTimeout = 5, kNotConverged = 7 };

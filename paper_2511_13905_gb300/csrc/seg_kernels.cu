@@ -94,8 +94,9 @@ __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, Seg
     const DF ax = a.proj ? df_zero() : sc.tot[5 * jj + 0];
     const DF r0s = sc.tot[5 * jj + 1], sf = sc.tot[5 * jj + 2];
     const DF smin = sc.tot[5 * jj + 3], smax = sc.tot[5 * jj + 4];
-    const float lsat = sc.totmax[2 * jj];
-    const float lneg = -sc.totmax[2 * jj + 1];
+    const float lsat = sc.totmax[3 * jj];
+    const float lneg = -sc.totmax[3 * jj + 1];
+    const float amax = sc.totmax[3 * jj + 2];
     const bool eq = (a.eq_mask >> jj) & 1;
     const bool finite = isfinite(ax.hi) && isfinite(r0s.hi) && isfinite(sf.hi) && isfinite(smin.hi) &&
                         isfinite(smax.hi);
@@ -148,6 +149,7 @@ __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, Seg
         rows[j].reg = a.two_c;
         if (search) {
             store_row_df(&rows[j], b, L, rL, SLs, H, rH, SHs, df_zero(), 0.0, two_c.hi, 1, 2);
+            rows[j].famax = amax;
             bc->active[j] = 1;
             bc->cmode[j] = 0;
             bc->brL[j] = L;
@@ -383,14 +385,17 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 acc.f[5] = fmaf(g, g, acc.f[5]);
                 gmax = fmaxf(gmax, fabsf(g));
             };
-            for_chunk<VEC>(
+            struct G4 {
+                float4 x, xp, g, gp;
+            };
+            for_chunk_x2<VEC>(
                 cb, ce,
-                [&](int64_t v) {
-                    float4 x = LD4L2(a.x, v), xp = LD4(a.x_prev, v), g = LD4L2(a.g, v), gp = LD4(a.g_prev, v);
-                    e(x.x, xp.x, g.x, gp.x);
-                    e(x.y, xp.y, g.y, gp.y);
-                    e(x.z, xp.z, g.z, gp.z);
-                    e(x.w, xp.w, g.w, gp.w);
+                [&](int64_t v) { return G4{LD4L2(a.x, v), LD4(a.x_prev, v), LD4L2(a.g, v), LD4(a.g_prev, v)}; },
+                [&](const G4& q) {
+                    e(q.x.x, q.xp.x, q.g.x, q.gp.x);
+                    e(q.x.y, q.xp.y, q.g.y, q.gp.y);
+                    e(q.x.z, q.xp.z, q.g.z, q.gp.z);
+                    e(q.x.w, q.xp.w, q.g.w, q.gp.w);
                     acc.tick();
                 },
                 [&](int64_t i) {
@@ -402,10 +407,9 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 acc.f[5] = fmaf(g, g, acc.f[5]);
                 gmax = fmaxf(gmax, fabsf(g));
             };
-            for_chunk<VEC>(
-                cb, ce,
-                [&](int64_t v) {
-                    float4 g = LD4L2(a.g, v);
+            for_chunk_x2<VEC>(
+                cb, ce, [&](int64_t v) { return LD4L2(a.g, v); },
+                [&](const float4& g) {
                     e(g.x);
                     e(g.y);
                     e(g.z);
@@ -450,7 +454,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
         for (int j = 0; j < a.nrows; ++j) {
             AccSplit<5, 0> acc;
             acc.init();
-            float lsat = 0.0f, lnegm = 0.0f;
+            float lsat = 0.0f, lnegm = 0.0f, amx = 0.0f;
             const bool eqj = (a.eq_mask >> j) & 1;
             int64_t cb, ce;
             block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
@@ -475,6 +479,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 acc.f[2] = fr ? fmaf(av, av, acc.f[2]) : acc.f[2];
                 acc.f[3] += av > 0.0f ? av * lo : (av < 0.0f ? av * hi : 0.0f);
                 acc.f[4] += av > 0.0f ? av * hi : (av < 0.0f ? av * lo : 0.0f);
+                amx = fmaxf(amx, fabsf(av));
                 if (av != 0.0f) {
                     // saturation bounds: only used widened by 1e-5, so a fast division will do
                     const float ra = __fdividef(1.0f, av);
@@ -534,11 +539,19 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                     zl = z.lo;
                     e(z.hi, z.lo, av, x);
                 };
-                for_chunk<VEC>(
+                struct B4 {
+                    int64_t v;
+                    float4 x, g, av, dp;
+                };
+                for_chunk_x2<VEC>(
                     cb, ce,
                     [&](int64_t v) {
-                        float4 x = LD4L2(a.x, v), g = LD4L2(a.g, v), av = LD4L2(a.A, v);
-                        float4 dp = first ? make_float4(0.f, 0.f, 0.f, 0.f) : LD4(a.d_prev, v);
+                        return B4{v, LD4L2(a.x, v), LD4L2(a.g, v), LD4L2(a.A, v),
+                                  first ? make_float4(0.f, 0.f, 0.f, 0.f) : LD4(a.d_prev, v)};
+                    },
+                    [&](const B4& q) {
+                        const int64_t v = q.v;
+                        const float4 x = q.x, g = q.g, av = q.av, dp = q.dp;
                         float4 d, zh, zl;
                         st(x.x, g.x, dp.x, av.x, d.x, zh.x, zl.x);
                         st(x.y, g.y, dp.y, av.y, d.y, zh.y, zl.y);
@@ -579,11 +592,11 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
             acc.fold();
             acc.d[0] = df_add(acc.d[0], fast_two_sum(axh, axl));
             acc.d[1] = df_add(acc.d[1], fast_two_sum(r0h, r0l));
-            float mx[2] = {lsat, lnegm};
-            block_reduce<5, 2>(acc.d, mx, sc, 5 * j, 2 * j);
+            float mx[3] = {lsat, lnegm, amx};
+            block_reduce<5, 3>(acc.d, mx, sc, 5 * j, 3 * j);
         }
         if (!ladder) {
-            if (!sy.reduce(sc, 5 * a.nrows, 2 * a.nrows,
+            if (!sy.reduce(sc, 5 * a.nrows, 3 * a.nrows,
                            [&](BlockScratch& s, SegState* st) { update_after_trial(a, s, st); }))
                 return;
             sy.fetch(bc);
@@ -765,15 +778,16 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                     search_pass_update<SegBcast, true>(s, 0, st->rows, &st->bc, a.nrows, a.tol_lambda, a.max_passes);
                     __syncwarp();
                     // the next pass classifies against the bracket its points will lie in.  The
-                    // lists are built once the bracket is within 10% of the root (the share of
-                    // elements it leaves undecided follows its width) and used from then on
+                    // lists are built once the bracket is within 50% of the root (the share of
+                    // elements it leaves undecided follows its width; the search usually ends
+                    // two passes later) and used from then on
                     if (threadIdx.x < a.nrows) {
                         const int r = threadIdx.x;
                         volatile SegBcast* vb = &st->bc;
                         if (vb->active[r]) {
                             const float L = st->rows[r].fL, H = st->rows[r].fH;
                             const int cm = vb->cmode[r];
-                            const bool narrow = (H - L) <= 0.1f * fmaxf(fabsf(L), fabsf(H));
+                            const bool narrow = (H - L) <= 0.5f * fmaxf(fabsf(L), fabsf(H));
                             vb->cmode[r] = !a.cidx ? 0 : (cm >= 1 ? 2 : (narrow ? 1 : 0));
                             vb->brL[r] = L;
                             vb->brH[r] = H;
@@ -809,50 +823,90 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
 #pragma unroll
                     for (int k = 0; k < K; ++k) p[k] = bc.pts[j][k];
                 }
-                AccSplit<K, K, 2, 8> acc;
+                // acc.f[0, K): r sums at the points of the elements whose clip state changes
+                // between the lowest and the highest point; [K, K + 3): the other elements as
+                // C = sum a bound (clipped at every point), AZ = sum a w_m and AA = sum a^2
+                // (free at every point; w_m the value at the reference point); [K + 3, 2K + 3):
+                // free-set curvature at the points.  w = z - t a is monotone in t, so the state
+                // at both extreme points decides every point between them; once the bracket is
+                // narrow almost every element is decided and costs a few operations, not 8 x 7.
+                // The decision costs a few operations per element and pays only when the
+                // points are close together (few elements change state between them); the
+                // span test is the same in every thread, so a pass takes one loop or the other.
+                AccSplit<K + 3, K, 2, 8> acc;
                 acc.init();
-                auto e = [&](float z, float zl, float av) {
+                const float pm = p[kMidPoint];
+                const bool narrow = (p[K - 1] - p[0]) <= 4e-3f * fmaxf(fabsf(p[0]), fabsf(p[K - 1]));
+                auto all_points = [&](float z, float zl, float av) {
                     const float aa = av * av;
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
                         const float w = __fadd_rn(fmaf(-p[k], av, z), zl);
                         const float x = clampf(w, lo, hi);  // free exactly when the clip leaves w
                         acc.f[k] = fmaf(av, x, acc.f[k]);
-                        acc.f[K + k] += (x == w) ? aa : 0.0f;
+                        acc.f[K + 3 + k] += (x == w) ? aa : 0.0f;
                     }
+                };
+                auto e = [&](float z, float zl, float av) {
+                    if (narrow) {
+                        const float w0 = __fadd_rn(fmaf(-p[0], av, z), zl);
+                        const float w1 = __fadd_rn(fmaf(-p[K - 1], av, z), zl);
+                        const float wmn = fminf(w0, w1), wmx = fmaxf(w0, w1);
+                        if (wmx < lo || wmn > hi) {
+                            acc.f[K] = fmaf(av, wmx < lo ? lo : hi, acc.f[K]);
+                            return;
+                        }
+                        if (wmn >= lo && wmx <= hi) {
+                            acc.f[K + 1] = fmaf(av, __fadd_rn(fmaf(-pm, av, z), zl), acc.f[K + 1]);
+                            acc.f[K + 2] = fmaf(av, av, acc.f[K + 2]);
+                            return;
+                        }
+                    }
+                    all_points(z, zl, av);
                 };
                 auto run = [&](auto rc, auto lc) {
                     constexpr bool R = decltype(rc)::value;
                     constexpr bool HL = decltype(lc)::value;
-                    for_chunk<VEC>(
-                        cb, ce,
-                        [&](int64_t v) {
-                            float4 z, zl = make_float4(0.f, 0.f, 0.f, 0.f), av;
-                            if constexpr (R) {
+                    struct P4 {
+                        float4 z, zl, av;
+                    };
+                    auto use4 = [&](const P4& q) {
+                        e(q.z.x, q.zl.x, q.av.x);
+                        e(q.z.y, q.zl.y, q.av.y);
+                        e(q.z.z, q.zl.z, q.av.z);
+                        e(q.z.w, q.zl.w, q.av.w);
+                        acc.tick();
+                    };
+                    auto use1 = [&](int64_t i) {
+                        if constexpr (R) {
+                            const int q = off + (int)(i - rb);
+                            e(smz[q], HL ? sml[q] : 0.0f, sma[q]);
+                        } else {
+                            e(zsrc[i], HL ? a.zlo[i] : 0.0f, a.A[i]);
+                        }
+                        acc.tick();
+                    };
+                    if constexpr (R) {
+                        // shared memory: short latency, one group per iteration
+                        for_chunk<VEC>(
+                            cb, ce,
+                            [&](int64_t v) {
                                 const int q = (off >> 2) + (int)(v - (rb >> 2));
-                                z = reinterpret_cast<const float4*>(smz)[q];
-                                if constexpr (HL) zl = reinterpret_cast<const float4*>(sml)[q];
-                                av = reinterpret_cast<const float4*>(sma)[q];
-                            } else {
-                                z = LD4L2(zsrc, v);
-                                if constexpr (HL) zl = LD4L2(a.zlo, v);
-                                av = LD4L2(a.A, v);
-                            }
-                            e(z.x, zl.x, av.x);
-                            e(z.y, zl.y, av.y);
-                            e(z.z, zl.z, av.z);
-                            e(z.w, zl.w, av.w);
-                            acc.tick();
-                        },
-                        [&](int64_t i) {
-                            if constexpr (R) {
-                                const int q = off + (int)(i - rb);
-                                e(smz[q], HL ? sml[q] : 0.0f, sma[q]);
-                            } else {
-                                e(zsrc[i], HL ? a.zlo[i] : 0.0f, a.A[i]);
-                            }
-                            acc.tick();
-                        });
+                                P4 d{reinterpret_cast<const float4*>(smz)[q], make_float4(0.f, 0.f, 0.f, 0.f),
+                                     reinterpret_cast<const float4*>(sma)[q]};
+                                if constexpr (HL) d.zl = reinterpret_cast<const float4*>(sml)[q];
+                                use4(d);
+                            },
+                            use1);
+                    } else {
+                        for_chunk_x2<VEC>(
+                            cb, ce,
+                            [&](int64_t v) {
+                                return P4{LD4L2(zsrc, v), HL ? LD4L2(a.zlo, v) : make_float4(0.f, 0.f, 0.f, 0.f),
+                                          LD4L2(a.A, v)};
+                            },
+                            use4, use1);
+                    }
                 };
                 if (res) {
                     if (has_lo) run(BoolC<true>{}, BoolC<true>{});
@@ -862,12 +916,24 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                     else run(BoolC<false>{}, BoolC<false>{});
                 }
                 acc.fold();
-                block_reduce<2 * K, 0>(acc.d, nullptr, sc, (lad ? 5 * nr : 0) + 2 * K * j, 0);
+                // two gathers of 16 and 3 values: one of 19 would round up to 32 per lane
+                DF v[2 * K], u[3];
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    v[k] = acc.d[k];
+                    v[K + k] = acc.d[K + 3 + k];
+                }
+                u[0] = acc.d[K];
+                u[1] = acc.d[K + 1];
+                u[2] = acc.d[K + 2];
+                const int voff = (lad ? 5 * nr : 0) + (2 * K + 3) * j;
+                block_reduce<2 * K, 0>(v, nullptr, sc, voff, 0);
+                block_reduce<3, 0>(u, nullptr, sc, voff + 2 * K, 0);
             }
             if (lad) {
                 // phase B's update, then the ladder pass's: rows that search and had no
                 // usable previous root keep the first points update_after_trial gave them
-                if (!sy.reduce(sc, (5 + 2 * K) * nr, 2 * nr, [&](BlockScratch& s, SegState* st) {
+                if (!sy.reduce(sc, (5 + 2 * K + 3) * nr, 3 * nr, [&](BlockScratch& s, SegState* st) {
                         update_after_trial(a, s, st, true);
                         __syncwarp();
                         volatile SegBcast* vb = &st->bc;
@@ -885,7 +951,8 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
 #pragma unroll
                         for (int r = 0; r < kMaxRows; ++r) held |= ((hb >> (8 * r)) & 1u) << r;
                         __syncwarp();
-                        search_pass_update<SegBcast, false>(s, 5 * nr, vr, vb, nr, a.tol_lambda, a.max_passes, held);
+                        search_pass_update<SegBcast, false, true>(s, 5 * nr, vr, vb, nr, a.tol_lambda, a.max_passes,
+                                                                  held);
                     }))
                     return;
                 sy.fetch(bc);
@@ -898,14 +965,14 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 lad = false;
                 continue;
             }
-            if (!sy.reduce(sc, 2 * K * a.nrows, 0, [&](BlockScratch& s, SegState* st) {
+            if (!sy.reduce(sc, (2 * K + 3) * a.nrows, 0, [&](BlockScratch& s, SegState* st) {
                     // every element of each active row was visited
                     if (threadIdx.x < a.nrows && st->bc.active[threadIdx.x])
                         st->rows[threadIdx.x].visited =
                             st->rows[threadIdx.x].visited + (double)(a.seg[threadIdx.x + 1] - a.seg[threadIdx.x]);
                     __syncwarp();
-                    search_pass_update<SegBcast, false>(s, 0, st->rows, &st->bc, a.nrows, a.tol_lambda,
-                                                        a.max_passes);
+                    search_pass_update<SegBcast, false, true>(s, 0, st->rows, &st->bc, a.nrows, a.tol_lambda,
+                                                              a.max_passes);
                 }))
                 return;
             sy.fetch(bc);
@@ -989,26 +1056,35 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                         a.x_out[i] = res ? e(0.0f, smz[q], 0.0f, sma[q]) : e(0.0f, a.z_in[i], 0.0f, a.A[i]);
                     });
             } else {
-                for_chunk<VEC>(
+                struct D4 {
+                    int64_t v;
+                    float4 x, zh, zl, av;
+                };
+                for_chunk_x2<VEC>(
                     cb, ce,
                     [&](int64_t v) {
-                        float4 x = LD4L2(a.x_prev, v), zh, zl, av;
+                        D4 q;
+                        q.v = v;
+                        q.x = LD4L2(a.x_prev, v);
                         if (res) {
-                            const int q = (off >> 2) + (int)(v - (rb >> 2));
-                            zh = reinterpret_cast<const float4*>(smz)[q];
-                            zl = reinterpret_cast<const float4*>(sml)[q];
-                            av = reinterpret_cast<const float4*>(sma)[q];
+                            const int k = (off >> 2) + (int)(v - (rb >> 2));
+                            q.zh = reinterpret_cast<const float4*>(smz)[k];
+                            q.zl = reinterpret_cast<const float4*>(sml)[k];
+                            q.av = reinterpret_cast<const float4*>(sma)[k];
                         } else {
-                            zh = LD4(a.z, v);
-                            zl = LD4(a.zlo, v);
-                            av = LD4(a.A, v);
+                            q.zh = LD4(a.z, v);
+                            q.zl = LD4(a.zlo, v);
+                            q.av = LD4(a.A, v);
                         }
+                        return q;
+                    },
+                    [&](const D4& q) {
                         float4 o;
-                        o.x = e(x.x, zh.x, zl.x, av.x);
-                        o.y = e(x.y, zh.y, zl.y, av.y);
-                        o.z = e(x.z, zh.z, zl.z, av.z);
-                        o.w = e(x.w, zh.w, zl.w, av.w);
-                        reinterpret_cast<float4*>(a.x)[v] = o;
+                        o.x = e(q.x.x, q.zh.x, q.zl.x, q.av.x);
+                        o.y = e(q.x.y, q.zh.y, q.zl.y, q.av.y);
+                        o.z = e(q.x.z, q.zh.z, q.zl.z, q.av.z);
+                        o.w = e(q.x.w, q.zh.w, q.zl.w, q.av.w);
+                        reinterpret_cast<float4*>(a.x)[q.v] = o;
                         if (++cnt == kFoldEvery) {
                             fold();
                             cnt = 0;

@@ -27,6 +27,7 @@ struct RowState {
     // (FP64 issues at a small fraction of the FP32 rate here and sits on the critical path)
     float b_hi, b_lo, fL, fH, rL_hi, rL_lo, rH_hi, rH_lo, fSL, fSH, freg;
     float lam_hi, lam_lo;  // lam as a float pair
+    float famax;           // max |a| over the row (single/independent rows; 0 where not set)
 };
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
@@ -216,13 +217,18 @@ __device__ __forceinline__ float next_point_warm_f(int lane, float L, float H, f
     const float w = H - L;
     const float am = fabsf(L), bm = fabsf(H);
     float v;
-    if (k == 0) v = NL;
+    if (!warm && (L * H <= 0.0f || fmaxf(am, bm) > 4.0f * fminf(am, bm))) {
+        // a cold start's bracket runs from 0 to a saturation bound, often tens of times the
+        // root, so Newton from its far end and the secant are wasted: all eight points go on a
+        // ladder around the Newton estimate from the zero end, dense near it (the estimate
+        // is usually within a few tens of percent) with far points in case it is not
+        const float base = (L == 0.0f && NL > L && NL < H) ? NL : (H == 0.0f && NH > L && NH < H) ? NH : sec;
+        v = base * (k == 0 ? 0.125f : k == 1 ? 0.5f : k == 2 ? 0.8f : k == 3 ? 1.0f : k == 4 ? 1.2f
+                    : k == 5 ? 1.45f : k == 6 ? 2.0f : 4.0f);
+    } else if (k == 0) v = NL;
     else if (k == 1) v = NH;
     else if (k == 2) v = sec;
-    else if (!warm && (L * H <= 0.0f || fmaxf(am, bm) > 4.0f * fminf(am, bm))) {
-        const float base = (L == 0.0f && NL > L && NL < H) ? NL : (H == 0.0f && NH > L && NH < H) ? NH : sec;
-        v = base * (k == 3 ? 0.125f : k == 4 ? 0.25f : k == 5 ? 0.5f : k == 6 ? 2.0f : 4.0f);
-    } else if (!warm) v = fmaf(w, (float)(k - 2) * (1.0f / 6.0f), L);
+    else if (!warm) v = fmaf(w, (float)(k - 2) * (1.0f / 6.0f), L);
     else if (k == 3) v = fmaf(0.5f, w, L);
     else v = lp * (k == 4 ? 0.97f : k == 5 ? 0.997f : k == 6 ? 1.003f : 1.03f);
     if (!(v > L && v < H)) v = fmaf(w, ((float)k + 0.5f) * 0.125f, L);
@@ -273,6 +279,7 @@ __device__ __forceinline__ void store_row(volatile RowState* r, double b, double
     r->fSL = (float)SL;
     r->fSH = (float)SH;
     r->freg = (float)r->reg;
+    r->famax = 0.0f;
 }
 
 // Refresh the float / double-float copy of a bracket whose FP64 fields were set directly.
@@ -346,6 +353,7 @@ __device__ __forceinline__ void store_row_df(volatile RowState* r, DF b, float L
     r->fSL = SL.hi;
     r->fSH = SH.hi;
     r->freg = freg;
+    r->famax = 0.0f;
 }
 
 
@@ -363,21 +371,76 @@ __device__ __forceinline__ float float_ulp_f(float v) {
     return nextafterf(f, INFINITY) - f;
 }
 
+// v moved by k float spacings towards +infinity (v finite and non-zero; the caller keeps
+// the result inside the bracket).
+__device__ __forceinline__ float float_steps(float v, int k) {
+    return __int_as_float(__float_as_int(v) + (v > 0.0f ? k : -k));
+}
+
+// Root in (L, H) of the cubic Hermite interpolant of r on the bracket: values rL > 0 >= rH
+// and slopes -SL, -SH at its ends.  A safeguarded Newton iteration on the cubic in
+// t = (lam - L) / (H - L), started at the secant point, keeping the sign bracket in t.
+__device__ __forceinline__ float hermite_root(float L, float H, float rL, float rH, float SL, float SH) {
+    const float w = H - L;
+    const float dL = -SL * w, dH = -SH * w;
+    const float c1 = dL;
+    const float c2 = 3.0f * (rH - rL) - 2.0f * dL - dH;
+    const float c3 = 2.0f * (rL - rH) + dL + dH;
+    float tl = 0.0f, th = 1.0f;
+    float t = __fdividef(rL, rL - rH);
+    if (!(t > 0.0f && t < 1.0f)) t = 0.5f;
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+        const float f = fmaf(fmaf(fmaf(c3, t, c2), t, c1), t, rL);
+        if (f > 0.0f) tl = t;
+        else th = t;
+        const float fp = fmaf(fmaf(3.0f * c3, t, 2.0f * c2), t, c1);
+        float tn = t - __fdividef(f, fp);
+        if (!(tn > tl && tn < th)) tn = 0.5f * (tl + th);
+        t = tn;
+    }
+    return fmaf(t, w, L);
+}
+
 // Trial point k of the next pass inside (L, H), float version of next_point.
-__device__ __forceinline__ float next_point_f(int lane, float L, float rL, float H, float rH, float NL, float NH) {
+//  * Once the Newton predictions from both ends lie inside the bracket and agree to a few
+//    float spacings, the root is located as finely as FP32 trial points can express it:
+//    the points are the floats around the prediction (-4, -2, -1, 0, +1, +2, +4, +8
+//    spacings), so the bracket closes on two neighbouring floats in one pass.
+//  * A bracket that contains 0 or spans more than a factor of 4 keeps the geometric
+//    ladder around the Newton estimate from its zero end (the secant otherwise).
+//  * Otherwise: Newton from both ends, the secant, the root e of the cubic Hermite
+//    interpolant of the bracket (values and slopes at both ends: far more accurate than
+//    either Newton step on a smooth stretch of r), and e -+ d, e -+ d/4 with d the largest
+//    distance from e to the other estimates, so the points cluster where the root is.
+__device__ __forceinline__ float next_point_f(int lane, float L, float rL, float H, float rH, float NL, float NH,
+                                              float SL, float SH) {
     const int k = lane & 7;
     const float w = H - L;
     const float am = fabsf(L), bm = fabsf(H);
+    const float ulp = float_ulp_f(fmaxf(am, bm));
+    const bool inL = NL > L && NL < H, inH = NH > L && NH < H;
+    const bool tight = inL && inH && fabsf(NL - NH) <= 16.0f * ulp;
+    const float sec = L + rL * __fdiv_rn(w, rL - rH);
     float v;
-    if (k == 0) v = NL;
+    if (tight) {
+        const float e = 0.5f * NL + 0.5f * NH;
+        v = e == 0.0f ? e : float_steps(e, k == 0 ? -4 : k == 1 ? -2 : k == 2 ? -1 : k == 3 ? 0 : k == 4 ? 1
+                                          : k == 5 ? 2 : k == 6 ? 4 : 8);
+    } else if (k == 0) v = NL;
     else if (k == 1) v = NH;
-    else if (k == 2) v = L + rL * __fdiv_rn(w, rL - rH);
+    else if (k == 2) v = sec;
     else if (L * H <= 0.0f || fmaxf(am, bm) > 4.0f * fminf(am, bm)) {
-        const float sec = L + rL * __fdiv_rn(w, rL - rH);
-        const float base = (L == 0.0f && NL > L && NL < H) ? NL : (H == 0.0f && NH > L && NH < H) ? NH : sec;
+        const float base = (L == 0.0f && inL) ? NL : (H == 0.0f && inH) ? NH : sec;
         v = base * (k == 3 ? 0.125f : k == 4 ? 0.25f : k == 5 ? 0.5f : k == 6 ? 2.0f : 4.0f);
     } else {
-        v = fmaf(w, (float)(k - 2) * (1.0f / 6.0f), L);
+        const float e = hermite_root(L, H, rL, rH, SL, SH);
+        const bool inS = sec > L && sec < H;
+        float d = ulp;
+        if (inL) d = fmaxf(d, fabsf(NL - e));
+        if (inH) d = fmaxf(d, fabsf(NH - e));
+        if (inS) d = fmaxf(d, fabsf(sec - e));
+        v = k == 3 ? e : k == 4 ? e - d : k == 5 ? e + d : k == 6 ? fmaf(-0.25f, d, e) : fmaf(0.25f, d, e);
     }
     if (!(v > L && v < H)) v = fmaf(w, ((float)k + 0.5f) * 0.125f, L);
     if (!(v > L && v < H)) {
@@ -398,10 +461,18 @@ __device__ __forceinline__ float next_point_f(int lane, float L, float rL, float
 // and the pass's three extra sums (the elements it decided) join that state.
 // Searches in `held` (bit j) were not evaluated in this pass: they keep their bracket and
 // points and stay active.
-template <class Bcast, bool CMP = false>
+// DEC: the pass summed per point only the elements whose clip state changes between the
+// lowest and the highest point; the others came as three sums at tot[base + stride j + 2K
+// ...]: C (a x bound over the elements clipped at every point), AZ (a w_m over those free
+// at every point, w_m their value at the reference point t_m = pts[j][kMidPoint]) and AA
+// (a^2 over the same), and each point adds C + AZ - (t_k - t_m) AA and AA back.
+constexpr int kMidPoint = 3;
+
+template <class Bcast, bool CMP = false, bool DEC = false>
 __device__ void search_pass_update(const BlockScratch& sc, int base, volatile RowState* rows, volatile Bcast* bc,
                                    int nsearch, double tol_lambda, int max_passes, unsigned held = 0u) {
-    constexpr int stride = CMP ? 2 * K + 4 : 2 * K;
+    static_assert(!(CMP && DEC), "one pass layout at a time");
+    constexpr int stride = CMP ? 2 * K + 4 : (DEC ? 2 * K + 3 : 2 * K);
     const int lane = threadIdx.x, j = lane >> 3, k = lane & 7, g0 = lane & ~7;
     const int jj = j < nsearch ? j : 0;
     const bool act = j < nsearch && rows[jj].active;
@@ -423,6 +494,14 @@ __device__ void search_pass_update(const BlockScratch& sc, int base, volatile Ro
         split_double(rows[jj].cC - (double)lk * rows[jj].cAA, ch, cl);
         rk = df_add(rk, DF{ch, cl});
         Sk += (float)rows[jj].cAA;
+    }
+    if (DEC) {
+        const int o = base + stride * jj + 2 * K;
+        const float tm = __shfl_sync(kFull, lk, g0 + kMidPoint);
+        const DF aa = sc.tot[o + 2];
+        const DF dec = df_add(df_add(sc.tot[o], sc.tot[o + 1]), df_neg(df_mul(two_sum(lk, -tm), aa)));
+        rk = df_add(rk, dec);
+        Sk += aa.hi;
     }
     // new lower end: the largest point with r > 0; new upper end: the smallest point above
     // it with r <= 0 (points the rounding noise puts out of order are ignored)
@@ -458,19 +537,26 @@ __device__ void search_pass_update(const BlockScratch& sc, int base, volatile Ro
     const DF gap = df_add(NL, df_neg(NH));
     const DF wd = two_sum(H, -L);
     const float w = wd.hi;
-    // tolerances relative to the bracket's magnitude (a negative bracket ends at 0)
+    // tolerances relative to the bracket's magnitude (a negative bracket ends at 0).  Where
+    // the row's largest |a| is known the search may also stop once the two Newton
+    // predictions agree to 100 tol_lambda of the root and to 1e-8 / max|a|: the final pass
+    // then takes one exact Newton step from their midpoint, which (at the default
+    // tol_lambda) moves x by less than 1e-7 and lam by less than 1e-7 of itself, so it needs
+    // no further pass (its own test runs it again if it does)
     const float mag = fmaxf(fabsf(L), fabsf(H));
     const float tol = (float)tol_lambda * mag;
+    const float am = rows[jj].famax;
+    const float tolg = am > 0.0f ? fmaxf(tol, fminf(100.0f * tol, __fdividef(1e-8f, am))) : tol;
     bool done = false;
     int how = 2;
     if (kH >= 0 && rH.hi == 0.0f && rH.lo == 0.0f) done = true;
-    else if (fabsf(gap.hi) <= tol || w <= tol || w <= 4.0f * float_ulp_f(mag)) done = true;
+    else if (fabsf(gap.hi) <= tolg || w <= tol || w <= 4.0f * float_ulp_f(mag)) done = true;
     if (!done && passes >= max_passes) {
         done = true;
         how = 3;  // not converged
     }
     done = done && row;
-    const float p = next_point_f(lane, L, rL.hi, H, rH.hi, NL.hi, NH.hi);
+    const float p = next_point_f(lane, L, rL.hi, H, rH.hi, NL.hi, NH.hi, SL, SH);
     if (row && k == 0) {
         volatile RowState* r = &rows[j];
         r->fL = L;
@@ -602,6 +688,33 @@ __device__ __forceinline__ void for_chunk(int64_t cb, int64_t ce, F4&& f4, F1&& 
         if (ve < vb) ve = vb;
         for (int64_t i = cb + threadIdx.x; i < vb; i += blockDim.x) f1(i);
         for (int64_t v = (vb >> 2) + threadIdx.x; v < (ve >> 2); v += blockDim.x) f4(v);
+        for (int64_t i = ve + threadIdx.x; i < ce; i += blockDim.x) f1(i);
+    } else {
+        for (int64_t i = cb + threadIdx.x; i < ce; i += blockDim.x) f1(i);
+    }
+}
+
+// for_chunk with two float4 groups per iteration: load4(v) issues a group's loads and
+// returns them, use4(data) consumes them (and ticks).  Both groups' loads are in flight
+// before either is used, which hides more of the memory latency of a streaming pass.
+// The groups are consumed in the same order as for_chunk's, so the sums are the same bits.
+template <bool VEC, class L4, class U4, class F1>
+__device__ __forceinline__ void for_chunk_x2(int64_t cb, int64_t ce, L4&& load4, U4&& use4, F1&& f1) {
+    if (VEC) {
+        int64_t vb = (cb + 3) & ~int64_t(3);
+        if (vb > ce) vb = ce;
+        int64_t ve = ce & ~int64_t(3);
+        if (ve < vb) ve = vb;
+        for (int64_t i = cb + threadIdx.x; i < vb; i += blockDim.x) f1(i);
+        const int64_t st = blockDim.x, v1 = ve >> 2;
+        int64_t v = (vb >> 2) + threadIdx.x;
+        for (; v + st < v1; v += 2 * st) {
+            auto d0 = load4(v);
+            auto d1 = load4(v + st);
+            use4(d0);
+            use4(d1);
+        }
+        if (v < v1) use4(load4(v));
         for (int64_t i = ve + threadIdx.x; i < ce; i += blockDim.x) f1(i);
     } else {
         for (int64_t i = cb + threadIdx.x; i < ce; i += blockDim.x) f1(i);

@@ -1,7 +1,8 @@
 """Free-set compaction (Sec. 4.2.1, params.compaction = 1) against the oracle on problems
 whose CTA shares stream from global memory (where it applies): single rows, an equality
-row on a negative bracket, the four-material step, and the 524,288-variable step; it
-visits fewer elements than the plain search and gives the same answer to the tolerance."""
+row on a negative bracket, the four-material step, and the 524,288-variable step; its lists
+are used (a pass visits only part of the elements) and it gives the same answer to the
+tolerance."""
 
 import numpy as np
 import pytest
@@ -60,6 +61,8 @@ def test_compacted_projection(dev, n, seed, eq):
     xr = np.clip(z64 - lr * a64, 0, 1)
     lam, x, vis = out[1]
     check(parity_errors(x, lam, xr, [lr], a[None, :], [b], C, 0.0, 1.0, eq=[eq]), "n=%d" % n)
+    # the lists were in use: a later pass visited only part of the row, fewer in all
+    assert vis % n != 0, vis
     assert vis < out[0][2], (vis, out[0][2])
 
 
@@ -89,7 +92,7 @@ def test_compacted_four_material_step(dev):
     info, x = infos[1]
     check(parity_errors(x, np.array(list(info.lambda_)[:4]), ref["x_new"], ref["lam"], f, ref["b"], C, 0.0, 1.0,
                         amax=np.ones(4)), "four materials")
-    assert info.visited < infos[0][0].visited
+    assert info.visited < infos[0][0].visited, (info.visited, infos[0][0].visited)
 
 
 def test_compacted_single_cta_step_config2(dev):
