@@ -58,37 +58,8 @@ struct SegArgs {
     int* ccnt;            // their lengths, per CTA, row and thread
 };
 
-// Free-set compaction lists.  Every thread keeps the elements of its own share that a
-// root search has not yet decided, entry q of thread t of a row at q * nthr + t (coalesced
-// when all threads read entry q), so appending needs no scan and the order is fixed.  A
-// thread visits at most seg_list_cap elements of a chunk in one sweep (float4 groups with
-// stride nthr, plus one element of the unaligned head and one of the tail).  The layout
-// uses the first CTA's chunk (the longest) for every CTA.
-__host__ __device__ inline int seg_list_cap(int64_t len, int nthr) {
-    const int64_t ng = len / 4 + 1;
-    return (int)(4 * ((ng + nthr - 1) / nthr) + 2);
-}
-
-__host__ __device__ inline int64_t seg_list_row_off(const int64_t* seg, int j, int nb, int nthr) {
-    int64_t off = 0;
-    for (int k = 0; k < j; ++k) {
-        const int64_t len = seg[k + 1] - seg[k];
-        const int64_t per = ((len + nb - 1) / nb + 3) & ~int64_t(3);
-        off += (int64_t)nthr * seg_list_cap(per < 4 ? 4 : per, nthr);
-    }
-    return off;
-}
-
-// Ints of one CTA's lists (every row).
-__host__ __device__ inline int64_t seg_list_cta(const int64_t* seg, int nrows, int nb, int nthr) {
-    return seg_list_row_off(seg, nrows, nb, nthr);
-}
-
-// Shared-memory residency of a CTA's share of a problem.  The CTA's chunk of row j is
-// [cb_j, ce_j) (block_chunk); it is kept from base_j = cb_j rounded down to a multiple of
-// four, at a float4-aligned offset, rows one after another.  seg_res_need is the number
-// of floats per array the CTA needs; the host sizes the launch's dynamic shared memory
-// with the same function the device uses to decide.
+// Work split of a problem over nb blocks.  seg_chunk(s, e, blk, nb) is block blk's
+// contiguous share of [s, e), a multiple of four long (the last one shorter or empty).
 __host__ __device__ inline void seg_chunk(int64_t s, int64_t e, int blk, int nb, int64_t& cb, int64_t& ce) {
     int64_t len = e - s;
     int64_t per = (len + nb - 1) / nb;
@@ -100,7 +71,49 @@ __host__ __device__ inline void seg_chunk(int64_t s, int64_t e, int blk, int nb,
     if (ce > e) ce = e;
 }
 
+// Block blk's share of row j: the block owns the chunk seg_chunk(0, n) of the whole array
+// and takes the part of it that lies in the row's segment [seg[j], seg[j + 1]).  With
+// several rows most of a block's shares are empty: a block's passes run over one or two
+// rows' elements in long loops rather than over a short piece of every row.
+__host__ __device__ inline void seg_row_chunk(const int64_t* seg, int nrows, int j, int blk, int nb, int64_t& cb,
+                                              int64_t& ce) {
+    int64_t gb, ge;
+    seg_chunk(seg[0], seg[nrows], blk, nb, gb, ge);
+    cb = gb > seg[j] ? gb : seg[j];
+    ce = ge < seg[j + 1] ? ge : seg[j + 1];
+    if (ce < cb) ce = cb;
+}
+
+// Free-set compaction lists.  Every thread keeps the elements of its own share that a
+// root search has not yet decided, entry q of thread t of a row at q * nthr + t (coalesced
+// when all threads read entry q), so appending needs no scan and the order is fixed.  A
+// thread visits at most seg_list_cap elements of a share in one sweep (float4 groups with
+// stride nthr, plus one element of the unaligned head and one of the tail).  Every row of
+// every block gets room for the longest block chunk.
+__host__ __device__ inline int seg_list_cap(int64_t len, int nthr) {
+    const int64_t ng = len / 4 + 1;
+    return (int)(4 * ((ng + nthr - 1) / nthr) + 2);
+}
+
+__host__ __device__ inline int64_t seg_list_row_off(const int64_t* seg, int nrows, int j, int nb, int nthr) {
+    int64_t gb, ge;
+    seg_chunk(seg[0], seg[nrows], 0, nb, gb, ge);
+    const int64_t per = ge - gb;
+    return (int64_t)j * nthr * seg_list_cap(per < 4 ? 4 : per, nthr);
+}
+
+// Ints of one CTA's lists (every row).
+__host__ __device__ inline int64_t seg_list_cta(const int64_t* seg, int nrows, int nb, int nthr) {
+    return seg_list_row_off(seg, nrows, nrows, nb, nthr);
+}
+
+// Shared-memory residency of a CTA's share of a problem.  The CTA's share of row j is
+// [cb_j, ce_j) (seg_row_chunk); a non-empty one is kept from base_j = cb_j rounded down to
+// a multiple of four, at a float4-aligned offset, rows one after another.  seg_res_need
+// is the number of floats per array the CTA needs; the host sizes the launch's dynamic
+// shared memory with the same function the device uses to decide.
 __host__ __device__ inline int seg_res_span(int64_t cb, int64_t ce) {
+    if (ce <= cb) return 0;
     const int64_t b4 = cb & ~int64_t(3);
     return (int)(((ce - b4) + 3) & ~int64_t(3));
 }
@@ -109,7 +122,7 @@ __host__ __device__ inline int seg_res_need(const int64_t* seg, int nrows, int b
     int tot = 0;
     for (int j = 0; j < nrows; ++j) {
         int64_t cb, ce;
-        seg_chunk(seg[j], seg[j + 1], blk, nb, cb, ce);
+        seg_row_chunk(seg, nrows, j, blk, nb, cb, ce);
         tot += seg_res_span(cb, ce);
     }
     return tot;

@@ -366,6 +366,12 @@ template <bool VEC, bool CMP, class Sync>
 __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, SegBcast& bc, float* sm) {
     const int nb = sy.size(), blk = sy.rank();
     const float lo = a.lo, hi = a.hi;
+    // A block whose share of a row is empty (seg_row_chunk) contributes zeros to that row's
+    // sums; the row loops end with a barrier before the grid reduction reads them.
+    auto zero_tot = [&](int voff, int nv, int moff, int nm) {
+        for (int i = threadIdx.x; i < nv; i += blockDim.x) sc.tot[voff + i] = df_zero();
+        for (int i = threadIdx.x; i < nm; i += blockDim.x) sc.totmax[moff + i] = 0.0f;
+    };
 
     if (!a.proj) {
         // ------------------------------------------------------------ phase A
@@ -457,7 +463,11 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
             float lsat = 0.0f, lnegm = 0.0f, amx = 0.0f;
             const bool eqj = (a.eq_mask >> j) & 1;
             int64_t cb, ce;
-            block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
+            seg_row_chunk(a.seg, a.nrows, j, blk, nb, cb, ce);
+            if (ce <= cb) {
+                zero_tot(5 * j, 5, 3 * j, 3);
+                continue;
+            }
             const int64_t rb = cb & ~int64_t(3);
             const int off = roff;
             roff += seg_res_span(cb, ce);
@@ -595,6 +605,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
             float mx[3] = {lsat, lnegm, amx};
             block_reduce<5, 3>(acc.d, mx, sc, 5 * j, 3 * j);
         }
+        __syncthreads();
         if (!ladder) {
             if (!sy.reduce(sc, 5 * a.nrows, 3 * a.nrows,
                            [&](BlockScratch& s, SegState* st) { update_after_trial(a, s, st); }))
@@ -628,17 +639,23 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
             int roff = 0;
             for (int j = 0; j < a.nrows; ++j) {
                 int64_t cb, ce;
-                block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
+                seg_row_chunk(a.seg, a.nrows, j, blk, nb, cb, ce);
                 const int64_t rb = cb & ~int64_t(3);
                 const int off = roff;
                 roff += seg_res_span(cb, ce);
                 if (!bc.active[j]) continue;
+                if (ce <= cb) {
+                    if (cmp && bc.cmode[j] != 0) a.ccnt[((int64_t)blk * kMaxRows + j) * nthr + tid] = 0;
+                    zero_tot((2 * K + 4) * j, 2 * K + 4, 0, 0);
+                    continue;
+                }
                 float p[K];
     #pragma unroll
                 for (int k = 0; k < K; ++k) p[k] = bc.pts[j][k];
                 const int mode = cmp ? bc.cmode[j] : 0;
                 const float bl = bc.brL[j], bu = bc.brH[j];
-                int* lst = cmp ? a.cidx + (int64_t)blk * lstride + seg_list_row_off(a.seg, j, nb, nthr) : nullptr;
+                int* lst = cmp ? a.cidx + (int64_t)blk * lstride + seg_list_row_off(a.seg, a.nrows, j, nb, nthr)
+                               : nullptr;
                 int* cntp = cmp ? a.ccnt + ((int64_t)blk * kMaxRows + j) * nthr + tid : nullptr;
                 int nkeep = 0;
                 // acc.f[0, K): r sums at the points; [K, K + 3): the elements this pass decides
@@ -774,6 +791,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 v[2 * K + 3] = DF{(float)nvis, 0.0f};
                 block_reduce<2 * K + 4, 0>(v, nullptr, sc, (2 * K + 4) * j, 0);
             }
+            __syncthreads();
             if (!sy.reduce(sc, (2 * K + 4) * a.nrows, 0, [&](BlockScratch& s, SegState* st) {
                     search_pass_update<SegBcast, true>(s, 0, st->rows, &st->bc, a.nrows, a.tol_lambda, a.max_passes);
                     __syncwarp();
@@ -808,7 +826,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
             int roff = 0;
             for (int j = 0; j < nr; ++j) {
                 int64_t cb, ce;
-                block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
+                seg_row_chunk(a.seg, a.nrows, j, blk, nb, cb, ce);
                 const int64_t rb = cb & ~int64_t(3);
                 const int off = roff;
                 roff += seg_res_span(cb, ce);
@@ -822,6 +840,10 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                     if (!bc.active[j]) continue;
 #pragma unroll
                     for (int k = 0; k < K; ++k) p[k] = bc.pts[j][k];
+                }
+                if (ce <= cb) {
+                    zero_tot((lad ? 5 * nr : 0) + (2 * K + 3) * j, 2 * K + 3, 0, 0);
+                    continue;
                 }
                 // acc.f[0, K): r sums at the points of the elements whose clip state changes
                 // between the lowest and the highest point; [K, K + 3): the other elements as
@@ -930,6 +952,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 block_reduce<2 * K, 0>(v, nullptr, sc, voff, 0);
                 block_reduce<3, 0>(u, nullptr, sc, voff + 2 * K, 0);
             }
+            __syncthreads();
             if (lad) {
                 // phase B's update, then the ladder pass's: rows that search and had no
                 // usable previous root keep the first points update_after_trial gave them
@@ -993,7 +1016,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
         for (int j = 0; j < a.nrows; ++j) {
             const float lh = bc.lam_hi[j], ll = bc.lam_lo[j];
             int64_t cb, ce;
-            block_chunk(a.seg[j], a.seg[j + 1], blk, nb, cb, ce);
+            seg_row_chunk(a.seg, a.nrows, j, blk, nb, cb, ce);
             const int64_t rb = cb & ~int64_t(3);
             const int off = roff;
             roff += seg_res_span(cb, ce);
