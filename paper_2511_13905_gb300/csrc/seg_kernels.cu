@@ -31,6 +31,11 @@ namespace cg = cooperative_groups;
 
 namespace pgdto {
 
+// Values per row in the trial-point pass's reduction: a^T x_t, r(0) + b, the free-set
+// curvature at 0, the sums of a times the row-minimising and row-maximising bounds, and
+// sum |a z_lo| (how far the FP32 trial point z_hi alone moves a row sum).
+constexpr int kBVals = 6;
+
 struct SegBcast {
     float c_hi, c_lo, beta_hi, beta_lo;  // step scalars c = omega alpha and beta as float pairs
     int branch, any_active, status, refine;  // refine: phase D runs again at the refined lam
@@ -91,9 +96,10 @@ __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, Seg
     const bool row = j < a.nrows;
     const int jj = row ? j : 0;
     const DF two_c = DF{a.two_c_df[0], a.two_c_df[1]};
-    const DF ax = a.proj ? df_zero() : sc.tot[5 * jj + 0];
-    const DF r0s = sc.tot[5 * jj + 1], sf = sc.tot[5 * jj + 2];
-    const DF smin = sc.tot[5 * jj + 3], smax = sc.tot[5 * jj + 4];
+    const DF ax = a.proj ? df_zero() : sc.tot[kBVals * jj + 0];
+    const DF r0s = sc.tot[kBVals * jj + 1], sf = sc.tot[kBVals * jj + 2];
+    const DF smin = sc.tot[kBVals * jj + 3], smax = sc.tot[kBVals * jj + 4];
+    const float zla = sc.tot[kBVals * jj + 5].hi;
     const float lsat = sc.totmax[3 * jj];
     const float lneg = -sc.totmax[3 * jj + 1];
     const float amax = sc.totmax[3 * jj + 2];
@@ -150,6 +156,7 @@ __device__ void update_after_trial(const SegArgs& a, const BlockScratch& sc, Seg
         if (search) {
             store_row_df(&rows[j], b, L, rL, SLs, H, rH, SHs, df_zero(), 0.0, two_c.hi, 1, 2);
             rows[j].famax = amax;
+            rows[j].fzla = zla;
             bc->active[j] = 1;
             bc->cmode[j] = 0;
             bc->brL[j] = L;
@@ -215,7 +222,10 @@ __device__ void update_final(const SegArgs& a, const BlockScratch& sc, SegState*
         const DF dl = spos ? q : df_zero();
         const float w = rows[j].fH - rows[j].fL;
         const float adl = fabsf(dl.hi);
-        const bool near = adl <= 4.0f * w || (spos && adl * S.hi <= 1e-6f * (fabsf(bj.hi) + fabsf(ax.hi)));
+        // the search may have run on z_hi alone (shares streaming from global memory), whose
+        // root is off by up to sum |a z_lo| over the slope: such a correction is taken too
+        const bool near = adl <= 4.0f * w ||
+                          (spos && adl * S.hi <= 1e-6f * (fabsf(bj.hi) + fabsf(ax.hi)) + 2.0f * rows[j].fzla);
         const DF ln = df_add(lam, dl);
         if (near && (df_pos(ln) || eqj)) {
             lam = ln;
@@ -458,14 +468,17 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
         const bool first = a.t == 0;
         int roff = 0;
         for (int j = 0; j < a.nrows; ++j) {
-            AccSplit<5, 0> acc;
+            // acc: free-set curvature at 0, sum a * (row-minimising bound), sum a * (row-
+            // maximising bound), sum |a z_lo|; the sums that enter b and r(0) are the TwoSum
+            // pairs below
+            AccSplit<0, 4, 1, 4> acc;
             acc.init();
             float lsat = 0.0f, lnegm = 0.0f, amx = 0.0f;
             const bool eqj = (a.eq_mask >> j) & 1;
             int64_t cb, ce;
             seg_row_chunk(a.seg, a.nrows, j, blk, nb, cb, ce);
             if (ce <= cb) {
-                zero_tot(5 * j, 5, 3 * j, 3);
+                zero_tot(kBVals * j, kBVals, 3 * j, 3);
                 continue;
             }
             const int64_t rb = cb & ~int64_t(3);
@@ -486,9 +499,10 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 const DF u = two_sum(r0h, q);
                 r0h = u.hi;
                 r0l = __fadd_rn(r0l, __fadd_rn(u.lo, fmaf(av, xc, -q) + (fr ? av * zl : 0.0f)));
-                acc.f[2] = fr ? fmaf(av, av, acc.f[2]) : acc.f[2];
-                acc.f[3] += av > 0.0f ? av * lo : (av < 0.0f ? av * hi : 0.0f);
-                acc.f[4] += av > 0.0f ? av * hi : (av < 0.0f ? av * lo : 0.0f);
+                acc.f[0] = fr ? fmaf(av, av, acc.f[0]) : acc.f[0];
+                acc.f[1] += av > 0.0f ? av * lo : (av < 0.0f ? av * hi : 0.0f);
+                acc.f[2] += av > 0.0f ? av * hi : (av < 0.0f ? av * lo : 0.0f);
+                acc.f[3] = fmaf(fabsf(av), fabsf(zl), acc.f[3]);
                 amx = fmaxf(amx, fabsf(av));
                 if (av != 0.0f) {
                     // saturation bounds: only used widened by 1e-5, so a fast division will do
@@ -600,14 +614,14 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                     });
             }
             acc.fold();
-            acc.d[0] = df_add(acc.d[0], fast_two_sum(axh, axl));
-            acc.d[1] = df_add(acc.d[1], fast_two_sum(r0h, r0l));
+            const DF v[kBVals] = {fast_two_sum(axh, axl), fast_two_sum(r0h, r0l), acc.d[0], acc.d[1], acc.d[2],
+                                  acc.d[3]};
             float mx[3] = {lsat, lnegm, amx};
-            block_reduce<5, 3>(acc.d, mx, sc, 5 * j, 3 * j);
+            block_reduce<kBVals, 3>(v, mx, sc, kBVals * j, 3 * j);
         }
         __syncthreads();
         if (!ladder) {
-            if (!sy.reduce(sc, 5 * a.nrows, 3 * a.nrows,
+            if (!sy.reduce(sc, kBVals * a.nrows, 3 * a.nrows,
                            [&](BlockScratch& s, SegState* st) { update_after_trial(a, s, st); }))
                 return;
             sy.fetch(bc);
@@ -842,7 +856,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                     for (int k = 0; k < K; ++k) p[k] = bc.pts[j][k];
                 }
                 if (ce <= cb) {
-                    zero_tot((lad ? 5 * nr : 0) + (2 * K + 3) * j, 2 * K + 3, 0, 0);
+                    zero_tot((lad ? kBVals * nr : 0) + (2 * K + 3) * j, 2 * K + 3, 0, 0);
                     continue;
                 }
                 // acc.f[0, K): r sums at the points of the elements whose clip state changes
@@ -930,12 +944,13 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                             use4, use1);
                     }
                 };
+                // a share streaming from global memory reads z_hi and a only (two thirds of the
+                // bytes); the final pass reads z_lo and corrects the root (update_final)
                 if (res) {
                     if (has_lo) run(BoolC<true>{}, BoolC<true>{});
                     else run(BoolC<true>{}, BoolC<false>{});
                 } else {
-                    if (has_lo) run(BoolC<false>{}, BoolC<true>{});
-                    else run(BoolC<false>{}, BoolC<false>{});
+                    run(BoolC<false>{}, BoolC<false>{});
                 }
                 acc.fold();
                 // two gathers of 16 and 3 values: one of 19 would round up to 32 per lane
@@ -948,7 +963,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 u[0] = acc.d[K];
                 u[1] = acc.d[K + 1];
                 u[2] = acc.d[K + 2];
-                const int voff = (lad ? 5 * nr : 0) + (2 * K + 3) * j;
+                const int voff = (lad ? kBVals * nr : 0) + (2 * K + 3) * j;
                 block_reduce<2 * K, 0>(v, nullptr, sc, voff, 0);
                 block_reduce<3, 0>(u, nullptr, sc, voff + 2 * K, 0);
             }
@@ -956,7 +971,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
             if (lad) {
                 // phase B's update, then the ladder pass's: rows that search and had no
                 // usable previous root keep the first points update_after_trial gave them
-                if (!sy.reduce(sc, (5 + 2 * K + 3) * nr, 3 * nr, [&](BlockScratch& s, SegState* st) {
+                if (!sy.reduce(sc, (kBVals + 2 * K + 3) * nr, 3 * nr, [&](BlockScratch& s, SegState* st) {
                         update_after_trial(a, s, st, true);
                         __syncwarp();
                         volatile SegBcast* vb = &st->bc;
@@ -974,7 +989,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
 #pragma unroll
                         for (int r = 0; r < kMaxRows; ++r) held |= ((hb >> (8 * r)) & 1u) << r;
                         __syncwarp();
-                        search_pass_update<SegBcast, false, true>(s, 5 * nr, vr, vb, nr, a.tol_lambda, a.max_passes,
+                        search_pass_update<SegBcast, false, true>(s, kBVals * nr, vr, vb, nr, a.tol_lambda, a.max_passes,
                                                                   held);
                     }))
                     return;

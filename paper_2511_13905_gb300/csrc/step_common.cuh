@@ -28,6 +28,7 @@ struct RowState {
     float b_hi, b_lo, fL, fH, rL_hi, rL_lo, rH_hi, rH_lo, fSL, fSH, freg;
     float lam_hi, lam_lo;  // lam as a float pair
     float famax;           // max |a| over the row (single/independent rows; 0 where not set)
+    float fzla;            // sum |a z_lo| over the row: the shift of a row sum without z_lo
 };
 
 __device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
@@ -280,6 +281,7 @@ __device__ __forceinline__ void store_row(volatile RowState* r, double b, double
     r->fSH = (float)SH;
     r->freg = (float)r->reg;
     r->famax = 0.0f;
+    r->fzla = 0.0f;
 }
 
 // Refresh the float / double-float copy of a bracket whose FP64 fields were set directly.
@@ -354,6 +356,7 @@ __device__ __forceinline__ void store_row_df(volatile RowState* r, DF b, float L
     r->fSH = SH.hi;
     r->freg = freg;
     r->famax = 0.0f;
+    r->fzla = 0.0f;
 }
 
 
