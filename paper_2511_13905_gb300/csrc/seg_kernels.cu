@@ -1024,9 +1024,15 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
     // lam by a Newton step on that residual and may ask for this pass again at the
     // refined lam (x_t is read from x_prev, so a repeated pass sees the same input).
     for (;;) {
-        AccSplit<2 * kMaxRows + 2, 0> acc;
-        acc.init();
+        // nrm: ||x_{t+1} - x_t||^2 and ||x_{t+1}||^2; the per-row sums are scalars of the row
+        // loop, kept per row by register selects (a runtime-indexed array would live in
+        // local memory)
+        AccSplit<2, 0> nrm;
+        nrm.init();
+        DF rsum[kMaxRows], rslope[kMaxRows];
         float amax_free[kMaxRows] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int q = 0; q < kMaxRows; ++q) rsum[q] = rslope[q] = df_zero();
         int roff = 0;
         for (int j = 0; j < a.nrows; ++j) {
             const float lh = bc.lam_hi[j], ll = bc.lam_lo[j];
@@ -1037,6 +1043,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
             roff += seg_res_span(cb, ce);
             float sh = 0.0f, sl = 0.0f, sfree = 0.0f;  // a^T x as hi (TwoSum) + lo; slope
             float amf = 0.0f;  // max |a| over the free set: how far a change of lam moves x
+            DF ra = df_zero(), rs = df_zero();
             int cnt = 0;
             auto e = [&](float x, float zh, float zl, float av) -> float {
                 const float p = lh * av;
@@ -1056,13 +1063,13 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 sfree = fr ? fmaf(av, av, sfree) : sfree;
                 amf = fr ? fmaxf(amf, fabsf(av)) : amf;
                 const float dx = xn - x;
-                acc.f[2 * kMaxRows] = fmaf(dx, dx, acc.f[2 * kMaxRows]);
-                acc.f[2 * kMaxRows + 1] = fmaf(xn, xn, acc.f[2 * kMaxRows + 1]);
+                nrm.f[0] = fmaf(dx, dx, nrm.f[0]);
+                nrm.f[1] = fmaf(xn, xn, nrm.f[1]);
                 return xn;
             };
             auto fold = [&]() {
-                acc.d[j] = df_add(acc.d[j], fast_two_sum(sh, sl));
-                acc.d[kMaxRows + j] = df_add_f(acc.d[kMaxRows + j], sfree);
+                ra = df_add(ra, fast_two_sum(sh, sl));
+                rs = df_add_f(rs, sfree);
                 sh = sl = sfree = 0.0f;
             };
             if (a.proj) {
@@ -1126,7 +1133,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                         if (++cnt == kFoldEvery) {
                             fold();
                             cnt = 0;
-                            acc.fold();
+                            nrm.fold();
                         }
                     },
                     [&](int64_t i) {
@@ -1138,20 +1145,28 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
             fold();
 #pragma unroll
             for (int q = 0; q < kMaxRows; ++q)
-                if (q == j) amax_free[q] = amf;  // register select, no indexed local array
+                if (q == j) {  // register selects
+                    amax_free[q] = amf;
+                    rsum[q] = ra;
+                    rslope[q] = rs;
+                }
         }
-        acc.fold();
+        nrm.fold();
         // pack: rows' a^T x, rows' slopes, then the two norms
         const int nr = a.nrows;
         DF packed[2 * kMaxRows + 2];
 #pragma unroll
-        for (int k = 0; k < 2 * kMaxRows + 2; ++k) packed[k] = df_zero();
-        for (int k = 0; k < nr; ++k) {
-            packed[k] = acc.d[k];
-            packed[nr + k] = acc.d[kMaxRows + k];
+        for (int k = 0; k < 2 * kMaxRows + 2; ++k) {
+            DF v = df_zero();
+#pragma unroll
+            for (int q = 0; q < kMaxRows; ++q) {
+                if (q < nr && k == q) v = rsum[q];
+                if (q < nr && k == nr + q) v = rslope[q];
+            }
+            if (k == 2 * nr) v = nrm.d[0];
+            if (k == 2 * nr + 1) v = nrm.d[1];
+            packed[k] = v;
         }
-        packed[2 * nr] = acc.d[2 * kMaxRows];
-        packed[2 * nr + 1] = acc.d[2 * kMaxRows + 1];
         const int nv = 2 * nr + (a.proj ? 0 : 2);
         block_reduce<2 * kMaxRows + 2, kMaxRows>(packed, amax_free, sc);
         if (!sy.reduce(sc, nv, nr, [&](BlockScratch& s, SegState* st) { update_final(a, s, st, sy.sticky(), sy.launches()); }))
