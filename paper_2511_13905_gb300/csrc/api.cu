@@ -451,6 +451,7 @@ static pgdto_status launch(pgdto_handle* h, bool proj, float* x, const float* g,
         for (int j = 0; j < h->m; ++j) a.bconst[j] = bconst[j];
         a.C = h->p.C;
         a.two_c = 2.0 / h->p.C;
+        split_to_floats(a.two_c, a.two_c_df);
         fill_step_df(h->p, a.step_df);
         a.alpha_max = h->p.alpha_max;
         a.alpha_fb = h->p.alpha_fallback;

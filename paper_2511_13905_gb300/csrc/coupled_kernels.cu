@@ -66,7 +66,14 @@ struct NewtonState {
     int stall;              // evaluations in a row without progress at the rounding floor
     int eq_mask;            // equality rows (always in the working set, never clamped or capped)
     int trial;              // lam is the full Newton step from base, not yet accepted
-    int pad;
+    // Float-pair copies written by the Newton update (phase E), which runs without FP64
+    // arithmetic; the doubles above (lam, d, base, base_*, phi) lag them while `stale` is
+    // set and are refreshed by nt_sync before the paths that read them.  The iterate and
+    // the direction themselves are bc.it_hi/it_lo and bc.d_hi/d_lo.
+    float base_h[kMaxRows], base_l[kMaxRows];
+    float fphi, fbase_phi;
+    float slope_h, slope_l, dtb_h, dtb_l, dd_h, dd_l;
+    int stale;
 };
 
 // Search state of one problem.  Every CTA keeps its own copy in shared memory and runs the
@@ -187,6 +194,9 @@ __device__ void cupd_after_trial(const CoupledArgs& a, const BlockScratch& sc, C
         nt->stall = 0;
         nt->trial = 0;
         nt->phi = INFINITY;
+        nt->fphi = INFINITY;
+        nt->fbase_phi = 0.0f;
+        nt->stale = 0;
         nt->tol = 1e-8;  // relative tolerance of the line search (the next Newton step corrects)
         nt->eq_mask = a.eq_mask;
     }
@@ -215,6 +225,22 @@ __device__ void cupd_plan_feasibility(CoupledState* ws) {
     } else {
         bc->mode = kModeFeas;
     }
+}
+
+// Refresh the FP64 Newton state from the float pairs the phase-E update left (thread 0).
+__device__ __forceinline__ void nt_sync(volatile NewtonState* nt, volatile CoupledBcast* bc, int m) {
+    if (!nt->stale) return;
+    for (int j = 0; j < m; ++j) {
+        nt->lam[j] = (double)bc->it_hi[j] + (double)bc->it_lo[j];
+        nt->d[j] = (double)bc->d_hi[j] + (double)bc->d_lo[j];
+        nt->base[j] = (double)nt->base_h[j] + (double)nt->base_l[j];
+    }
+    nt->phi = (double)nt->fphi;
+    nt->base_phi = (double)nt->fbase_phi;
+    nt->base_slope = (double)nt->slope_h + (double)nt->slope_l;
+    nt->base_dtb = (double)nt->dtb_h + (double)nt->dtb_l;
+    nt->base_dd = (double)nt->dd_h + (double)nt->dd_l;
+    nt->stale = 0;
 }
 
 __device__ __forceinline__ void set_iterate(volatile CoupledBcast* bc, volatile NewtonState* nt, int m) {
@@ -290,6 +316,7 @@ __device__ void cstart_line_search(CoupledState* ws) {
     volatile CoupledBcast* bc = &ws->bc;
     volatile NewtonState* nt = &ws->nt;
     volatile RowState* ls = &ws->ls;
+    nt_sync(nt, bc, M);
     for (int j = 0; j < M; ++j) nt->lam[j] = nt->base[j];
     set_iterate(bc, nt, M);
     double cap = INFINITY;  // the step at which an inequality multiplier reaches 0
@@ -330,128 +357,163 @@ __device__ void cstart_line_search(CoupledState* ws) {
 // KKT residual fell; otherwise the step is replaced by an exact line search from its base.
 // At an accepted point: KKT test, then the Newton direction on the working set and the
 // next full step max(lam + d, 0) as the new trial.
+// Phase E's update on warp 0, one row per lane, in double-float arithmetic on the FP32
+// pipes with no FP64 instruction: lane r < M forms h_r and its scale, holds row r of the
+// Jacobian during the elimination (the pivot row is broadcast by shuffles) and stores row
+// r's results as float pairs (the FP64 copies are refreshed later, nt_sync).  An FP64
+// one-thread version took about 29,000 cycles per call here and an FP64 one-lane-per-row
+// one about 9,000: an FP64 warp instruction costs many issue cycles on this part however
+// few lanes are active.
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ DF shfl_df(DF v, int src) {
+    return DF{__shfl_sync(kFull, v.hi, src), __shfl_sync(kFull, v.lo, src)};
+}
+
 template <int M>
 __device__ void cupd_after_eval(const CoupledArgs& a, const BlockScratch& sc, CoupledState* ws) {
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x;
     volatile CoupledBcast* bc = &ws->bc;
     volatile RowState* rows = ws->rows;
     volatile NewtonState* nt = &ws->nt;
-    const double two_c = a.two_c;
-    double h[M], scale[M];
-    bool conv = true;
-    for (int j = 0; j < M; ++j) {
-        h[j] = df_to_double(sc.tot[j]) - rows[j].b - two_c * nt->lam[j];
-        scale[j] = fmax(1.0, fmax(fabs(rows[j].b), df_to_double(sc.tot[M + j])));
-        const double tol = 1e-9 * scale[j];
-        if (nt->lam[j] > 0.0 || ((a.eq_mask >> j) & 1)) {
-            if (!(fabs(h[j]) <= tol)) conv = false;
-        } else if (!(h[j] <= tol)) {
-            conv = false;
+    const bool row = lane < M;
+    const int r = row ? lane : 0;
+    const DF two_c = DF{a.two_c_df[0], a.two_c_df[1]};
+    const bool eq = (a.eq_mask >> r) & 1;
+    const DF lam = DF{bc->it_hi[r], bc->it_lo[r]};
+    const DF b = DF{rows[r].b_hi, rows[r].b_lo};
+    const DF h = df_sub(df_sub(sc.tot[r], b), df_mul(two_c, lam));
+    const float scale = fmaxf(1.0f, fmaxf(fabsf(b.hi), sc.tot[M + r].hi));
+    const bool lpos = df_pos(lam), hpos = df_pos(h);
+    const bool act = lpos || eq;
+    const float tol = 1e-9f * scale;
+    bool conv = __all_sync(kFull, !row || (act ? fabsf(h.hi) <= tol : h.hi <= tol));
+    if (!__all_sync(kFull, !row || isfinite(h.hi))) {
+        if (lane == 0) {
+            bc->status = kErrNonfinite;
+            bc->mode = kModeDone;
         }
-    }
-    if (!isfinite(h[0]) || !isfinite(h[M - 1])) {
-        bc->status = kErrNonfinite;
-        bc->mode = kModeDone;
         return;
     }
-    double phi = 0.0;
-    for (int j = 0; j < M; ++j)
-        phi = fmax(phi, (nt->lam[j] > 0.0 || ((a.eq_mask >> j) & 1) ? fabs(h[j]) : fmax(h[j], 0.0)) / scale[j]);
+    float ph = row ? __fdividef(act ? fabsf(h.hi) : fmaxf(h.hi, 0.0f), scale) : 0.0f;
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) ph = fmaxf(ph, __shfl_xor_sync(kFull, ph, o));
+    const float phi = __shfl_sync(kFull, ph, 0);
+    int iters = nt->iters;
     if (nt->trial) {
-        if (!(phi < nt->base_phi * (1.0 - 1e-4) || phi <= 1e-8)) {
-            cstart_line_search<M>(ws);  // the full step did not reduce the residual
+        if (!(phi < nt->fbase_phi * (1.0f - 1e-4f) || phi <= 1e-8f)) {
+            if (lane == 0) cstart_line_search<M>(ws);  // the full step did not reduce the residual
             return;
         }
-        nt->trial = 0;
-        nt->iters = nt->iters + 1;
+        iters += 1;
     }
     // stop at the rounding floor of the FP32 sums: the scaled KKT residual is small and
     // has stopped halving over the last iterations
-    const double prev = nt->phi;
-    const int stall = (nt->iters >= 2 && phi <= 1e-7 && phi >= 0.5 * prev) ? nt->stall + 1 : 0;
-    nt->stall = stall;
-    nt->phi = phi;
+    const float prev = nt->fphi;
+    const int stall = (iters >= 2 && phi <= 1e-7f && phi >= 0.5f * prev) ? nt->stall + 1 : 0;
     if (stall >= 2) conv = true;
-    int S[M], ns = 0;
-    for (int j = 0; j < M; ++j)
-        if (nt->lam[j] > 0.0 || h[j] > 0.0 || ((a.eq_mask >> j) & 1)) S[ns++] = j;  // equality rows: always
-    if (conv || ns == 0) {
-        bc->mode = kModeDone;
+    // working set: rows with lam_j > 0, h_j > 0, and equality rows (always)
+    const unsigned rmask = (1u << M) - 1u;
+    unsigned inS = __ballot_sync(kFull, row && (lpos || hpos || eq)) & rmask;
+    __syncwarp();
+    if (lane == 0) {
+        nt->trial = 0;
+        nt->iters = iters;
+        nt->stall = stall;
+        nt->fphi = phi;
+        nt->stale = 1;
+    }
+    if (conv || inS == 0u) {
+        if (lane == 0) bc->mode = kModeDone;
         return;
     }
-    if (nt->iters >= a.maxiter_newton) {
-        nt->how = 3;
-        bc->mode = kModeDone;
+    if (iters >= a.maxiter_newton) {
+        if (lane == 0) {
+            nt->how = 3;
+            bc->mode = kModeDone;
+        }
         return;
     }
-    // J_SS d_S = h_S (eq. reg_jacobian restricted to the working set), Gaussian elimination;
-    // a row at lam_j = 0 whose direction would push it below zero leaves the set and the
-    // system is solved again (at most M times)
-    double d[M];
+    // J_SS d_S = h_S (eq. reg_jacobian restricted to the working set): Gaussian elimination
+    // on the full M x M system with the rows and columns outside the set replaced by the
+    // identity (d_j = 0 there); a row at lam_j = 0 whose direction would push it below zero
+    // leaves the set and the system is solved again (at most M times).  J_SS is symmetric
+    // positive definite (A D A^T + (2/C) I), so no pivoting is needed.
+    DF dq[M];
+#pragma unroll
     for (int round = 0; round < M; ++round) {
-        double Mx[M][M], rhs[M];
-        for (int p = 0; p < ns; ++p) {
-            for (int q = 0; q < ns; ++q) {
-                const int jp = S[p], jq = S[q];
-                const int lo = jp < jq ? jp : jq, hi = jp < jq ? jq : jp;
-                Mx[p][q] = df_to_double(sc.tot[2 * M + jidx<M>(lo, hi)]) + (jp == jq ? two_c : 0.0);
+        DF Mr[M];
+        const bool rin = (inS >> r) & 1u;
+#pragma unroll
+        for (int q = 0; q < M; ++q) {
+            const int lo_ = r < q ? r : q, hi_ = r < q ? q : r;
+            DF v = sc.tot[2 * M + jidx<M>(lo_, hi_)];
+            if (r == q) v = df_add(v, two_c);
+            Mr[q] = (rin && ((inS >> q) & 1u)) ? v : DF{r == q ? 1.0f : 0.0f, 0.0f};
+        }
+        DF rhs = rin ? h : df_zero();
+        DF inv[M];
+#pragma unroll
+        for (int p = 0; p < M; ++p) {
+            DF prow[M];
+#pragma unroll
+            for (int q = p; q < M; ++q) prow[q] = shfl_df(Mr[q], p);
+            const DF prhs = shfl_df(rhs, p);
+            inv[p] = df_div(DF{1.0f, 0.0f}, prow[p]);
+            if (r > p) {
+                const DF f = df_mul(Mr[p], inv[p]);
+#pragma unroll
+                for (int q = p; q < M; ++q) Mr[q] = df_sub(Mr[q], df_mul(f, prow[q]));
+                rhs = df_sub(rhs, df_mul(f, prhs));
             }
-            rhs[p] = h[S[p]];
         }
-        for (int p = 0; p < ns; ++p) {
-            const double inv = 1.0 / Mx[p][p];
-            for (int r = p + 1; r < ns; ++r) {
-                const double f = Mx[r][p] * inv;
-                for (int q = p; q < ns; ++q) Mx[r][q] -= f * Mx[p][q];
-                rhs[r] -= f * rhs[p];
-            }
+#pragma unroll
+        for (int p = M - 1; p >= 0; --p) {
+            DF v = rhs;
+#pragma unroll
+            for (int q = p + 1; q < M; ++q) v = df_sub(v, df_mul(Mr[q], dq[q]));
+            dq[p] = shfl_df(df_mul(v, inv[p]), p);
         }
-        double dS[M];
-        for (int p = ns - 1; p >= 0; --p) {
-            double v = rhs[p];
-            for (int q = p + 1; q < ns; ++q) v -= Mx[p][q] * dS[q];
-            dS[p] = v / Mx[p][p];
-        }
-        for (int j = 0; j < M; ++j) d[j] = 0.0;
-        for (int p = 0; p < ns; ++p) d[S[p]] = dS[p];
-        int keep = 0;
-        bool dropped = false;
-        for (int p = 0; p < ns; ++p) {
-            const int j = S[p];
-            if (nt->lam[j] <= 0.0 && d[j] < 0.0 && !((a.eq_mask >> j) & 1)) dropped = true;
-            else S[keep++] = j;
-        }
-        if (!dropped || keep == 0) break;
-        ns = keep;
+        const unsigned drop =
+            __ballot_sync(kFull, row && ((inS >> r) & 1u) && !lpos && df_pos(df_neg(dq[r])) && !eq) & rmask;
+        if (drop == 0u || drop == inS) break;
+        inS &= ~drop;
     }
-    double slope0 = 0.0, dtb = 0.0, dd = 0.0;
-    for (int j = 0; j < M; ++j) {
-        slope0 += d[j] * h[j];
-        dtb += d[j] * (rows[j].b + two_c * nt->lam[j]);
-        dd += d[j] * d[j];
+    const DF dr = row ? dq[r] : df_zero();
+    DF s0 = df_mul(dr, h), stb = df_mul(dr, df_add(b, df_mul(two_c, lam))), sdd = df_mul(dr, dr);
+#pragma unroll
+    for (int o = 1; o < 4; o <<= 1) {
+        s0 = df_add(s0, DF{__shfl_xor_sync(kFull, s0.hi, o), __shfl_xor_sync(kFull, s0.lo, o)});
+        stb = df_add(stb, DF{__shfl_xor_sync(kFull, stb.hi, o), __shfl_xor_sync(kFull, stb.lo, o)});
+        sdd = df_add(sdd, DF{__shfl_xor_sync(kFull, sdd.hi, o), __shfl_xor_sync(kFull, sdd.lo, o)});
     }
-    if (!(slope0 > 0.0)) {
-        bc->mode = kModeDone;  // no ascent along d: the rounding floor is reached
+    if (!df_pos(s0)) {
+        if (lane == 0) bc->mode = kModeDone;  // no ascent along d: the rounding floor is reached
         return;
     }
-    for (int j = 0; j < M; ++j) {
-        nt->d[j] = d[j];
-        nt->base[j] = nt->lam[j];
-        float dh, dl;
-        split_double(d[j], dh, dl);
-        bc->d_hi[j] = dh;
-        bc->d_lo[j] = dl;
+    if (row) {
+        bc->d_hi[r] = dr.hi;
+        bc->d_lo[r] = dr.lo;
+        nt->base_h[r] = lam.hi;
+        nt->base_l[r] = lam.lo;
+        // the full Newton step, kept in lam >= 0, is evaluated by the next E pass
+        DF ln = df_add(lam, dr);
+        if (!eq && !df_pos(ln)) ln = df_zero();
+        bc->it_hi[r] = ln.hi;
+        bc->it_lo[r] = ln.lo;
     }
-    nt->base_phi = phi;
-    nt->base_slope = slope0;
-    nt->base_dtb = dtb;
-    nt->base_dd = two_c * dd;
-    // the full Newton step, kept in lam >= 0, is evaluated by the next E pass
-    for (int j = 0; j < M; ++j)
-        nt->lam[j] = ((a.eq_mask >> j) & 1) ? nt->lam[j] + d[j] : fmax(nt->lam[j] + d[j], 0.0);
-    set_iterate(bc, nt, M);
-    nt->trial = 1;
-    bc->mode = kModeEval;
+    if (lane == 0) {
+        const DF dd = df_mul(two_c, sdd);
+        nt->fbase_phi = phi;
+        nt->slope_h = s0.hi;
+        nt->slope_l = s0.lo;
+        nt->dtb_h = stb.hi;
+        nt->dtb_l = stb.lo;
+        nt->dd_h = dd.hi;
+        nt->dd_l = dd.lo;
+        nt->trial = 1;
+        bc->mode = kModeEval;
+    }
 }
 
 // Phase LS: one pass of the exact line search along d.  The first pass of a direction
@@ -518,6 +580,7 @@ __device__ void cupd_after_line(const CoupledArgs& a, const BlockScratch& sc, Co
     if (lane != 0) return;
     nt->passes = nt->passes + 1;
     if (bc->any_active) return;
+    nt_sync(nt, bc, M);
     // line search finished: take the step
     double g = ls->lam;
     const double cap = nt->cap;
@@ -544,6 +607,7 @@ __device__ __forceinline__ void cfinish_if_done(CoupledState* ws) {
     volatile CoupledBcast* bc = &ws->bc;
     volatile NewtonState* nt = &ws->nt;
     if (bc->mode != kModeDone) return;
+    nt_sync(nt, bc, M);
     for (int j = 0; j < M; ++j) {
         float h, l;
         split_double(nt->lam[j], h, l);
@@ -569,6 +633,7 @@ __device__ void cupd_final(const CoupledArgs& a, const BlockScratch& sc, Coupled
     }
     rc = __shfl_sync(kFull, rc, 1);
     if (lane != 0) return;
+    nt_sync(nt, bc, M);
     int status = bc->status;
     for (int j = 0; j < M; ++j) {
         const double ax = df_to_double(sc.tot[j]);
@@ -1032,6 +1097,7 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
             if (!grid_allreduce_update(&ws->ctrl, ws->part, sc, 2 * M + NJ, 0, a.timeout_cycles,
                                     [&](BlockScratch& s) {
                                         cupd_after_eval<M>(a, s, cs);
+                                        __syncwarp();
                                         if (threadIdx.x == 0) {
                                             volatile NewtonState* nt = &cs->nt;
                                             nt->passes = nt->passes + 1;

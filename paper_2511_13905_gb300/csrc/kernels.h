@@ -166,6 +166,7 @@ struct CoupledArgs {
     double bconst[kMaxRows];
     double C, alpha_max, alpha_fb, eps_alpha, omega, tol_lambda, tol_N, c1;
     double two_c;         // 2 / C (computed by the host)
+    float two_c_df[2];    // 2 / C as a (hi, lo) float pair
     float step_df[8];     // alpha_max, alpha_fb, eps_alpha, omega as (hi, lo) float pairs
     int max_passes, maxiter_newton;
     int fault_inject;
