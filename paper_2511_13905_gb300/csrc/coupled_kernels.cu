@@ -162,12 +162,13 @@ __device__ void cupd_after_trial(const CoupledArgs& a, const BlockScratch& sc, C
     else if (k == 1) q = rH / SHs;
     const double NL = L + __shfl_sync(kFull, q, lane & ~7);
     const double NH = H + __shfl_sync(kFull, q, (lane & ~7) + 1);
-    const float p = next_point(lane, L, rL, H, rH, NL, NH);
+    const float p = next_point(lane, L, rL, H, rH, NL, NH, true);
     if (row && k == 0) {
         ws->info.b[j] = b;
         rows[j].reg = two_c;
         if (search) {
             store_row(&rows[j], b, L, rL, SLs, H, rH, SHs, 0.0, 0.0, 1, 0, 2);
+            rows[j].famax = sc.totmax[2 * M + jj];
             bc->active[j] = 1;
         } else if (closed) {
             const double lam = 0.5 * a.C * ((down ? smax : smin) - b);
@@ -779,11 +780,11 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
         const bool first = a.t == 0;
         AccSplit<5 * M, 0> acc;
         acc.init();
-        float mx[2 * M];  // per row: the upper saturation bound, minus the lower one
+        float mx[3 * M];  // per row: the upper saturation bound, minus the lower one, max |a_j|
         // a_j^T x_t enters b_j: exact products, hi parts summed with TwoSum, the rest in bl
         float bsh[M], bsl[M];
 #pragma unroll
-        for (int j = 0; j < M; ++j) mx[2 * j] = mx[2 * j + 1] = bsh[j] = bsl[j] = 0.0f;
+        for (int j = 0; j < M; ++j) mx[2 * j] = mx[2 * j + 1] = mx[2 * M + j] = bsh[j] = bsl[j] = 0.0f;
         const int eqm = a.eq_mask;
         auto rowsum = [&](float z, const float (&av)[M], float x) {
             const bool fr = z >= lo && z <= hi;
@@ -791,6 +792,7 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
 #pragma unroll
             for (int j = 0; j < M; ++j) {
                 const float aj = av[j];
+                mx[2 * M + j] = fmaxf(mx[2 * M + j], fabsf(aj));
                 const float ph = aj * x;
                 const DF t = two_sum(bsh[j], ph);
                 bsh[j] = t.hi;
@@ -894,8 +896,8 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
         acc.fold();
 #pragma unroll
         for (int j = 0; j < M; ++j) acc.d[5 * j] = df_add(acc.d[5 * j], fast_two_sum(bsh[j], bsl[j]));
-        block_reduce<5 * M, 2 * M>(acc.d, mx, sc);
-        if (!grid_allreduce_update(&ws->ctrl, ws->part, sc, 5 * M, 2 * M, a.timeout_cycles, [&](BlockScratch& s) {
+        block_reduce<5 * M, 3 * M>(acc.d, mx, sc);
+        if (!grid_allreduce_update(&ws->ctrl, ws->part, sc, 5 * M, 3 * M, a.timeout_cycles, [&](BlockScratch& s) {
                 cupd_after_trial<M>(a, s, cs);
                 __syncwarp();
                 if (threadIdx.x == 0) {

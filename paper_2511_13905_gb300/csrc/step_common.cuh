@@ -135,11 +135,18 @@ __device__ __forceinline__ bool wide_bracket(double L, double H) {
 }
 
 __device__ __forceinline__ float next_point(int lane, double L, double rL, double H, double rH, double NL,
-                                            double NH) {
+                                            double NH, bool cold = false) {
     const int k = lane & 7;
     const double w = H - L;
     double v;
-    if (k == 0) v = NL;
+    if (cold && wide_bracket(L, H)) {
+        // a cold start: all eight points on the ladder around the Newton estimate from the
+        // zero end, as next_point_warm_f does for single rows
+        const double sec = L + rL * w / (rL - rH);
+        const double base = (L == 0.0 && NL > L && NL < H) ? NL : (H == 0.0 && NH > L && NH < H) ? NH : sec;
+        v = base * (k == 0 ? 0.125 : k == 1 ? 0.5 : k == 2 ? 0.8 : k == 3 ? 1.0 : k == 4 ? 1.2 : k == 5 ? 1.45
+                    : k == 6 ? 2.0 : 4.0);
+    } else if (k == 0) v = NL;
     else if (k == 1) v = NH;
     else if (k == 2) v = L + rL * w / (rL - rH);
     else if (wide_bracket(L, H)) {
