@@ -498,119 +498,178 @@ def run_batched(args, local_rank=0):
 # --------------------------------------------------------------------------- serving
 
 def run_serving(args, local_rank=0):
-    """Served (continuous batching) vs plain (one launch per request) on the same offered load.
+    """The serving stream: `sessions` design sessions x `serve_steps` steps = 2048 requests by
+    default, n log-uniform in [4096, n_max], m in {1, 2, 4} (half of the m > 1 sessions with
+    independent rows, half coupled), inputs from each request's seed.  Requests arrive by a
+    seeded Poisson process; request i is step i // sessions of session i % sessions (round
+    robin), and a session's next step needs its previous result.
 
-    `sessions` design sessions from the serving workload recipe (n log-uniform in
-    [4096, n_max], m in {1, 2, 4}, half of the m > 1 sessions independent, half coupled).
-    In each of `waves` waves every session submits its next step at once; a request's
-    latency runs from the wave's start to the moment its rho_{t+1} is in host memory.
-    Plain: the same requests one after another, each its own launch (H2D of grad f and A,
-    pgdto_step, D2H of x).  Both move the same bytes per request."""
+    Each step's constraint values g_j(x_t) = a_j^T x_t follow the session's own designs;
+    they are recorded by an untimed dry run through plain handles (formed on the device)
+    and replayed by both timed arms, so the clients do no arithmetic on the timed path.
+
+    Plain: one worker takes the requests in arrival order, one launch each (H2D of grad f
+    and A from the host arrays, pgdto_step, D2H of x_{t+1}).  Its capacity (steps/s with
+    every request waiting from the start) sets the arrival rates: 0.5, 0.8 and 1.2 times it.
+    Served: pgdto_submit at each arrival time, continuous batching in the server, latency
+    from the arrival to the completion the server stamps.  Latency = completion - arrival,
+    queueing included."""
     import numpy as np
     import torch
 
     from paper_2511_13905_gb300 import binding, inputs
     dev = torch.device("cuda", local_rank)
-    reqs = inputs.serving_requests(count=args.serve_sessions, n_max=args.serve_nmax)
+    S, K = args.serve_sessions, args.serve_steps
+    reqs = inputs.serving_requests(count=S, n_max=args.serve_nmax)
     probs = [inputs.request_problem(r) for r in reqs]
-    rng = np.random.default_rng(inputs.SEED_BASE + 77)
-    grads = [[(p["g"] * np.float32(1.0 + 0.05 * k)).astype(np.float32) for k in range(2)] for p in probs]
-    waves = args.serve_waves
-
-    def constraint_values(p, x):
-        # g_j(x_t) at the session's current design (all rows are linear here), computed by
-        # the client between waves, outside the timed region
-        x = x.astype(np.float64)
-        if p["mode"] == "independent":
-            return np.add.reduceat(x, p["seg"][:-1])
-        return np.atleast_2d(p["A"]).astype(np.float64) @ x
+    grads = [[np.ascontiguousarray((p["g"] * np.float32(1.0 + 0.05 * k)).astype(np.float32)) for k in range(2)]
+             for p in probs]
+    Ahost = [np.ascontiguousarray(p["A"]).ravel() for p in probs]
+    order = [(i % S, i // S) for i in range(S * K)]
 
     def pct(v, q):
         v = sorted(v)
         return v[min(len(v) - 1, int(round(q * (len(v) - 1))))]
 
-    # served
-    srv = binding.Server(budget_bytes=64 << 30, max_sessions=len(probs) + 1)
-    outs = [np.empty(p["n"], np.float32) for p in probs]
-    gvals = [np.asarray(p["gval"], np.float64) for p in probs]
-    nc_served = 0
-    lat = []
-    warm = True
-    t_total = 0.0
-    for w in range(waves + 1):
-        t0 = srv.clock_us()
-        tickets = []
-        for i, p in enumerate(probs):
-            st, t = srv.submit(i, p["n"], p["m"], grads[i][w % 2], np.ascontiguousarray(p["A"]), gvals[i], p["G"],
-                               outs[i], x0=p["x"] if w == 0 else None, seg=p.get("seg"))
-            if st != binding.PGDTO_OK:
-                raise RuntimeError("submit failed: %s" % st)
-            tickets.append(t)
-        done_at = {}
-        for i in range(len(tickets)):
-            # blocking waits; each completion time was stamped by the server when published
-            st, d, _, t_done = srv.wait(tickets[i])
-            if st != binding.PGDTO_OK or d not in (binding.PGDTO_OK, binding.PGDTO_NOT_CONVERGED):
-                raise RuntimeError("served step failed: %s / %s" % (st, d))
-            nc_served += int(d == binding.PGDTO_NOT_CONVERGED)
-            done_at[i] = t_done
-        t1 = max(done_at.values())
-        if not warm:
-            lat += [(done_at[i] - t0) * 1e-6 for i in range(len(probs))]
-            t_total += (t1 - t0) * 1e-6
-        warm = False
-        gvals = [constraint_values(p, outs[i]) for i, p in enumerate(probs)]
-    stats = srv.stats()
-    srv.close()
-    served_final = [o.copy() for o in outs]
-    served = {"p50_ms": 1e3 * pct(lat, 0.5), "p99_ms": 1e3 * pct(lat, 0.99),
-              "steps_per_s": len(lat) / t_total, "launches": stats["batches"], "not_converged": nc_served}
-
-    # plain: one launch per request
-    handles = [binding.Handle(p["n"], p["m"], seg=p.get("seg")) for p in probs]
-    xd = [torch.from_numpy(p["x"].copy()).to(dev) for p in probs]
-    gd = [torch.empty(p["n"], device=dev) for p in probs]
-    Ad = [torch.empty(np.asarray(p["A"]).size, device=dev) for p in probs]
-    # the same host arrays the served arm submits (pageable NumPy memory), copied by DMA
-    # straight to and from the device as the server does
-    ghost = [[torch.from_numpy(g) for g in gg] for gg in grads]
-    Ahost = [torch.from_numpy(np.ascontiguousarray(p["A"]).ravel()) for p in probs]
-    for h in handles:
+    # ---- untimed dry run: each session's constraint values along its own trajectory
+    gvals = [[None] * K for _ in range(S)]
+    dry_final = []
+    for s, p in enumerate(probs):
+        n, m = p["n"], p["m"]
+        h = binding.Handle(n, m, seg=p.get("seg"))
         h.set_state(None, None, None, 0)
-    gvals = [np.asarray(p["gval"], np.float64) for p in probs]
-    nc_plain = 0
-    lat_p = []
-    t_total_p = 0.0
-    warm = True
-    for w in range(waves + 1):
+        x = torch.from_numpy(p["x"].copy()).to(dev)
+        A = torch.from_numpy(Ahost[s]).to(dev)
+        for k in range(K):
+            if p["mode"] == "independent":
+                seg = p["seg"]
+                gv = [float(x[seg[j]:seg[j + 1]].double().sum().item()) for j in range(m)]
+            else:
+                gv = (A.reshape(m, n).double() @ x.double()).tolist()
+            gvals[s][k] = gv
+            st, _ = h.step(x, torch.from_numpy(grads[s][k % 2]).to(dev), A, gv, p["G"], want_info=True)
+            if st not in (binding.PGDTO_OK, binding.PGDTO_NOT_CONVERGED):
+                raise RuntimeError("dry-run step failed: %s" % st)
+        dry_final.append(x.cpu().numpy())
+        h.close()
+    torch.cuda.synchronize()
+
+    # ---- plain arm: one worker, arrival order, one launch per request
+    def run_plain(arrivals):
+        handles = [binding.Handle(p["n"], p["m"], seg=p.get("seg")) for p in probs]
+        for h in handles:
+            h.set_state(None, None, None, 0)
+        xd = [torch.from_numpy(p["x"].copy()).to(dev) for p in probs]
+        gd = [torch.empty(p["n"], device=dev) for p in probs]
+        Ad = [torch.empty(Ahost[s].size, device=dev) for s in range(S)]
+        gh = [[torch.from_numpy(g) for g in gg] for gg in grads]
+        Ah = [torch.from_numpy(a) for a in Ahost]
+        outs = [np.empty(p["n"], np.float32) for p in probs]
+        nc = 0
+        lat = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for i, p in enumerate(probs):
-            gd[i].copy_(ghost[i][w % 2])
-            Ad[i].copy_(Ahost[i])
-            st, _ = handles[i].step(xd[i], gd[i], Ad[i], gvals[i], p["G"], want_info=True)
+        last = t0
+        for i, (s, k) in enumerate(order):
+            t_arr = t0 + arrivals[i]
+            now = time.perf_counter()
+            while now < t_arr:
+                if t_arr - now > 2e-4:
+                    time.sleep(t_arr - now - 1e-4)
+                now = time.perf_counter()
+            gd[s].copy_(gh[s][k % 2])
+            Ad[s].copy_(Ah[s])
+            st, _ = handles[s].step(xd[s], gd[s], Ad[s], gvals[s][k], probs[s]["G"], want_info=True)
             if st not in (binding.PGDTO_OK, binding.PGDTO_NOT_CONVERGED):
                 raise RuntimeError("plain step failed: %s" % st)
-            nc_plain += int(st == binding.PGDTO_NOT_CONVERGED)
-            torch.from_numpy(outs[i]).copy_(xd[i])
-            if not warm:
-                lat_p.append(time.perf_counter() - t0)
-        t1 = time.perf_counter()
-        if not warm:
-            t_total_p += t1 - t0
-        warm = False
-        gvals = [constraint_values(p, outs[i]) for i, p in enumerate(probs)]
-    for h in handles:
-        h.close()
-    plain = {"p50_ms": 1e3 * pct(lat_p, 0.5), "p99_ms": 1e3 * pct(lat_p, 0.99),
-             "steps_per_s": len(lat_p) / t_total_p, "not_converged": nc_plain}
-    # equal accuracy: both arms ran the same trajectories; the designs they end on
-    diff = max(float(np.max(np.abs(a.astype(np.float64) - b.astype(np.float64)))) for a, b in zip(served_final, outs))
-    return {"sessions": len(probs), "waves": waves, "requests_timed": len(lat),
+            nc += int(st == binding.PGDTO_NOT_CONVERGED)
+            torch.from_numpy(outs[s]).copy_(xd[s])
+            last = time.perf_counter()
+            lat.append(last - t_arr)
+        for h in handles:
+            h.close()
+        return {"p50_ms": 1e3 * pct(lat, 0.5), "p99_ms": 1e3 * pct(lat, 0.99),
+                "steps_per_s": len(lat) / (last - t0), "not_converged": nc, "launches": len(lat)}, outs
+
+    # ---- served arm: submit at each arrival time, the server batches what is ready
+    def run_served(arrivals):
+        srv = binding.Server(budget_bytes=64 << 30, max_sessions=S + 1)
+        outs = [np.empty(p["n"], np.float32) for p in probs]
+        last_ticket = [None] * S
+        done_t = {}
+        arr_t = []
+        tickets = []
+        nc = 0
+
+        def collect(ticket):
+            nonlocal nc
+            st, d, _, t_done = srv.wait(ticket)
+            if st != binding.PGDTO_OK or d not in (binding.PGDTO_OK, binding.PGDTO_NOT_CONVERGED):
+                raise RuntimeError("served step failed: %s / %s" % (st, d))
+            nc += int(d == binding.PGDTO_NOT_CONVERGED)
+            done_t[ticket] = t_done
+
+        # sessions open before the timed stream, as the plain arm creates its handles
+        for s, p in enumerate(probs):
+            st = srv.open(s, p["n"], p["m"], p["x"], seg=p.get("seg"))
+            if st != binding.PGDTO_OK:
+                raise RuntimeError("session open failed: %s" % st)
+        t0 = srv.clock_us()
+        for i, (s, k) in enumerate(order):
+            t_arr = t0 + int(1e6 * arrivals[i])
+            now = srv.clock_us()
+            while now < t_arr:
+                if t_arr - now > 200:
+                    time.sleep((t_arr - now - 100) * 1e-6)
+                now = srv.clock_us()
+            p = probs[s]
+            while True:
+                st, t = srv.submit(s, p["n"], p["m"], grads[s][k % 2], Ahost[s], gvals[s][k], p["G"], outs[s],
+                                   seg=p.get("seg"))
+                if st == binding.PGDTO_OK:
+                    break
+                if st != binding.PGDTO_ERR_BUSY or last_ticket[s] is None or last_ticket[s] in done_t:
+                    raise RuntimeError("submit failed: %s" % st)
+                collect(last_ticket[s])  # the session's previous step is still running
+            last_ticket[s] = t
+            tickets.append(t)
+            arr_t.append(t_arr)
+        for t in tickets:
+            if t not in done_t:
+                collect(t)
+        stats = srv.stats()
+        srv.close()
+        lat = [(done_t[t] - a) * 1e-6 for t, a in zip(tickets, arr_t)]
+        span = (max(done_t.values()) - t0) * 1e-6
+        return {"p50_ms": 1e3 * pct(lat, 0.5), "p99_ms": 1e3 * pct(lat, 0.99), "steps_per_s": len(lat) / span,
+                "not_converged": nc, "launches": stats["batches"]}, outs
+
+    def diff(a, b):
+        return max(float(np.max(np.abs(x.astype(np.float64) - y.astype(np.float64)))) for x, y in zip(a, b))
+
+    rng = np.random.default_rng(inputs.SEED_BASE + 5000)
+    unit = rng.exponential(1.0, S * K)  # one exponential draw per request, scaled by each rate
+    # plain capacity: every request waiting from the start
+    plain_sat, _ = run_plain(np.zeros(S * K))
+    cap = plain_sat["steps_per_s"]
+    rates = []
+    for f in (0.5, 0.8, 1.2):
+        lam = f * cap
+        arrivals = np.cumsum(unit) / lam
+        pl, out_p = run_plain(arrivals)
+        sv, out_s = run_served(arrivals)
+        rates.append({"rate_vs_plain_capacity": f, "offered_steps_per_s": lam, "plain": pl, "served": sv,
+                      "max_abs_diff_final_x_served_vs_plain": diff(out_s, out_p),
+                      "max_abs_diff_final_x_served_vs_dry_run": diff(out_s, dry_final)})
+    torch.cuda.synchronize()
+    return {"requests": S * K, "sessions": S, "steps_per_session": K,
             "n_range": [min(p["n"] for p in probs), max(p["n"] for p in probs)],
+            "n_total": int(sum(p["n"] for p in probs)),
             "modes": {m: sum(1 for p in probs if p["mode"] == m) for m in ("single", "independent", "coupled")},
-            "served": served, "plain": plain, "max_abs_diff_final_x": diff,
-            "latency": "wave start to rho_{t+1} in host memory; every session submits one step per wave"}
+            "plain_capacity_steps_per_s": cap, "rates": rates,
+            "arrivals": "Poisson (seeded exponential gaps), request i = step i // %d of session i %% %d; a session's "
+                        "next step waits for its previous result" % (S, S),
+            "latency": "arrival to rho_{t+1} in host memory (queueing included)"}
 
 
 # --------------------------------------------------------------------------- oracle leg
@@ -834,9 +893,9 @@ def main():
     ap.add_argument("--no-errors", action="store_true", help="skip the oracle errors")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--batch-instances", type=int, default=256)
-    ap.add_argument("--serve-sessions", type=int, default=48)
-    ap.add_argument("--serve-waves", type=int, default=12)
-    ap.add_argument("--serve-nmax", type=int, default=1 << 20)
+    ap.add_argument("--serve-sessions", type=int, default=128)
+    ap.add_argument("--serve-steps", type=int, default=16)
+    ap.add_argument("--serve-nmax", type=int, default=4 << 20)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

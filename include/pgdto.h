@@ -224,9 +224,11 @@ pgdto_status pgdto_project_many(int count, pgdto_handle* const* hs, const float*
  * batching: every session keeps its design x and optimizer state on the device between
  * its steps; a submitted step's inputs are copied by DMA from the caller's buffers on a
  * copy stream and, while one cycle runs on the GPU, newly arrived steps queue for the
- * next.  A cycle launches every queued single/independent session as one batched step
- * (pgdto_step_many), then each coupled-row session in a launch of its own, smallest
- * first; each launch's results are delivered as soon as that launch completes.  Sessions are admitted while their device memory fits the HBM budget;
+ * next.  A cycle launches every queued single/independent session small enough for one
+ * thread-block cluster as one batched step (pgdto_step_many), then each coupled-row
+ * session and each larger session in a whole-GPU launch of its own, smallest first; a
+ * completion thread delivers each launch's results as soon as that launch completes,
+ * while the next cycle is already being launched.  Sessions are admitted while their device memory fits the HBM budget;
  * otherwise submit returns PGDTO_ERR_BUSY and the caller retries after sessions close.
  * The paper has no serving layer; the step each request runs is Alg. 3 as above.
  */
@@ -258,6 +260,13 @@ pgdto_status pgdto_server_create(pgdto_server** srv, uint64_t budget_bytes, int 
  * session limit reached, or this session already has a step queued or running.
  * PGDTO_ERR_CUDA: an upload failed (a new session is not kept). */
 pgdto_status pgdto_submit(pgdto_server* srv, const pgdto_request* req, uint64_t* ticket);
+
+/* Open a session without a step: admission (session limit, HBM budget), the session's
+ * device state, and the upload of its starting design req->x0 (host, n floats; copied
+ * before the call returns).  Only req->session, n, m, seg_offsets, lo, hi, x0 and eq_mask
+ * are read.  Its first pgdto_submit then needs no x0.  PGDTO_ERR_ARG if the session is
+ * already open, PGDTO_ERR_BUSY if it would not fit, PGDTO_ERR_CUDA if the upload failed. */
+pgdto_status pgdto_server_open(pgdto_server* srv, const pgdto_request* req);
 
 /* Non-blocking: *done = PGDTO_ERR_BUSY while the step is queued or running, else its final
  * status (x_out written, info filled when non-NULL).  A finished ticket is forgotten after

@@ -110,6 +110,7 @@ def load(path=None):
         "pgdto_server_create": (ctypes.c_int, [ctypes.POINTER(H), ctypes.c_uint64, ctypes.c_int,
                                                ctypes.POINTER(Params), P]),
         "pgdto_submit": (ctypes.c_int, [H, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+        "pgdto_server_open": (ctypes.c_int, [H, ctypes.POINTER(Request)]),
         "pgdto_poll": (ctypes.c_int, [H, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Info)]),
         "pgdto_wait": (ctypes.c_int, [H, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(Info),
                                       ctypes.POINTER(ctypes.c_int64)]),
@@ -348,6 +349,18 @@ class Server:
         if st == PGDTO_OK:
             self._keep[t.value] = x_out
         return st, t.value
+
+    def open(self, session, n, m, x0, seg=None, lo=0.0, hi=1.0, eq_mask=0):
+        """pgdto_server_open: admit a session and upload its starting design (no step)."""
+        r = Request()
+        r.eq_mask = int(eq_mask)
+        r.session, r.n, r.m, r.lo, r.hi = int(session), int(n), int(m), float(lo), float(hi)
+        segarr = None
+        if seg is not None:
+            segarr = (ctypes.c_int64 * (m + 1))(*[int(v) for v in seg])
+            r.seg_offsets = segarr
+        r.x0 = x0.ctypes.data
+        return self.lib.pgdto_server_open(self.h, ctypes.byref(r))
 
     def poll(self, ticket):
         """(call status, done status or PGDTO_ERR_BUSY, Info)."""

@@ -283,6 +283,8 @@ extern "C" pgdto_status pgdto_set_stream(pgdto_handle* h, void* s) {
 
 extern "C" int64_t pgdto_kernel_launches(const pgdto_handle* h) { return h ? h->launches : -1; }
 
+int pgdto_handle_whole_gpu(const pgdto_handle* h) { return h && h->engine == 1 ? 1 : 0; }
+
 extern "C" pgdto_status pgdto_set_state(pgdto_handle* h, const float* x_prev, const float* g_prev,
                                         const float* d_prev, int t) {
     if (!h || t < 0) return PGDTO_ERR_ARG;

@@ -19,3 +19,7 @@ pgdto_status pgdto_info_enqueue(pgdto_handle* h, pgdto_info_slot* slot);
 // pgdto_info_enqueue): the step's status, and `info` when non-null.  An error clears the
 // control block with an asynchronous memset on the handle's stream, as pgdto_last_info does.
 pgdto_status pgdto_info_collect(pgdto_handle* h, const pgdto_info_slot* slot, pgdto_info* info);
+
+// 1 when the handle's steps run on the grid engine (every SM on the one problem), 0 when
+// they run on one thread-block cluster; the server batches only the latter.
+int pgdto_handle_whole_gpu(const pgdto_handle* h);

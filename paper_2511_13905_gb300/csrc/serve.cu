@@ -56,6 +56,13 @@ struct Done {
     int64_t t_us = 0;  // completion on the server's clock
 };
 
+// One launch unit of a cycle (the batched group, or one session's own launch) and the
+// event recorded behind it; the completion thread finishes units in launch order.
+struct Unit {
+    cudaEvent_t ev = nullptr;
+    std::vector<Request> reqs;
+};
+
 }  // namespace
 
 struct pgdto_server {
@@ -65,17 +72,22 @@ struct pgdto_server {
     cudaStream_t stream = nullptr;  // launches and result copies
     cudaStream_t copy = nullptr;    // input uploads
     cudaStream_t dtoh = nullptr;    // result downloads
-    std::vector<cudaEvent_t> unit_done;  // one per launch unit of a cycle (batched group, own launches)
+    std::vector<cudaEvent_t> free_events;  // recorded behind launch units, recycled when finished
+    std::vector<cudaEvent_t> all_events;
     std::mutex mu;
     std::condition_variable cv;       // service thread: work queued
     std::condition_variable cv_done;  // waiters: a result was published
+    std::condition_variable cv_fin;   // completion thread: a unit was launched
+    std::deque<Unit> inflight;        // launched, not yet finished (launch order)
+    std::thread finisher;
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
     std::thread worker;
     bool stop = false;
+    bool fin_stop = false;            // the service thread has stopped: finish what is in flight
     uint64_t next_ticket = 1;
     std::map<uint64_t, Session*> sessions;
     std::deque<Request> pending;
-    std::vector<Request> running;
+    std::vector<Request> running;     // every request launched and not yet published
     std::map<uint64_t, Done> done;
     int64_t batches = 0, steps = 0;
 };
@@ -103,13 +115,13 @@ void free_session(Session* s) {
 }
 
 // Complete one launch unit: wait for its event, copy the designs to the callers' buffers,
-// publish the reports (poll sees them at once), release closing sessions.
-void finish_unit(pgdto_server* srv, cudaEvent_t ev, std::vector<Request>& unit) {
-    cudaEventSynchronize(ev);
-    std::vector<Done> results(unit.size());
-    cudaStreamWaitEvent(srv->dtoh, ev, 0);
-    for (size_t i = 0; i < unit.size(); ++i) {
-        Request& r = unit[i];
+// publish the reports (poll sees them at once), release closing sessions, recycle the event.
+void finish_unit(pgdto_server* srv, Unit& unit) {
+    cudaEventSynchronize(unit.ev);
+    std::vector<Done> results(unit.reqs.size());
+    cudaStreamWaitEvent(srv->dtoh, unit.ev, 0);
+    for (size_t i = 0; i < unit.reqs.size(); ++i) {
+        Request& r = unit.reqs[i];
         memset(&results[i].info, 0, sizeof(results[i].info));
         results[i].status = pgdto_info_collect(r.s->h, r.s->slot, &results[i].info);
         if (r.x_out &&
@@ -121,46 +133,64 @@ void finish_unit(pgdto_server* srv, cudaEvent_t ev, std::vector<Request>& unit) 
         for (Done& d : results) d.status = PGDTO_ERR_CUDA;
     const int64_t now = clock_us(srv);
     for (Done& d : results) d.t_us = now;
-    std::lock_guard<std::mutex> lock(srv->mu);
-    for (size_t i = 0; i < unit.size(); ++i) {
-        Request& r = unit[i];
-        srv->done[r.ticket] = results[i];
-        r.s->busy = false;
-        for (size_t q = 0; q < srv->running.size(); ++q)
-            if (srv->running[q].ticket == r.ticket) {
-                srv->running.erase(srv->running.begin() + q);
-                break;
+    std::vector<Session*> closed;
+    {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        for (size_t i = 0; i < unit.reqs.size(); ++i) {
+            Request& r = unit.reqs[i];
+            srv->done[r.ticket] = results[i];
+            r.s->busy = false;
+            for (size_t q = 0; q < srv->running.size(); ++q)
+                if (srv->running[q].ticket == r.ticket) {
+                    srv->running.erase(srv->running.begin() + q);
+                    break;
+                }
+            if (r.close) {
+                srv->in_use -= r.s->bytes;
+                srv->sessions.erase(r.s->id);
+                closed.push_back(r.s);
             }
-        if (r.close) {
-            srv->in_use -= r.s->bytes;
-            srv->sessions.erase(r.s->id);
-            free_session(r.s);
+            srv->steps += 1;
         }
-        srv->steps += 1;
+        srv->free_events.push_back(unit.ev);
     }
     srv->cv_done.notify_all();
+    // device memory is released outside the lock (freeing waits for the device)
+    for (Session* c : closed) free_session(c);
 }
 
-// One cycle: every single/independent session in one batched step (pgdto_step_many: one
-// thread-block cluster per session, sized by its n, all side by side), then each coupled
-// session in a launch of its own, smallest first; each unit's results are reported as
-// soon as its own event completes.  A cycle with one single/independent session runs it
-// through pgdto_step, on the engine its handle chose (the whole GPU for a large n).
+cudaEvent_t take_event(pgdto_server* srv) {
+    std::lock_guard<std::mutex> lock(srv->mu);
+    if (srv->free_events.empty()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        srv->all_events.push_back(e);
+        return e;
+    }
+    cudaEvent_t e = srv->free_events.back();
+    srv->free_events.pop_back();
+    return e;
+}
+
+// One cycle: every small single/independent session in one batched step (pgdto_step_many:
+// one thread-block cluster per session, sized by its n, all side by side), then each
+// coupled session and each single/independent session whose handle runs on the whole GPU
+// (n beyond the cluster range) in a launch of its own, smallest first.  A lone batched
+// session runs through pgdto_step as well.  The launches are enqueued and handed to the
+// completion thread, which reports each unit as soon as its own event completes, while
+// this thread goes on to launch the next cycle.
 void run_cycle(pgdto_server* srv, std::vector<Request>& batch) {
     std::vector<Request> group;
     std::vector<Request> own;
-    for (Request& r : batch) (r.s->coupled ? own : group).push_back(r);
+    for (Request& r : batch)
+        (r.s->coupled || pgdto_handle_whole_gpu(r.s->h) ? own : group).push_back(r);
     if (group.size() == 1) {
         own.push_back(group[0]);
         group.clear();
     }
     std::sort(own.begin(), own.end(), [](const Request& a, const Request& b) { return a.s->n < b.s->n; });
-    while (srv->unit_done.size() < own.size() + 1) {
-        cudaEvent_t e;
-        cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-        srv->unit_done.push_back(e);
-    }
     for (Request& r : batch) cudaStreamWaitEvent(srv->stream, r.s->uploaded, 0);
+    std::vector<Unit> units;
     if (!group.empty()) {
         std::vector<pgdto_handle*> hs;
         std::vector<float*> xs;
@@ -178,20 +208,27 @@ void run_cycle(pgdto_server* srv, std::vector<Request>& batch) {
         }
         pgdto_step_many((int)hs.size(), hs.data(), xs.data(), gs.data(), As.data(), gv.data(), GG.data(), nullptr);
         for (Request& r : group) pgdto_info_enqueue(r.s->h, r.s->slot);
-        cudaEventRecord(srv->unit_done[0], srv->stream);
+        Unit u;
+        u.ev = take_event(srv);
+        u.reqs = group;
+        cudaEventRecord(u.ev, srv->stream);
+        units.push_back(u);
     }
-    for (size_t q = 0; q < own.size(); ++q) {
-        Request& r = own[q];
+    for (Request& r : own) {
         pgdto_step(r.s->h, r.s->x, r.s->g, r.s->A, r.g_val, r.G, nullptr);
         pgdto_info_enqueue(r.s->h, r.s->slot);
-        cudaEventRecord(srv->unit_done[q + 1], srv->stream);
+        Unit u;
+        u.ev = take_event(srv);
+        u.reqs.assign(1, r);
+        cudaEventRecord(u.ev, srv->stream);
+        units.push_back(u);
     }
-    srv->batches += (group.empty() ? 0 : 1) + (int64_t)own.size();
-    if (!group.empty()) finish_unit(srv, srv->unit_done[0], group);
-    for (size_t q = 0; q < own.size(); ++q) {
-        std::vector<Request> one(1, own[q]);
-        finish_unit(srv, srv->unit_done[q + 1], one);
+    {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        srv->batches += (int64_t)units.size();
+        for (Unit& u : units) srv->inflight.push_back(u);
     }
+    srv->cv_fin.notify_one();
     batch.clear();
 }
 
@@ -202,15 +239,70 @@ void service(pgdto_server* srv) {
             std::unique_lock<std::mutex> lock(srv->mu);
             srv->cv.wait(lock, [&] { return srv->stop || !srv->pending.empty(); });
             if (srv->pending.empty() && srv->stop) return;
-            // everything queued now joins this launch (one step per session: submit enforces it)
+            // everything queued now joins this cycle (one step per session: submit enforces it)
             while (!srv->pending.empty()) {
                 batch.push_back(srv->pending.front());
+                srv->running.push_back(srv->pending.front());
                 srv->pending.pop_front();
             }
-            srv->running = batch;
         }
         run_cycle(srv, batch);
     }
+}
+
+// The completion thread: finishes launched units in launch order (one stream, so that is
+// also their completion order) until the server stops and nothing is in flight.
+void finisher(pgdto_server* srv) {
+    for (;;) {
+        Unit u;
+        {
+            std::unique_lock<std::mutex> lock(srv->mu);
+            srv->cv_fin.wait(lock, [&] { return srv->fin_stop || !srv->inflight.empty(); });
+            if (srv->inflight.empty()) return;
+            u = srv->inflight.front();
+            srv->inflight.pop_front();
+        }
+        finish_unit(srv, u);
+    }
+}
+
+// Admit and create a session (the caller holds the server's lock): the handle, the device
+// design and input staging, the pinned report slot.  PGDTO_ERR_BUSY when the session limit
+// or the HBM budget would be exceeded.
+pgdto_status create_session(pgdto_server* srv, const pgdto_request* req, Session** out) {
+    if (!req->x0) return PGDTO_ERR_ARG;
+    const bool coupled = req->m > 1 && !req->seg_offsets;
+    const int64_t a_len = coupled || (req->m == 1) ? req->n * (int64_t)req->m : req->n;
+    const uint64_t bytes = session_bytes(req->n, a_len);
+    if ((int)srv->sessions.size() >= srv->max_sessions || srv->in_use + bytes > srv->budget)
+        return PGDTO_ERR_BUSY;
+    Session* s = new Session();
+    s->id = req->session;
+    s->n = req->n;
+    s->m = req->m;
+    s->a_len = a_len;
+    s->coupled = coupled;
+    s->bytes = bytes;
+    pgdto_params p = srv->params;
+    p.mode = PGDTO_AUTO;
+    p.eq_mask = req->eq_mask;
+    if (coupled) p.engine = 0;  // coupled rows run on the grid engine (one launch each)
+    pgdto_status st = pgdto_create(&s->h, req->n, req->m, req->seg_offsets, req->lo, req->hi, &p, srv->stream);
+    const size_t nb = (size_t)req->n * sizeof(float);
+    if (st == PGDTO_OK && (cudaMalloc(&s->x, nb) != cudaSuccess || cudaMalloc(&s->g, nb) != cudaSuccess ||
+                           cudaMalloc(&s->A, (size_t)a_len * sizeof(float)) != cudaSuccess ||
+                           cudaMallocHost(&s->slot, sizeof(pgdto_info_slot)) != cudaSuccess ||
+                           cudaEventCreateWithFlags(&s->uploaded, cudaEventDisableTiming) != cudaSuccess))
+        st = PGDTO_ERR_OOM;
+    if (st == PGDTO_OK) st = pgdto_set_state(s->h, nullptr, nullptr, nullptr, 0);
+    if (st != PGDTO_OK) {
+        free_session(s);
+        return st == PGDTO_ERR_OOM ? PGDTO_ERR_BUSY : st;
+    }
+    srv->sessions[s->id] = s;
+    srv->in_use += bytes;
+    *out = s;
+    return PGDTO_OK;
 }
 
 }  // namespace
@@ -233,6 +325,7 @@ extern "C" pgdto_status pgdto_server_create(pgdto_server** out, uint64_t budget_
         return PGDTO_ERR_CUDA;
     }
     srv->worker = std::thread(service, srv);
+    srv->finisher = std::thread(finisher, srv);
     *out = srv;
     return PGDTO_OK;
 }
@@ -249,37 +342,8 @@ extern "C" pgdto_status pgdto_submit(pgdto_server* srv, const pgdto_request* req
         if (s->n != req->n || s->m != req->m) return PGDTO_ERR_ARG;
         if (s->busy) return PGDTO_ERR_BUSY;
     } else {
-        if (!req->x0) return PGDTO_ERR_ARG;
-        const bool coupled = req->m > 1 && !req->seg_offsets;
-        const int64_t a_len = coupled || (req->m == 1) ? req->n * (int64_t)req->m : req->n;
-        const uint64_t bytes = session_bytes(req->n, a_len);
-        if ((int)srv->sessions.size() >= srv->max_sessions || srv->in_use + bytes > srv->budget)
-            return PGDTO_ERR_BUSY;
-        s = new Session();
-        s->id = req->session;
-        s->n = req->n;
-        s->m = req->m;
-        s->a_len = a_len;
-        s->coupled = coupled;
-        s->bytes = bytes;
-        pgdto_params p = srv->params;
-        p.mode = PGDTO_AUTO;
-        p.eq_mask = req->eq_mask;
-        if (coupled) p.engine = 0;  // coupled rows run on the grid engine (one launch each)
-        pgdto_status st = pgdto_create(&s->h, req->n, req->m, req->seg_offsets, req->lo, req->hi, &p, srv->stream);
-        const size_t nb = (size_t)req->n * sizeof(float);
-        if (st == PGDTO_OK && (cudaMalloc(&s->x, nb) != cudaSuccess || cudaMalloc(&s->g, nb) != cudaSuccess ||
-                               cudaMalloc(&s->A, (size_t)a_len * sizeof(float)) != cudaSuccess ||
-                               cudaMallocHost(&s->slot, sizeof(pgdto_info_slot)) != cudaSuccess ||
-                               cudaEventCreateWithFlags(&s->uploaded, cudaEventDisableTiming) != cudaSuccess))
-            st = PGDTO_ERR_OOM;
-        if (st == PGDTO_OK) st = pgdto_set_state(s->h, nullptr, nullptr, nullptr, 0);
-        if (st != PGDTO_OK) {
-            free_session(s);
-            return st == PGDTO_ERR_OOM ? PGDTO_ERR_BUSY : st;
-        }
-        srv->sessions[s->id] = s;
-        srv->in_use += bytes;
+        pgdto_status cst = create_session(srv, req, &s);
+        if (cst != PGDTO_OK) return cst;
         fresh = true;
     }
     // the session is reserved (busy) while its inputs upload outside the lock, so other
@@ -319,6 +383,30 @@ extern "C" pgdto_status pgdto_submit(pgdto_server* srv, const pgdto_request* req
     *ticket = r.ticket;
     lock.unlock();
     srv->cv.notify_one();
+    return PGDTO_OK;
+}
+
+extern "C" pgdto_status pgdto_server_open(pgdto_server* srv, const pgdto_request* req) {
+    if (!srv || !req || !req->x0 || req->n < 1 || req->m < 1 || req->m > 4) return PGDTO_ERR_ARG;
+    std::unique_lock<std::mutex> lock(srv->mu);
+    if (srv->sessions.count(req->session)) return PGDTO_ERR_ARG;
+    Session* s = nullptr;
+    pgdto_status st = create_session(srv, req, &s);
+    if (st != PGDTO_OK) return st;
+    s->busy = true;  // reserved while the design uploads outside the lock
+    lock.unlock();
+    cudaError_t e = cudaMemcpyAsync(s->x, req->x0, (size_t)s->n * sizeof(float), cudaMemcpyHostToDevice, srv->copy);
+    if (e == cudaSuccess) e = cudaEventRecord(s->uploaded, srv->copy);
+    if (e == cudaSuccess) e = cudaEventSynchronize(s->uploaded);
+    lock.lock();
+    s->busy = false;
+    if (e != cudaSuccess) {
+        srv->in_use -= s->bytes;
+        srv->sessions.erase(s->id);
+        lock.unlock();
+        free_session(s);
+        return PGDTO_ERR_CUDA;
+    }
     return PGDTO_OK;
 }
 
@@ -395,10 +483,16 @@ extern "C" void pgdto_server_destroy(pgdto_server* srv) {
     }
     srv->cv.notify_all();
     if (srv->worker.joinable()) srv->worker.join();
+    {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        srv->fin_stop = true;
+    }
+    srv->cv_fin.notify_all();
+    if (srv->finisher.joinable()) srv->finisher.join();
     cudaStreamSynchronize(srv->stream);
     for (auto& kv : srv->sessions) free_session(kv.second);
     srv->sessions.clear();
-    for (cudaEvent_t e : srv->unit_done) cudaEventDestroy(e);
+    for (cudaEvent_t e : srv->all_events) cudaEventDestroy(e);
     cudaStreamDestroy(srv->copy);
     cudaStreamDestroy(srv->dtoh);
     delete srv;

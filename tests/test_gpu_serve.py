@@ -203,3 +203,84 @@ def test_served_equality_session_equals_a_handle(dev):
     assert st == 0 and info1.lambda_[0] < 0.0
     assert np.array_equal(x.cpu().numpy(), out)
     assert info.lambda_[0] == info1.lambda_[0]
+
+
+def test_large_coupled_session_in_the_mix_equals_its_run_alone(dev):
+    """A coupled session of more than 2^20 variables (four rows) served together with the
+    small sessions: its steps equal the same steps run alone through a handle (the same
+    grid-engine kernel, bit for bit), and its first step matches the oracle."""
+    import torch
+    from paper_2511_13905_gb300 import binding
+    steps = 2
+    big = {"id": 9, "n": (1 << 20) + 3, "m": 4, "mode": "coupled", "seed": 19}
+    sess = _sessions() + [(big, inputs.request_problem(big))]
+    srv = binding.Server(budget_bytes=16 << 30, max_sessions=64)
+    xs = {r["id"]: p["x"].copy() for r, p in sess}
+    served = {}
+    first = None
+    for k in range(steps):
+        tickets = {}
+        for r, p in sess:
+            g, gval = _grads(p, xs[r["id"]], k)
+            if k == 0 and r["id"] == big["id"]:
+                first = (g, gval)
+            out = np.empty(p["n"], np.float32)
+            st, t = srv.submit(r["id"], p["n"], p["m"], g, np.ascontiguousarray(p["A"]), gval, p["G"], out,
+                               x0=p["x"] if k == 0 else None, seg=p.get("seg"), close=(k == steps - 1))
+            assert st == binding.PGDTO_OK
+            tickets[r["id"]] = (t, out)
+        for rid, (t, out) in tickets.items():
+            done, info = _wait(srv, t)
+            assert done == binding.PGDTO_OK, (rid, done)
+            xs[rid] = out
+            served[(rid, k)] = (out.copy(), list(info.lambda_))
+    srv.close()
+    p = sess[-1][1]
+    h = binding.Handle(p["n"], p["m"], engine=1)
+    h.set_state(None, None, None, 0)
+    x = torch.from_numpy(p["x"].copy()).to(dev)
+    A = torch.from_numpy(np.ascontiguousarray(p["A"])).to(dev)
+    xh = p["x"].copy()
+    for k in range(steps):
+        g, gval = _grads(p, xh, k)
+        st, info = h.step(x, torch.from_numpy(g).to(dev), A, gval, p["G"])
+        assert st == 0
+        xh = x.cpu().numpy()
+        out, lam = served[(big["id"], k)]
+        assert np.array_equal(xh, out), k
+        assert lam == list(info.lambda_)
+    h.close()
+    g, gval = first
+    ref = oracle_step(p["x"], p["x"], g, np.zeros(p["n"]), np.zeros(p["n"]), p["A"], gval, p["G"], 0,
+                      mode="coupled")
+    out, lam = served[(big["id"], 0)]
+    err = parity_errors(out, lam[:4], ref["x_new"], ref["lam"], p["A"], ref["b"], C, 0.0, 1.0)
+    print("large coupled session, first step vs oracle:", {k: err[k] for k in ("lam_rel", "x_abs", "viol_rel")})
+    assert err["lam_rel"] <= 1e-6 and err["x_abs"] <= 1e-6 and err["viol_rel"] <= 1e-6, err
+
+
+def test_open_then_submit_equals_a_first_submit(dev):
+    """pgdto_server_open admits a session and uploads its design without a step; the first
+    submit then needs no x0 and gives the same step as a session opened by its first submit.
+    Opening twice is an argument error, and the budget applies at open."""
+    from paper_2511_13905_gb300 import binding
+    r, p = _sessions()[1]
+    g, gval = _grads(p, p["x"], 0)
+    A = np.ascontiguousarray(p["A"])
+    srv = binding.Server(budget_bytes=4 << 30, max_sessions=8)
+    assert srv.open(1, p["n"], p["m"], p["x"], seg=p.get("seg")) == binding.PGDTO_OK
+    assert srv.open(1, p["n"], p["m"], p["x"], seg=p.get("seg")) == binding.PGDTO_ERR_ARG
+    out1 = np.empty(p["n"], np.float32)
+    st, t1 = srv.submit(1, p["n"], p["m"], g, A, gval, p["G"], out1, seg=p.get("seg"))
+    assert st == binding.PGDTO_OK
+    out2 = np.empty(p["n"], np.float32)
+    st, t2 = srv.submit(2, p["n"], p["m"], g, A, gval, p["G"], out2, x0=p["x"], seg=p.get("seg"))
+    assert st == binding.PGDTO_OK
+    for t in (t1, t2):
+        st, done, _, _ = srv.wait(t)
+        assert st == binding.PGDTO_OK and done == binding.PGDTO_OK
+    assert np.array_equal(out1, out2)
+    srv.close()
+    tiny = binding.Server(budget_bytes=1 << 20, max_sessions=4)
+    assert tiny.open(3, p["n"], p["m"], p["x"], seg=p.get("seg")) == binding.PGDTO_ERR_BUSY
+    tiny.close()
