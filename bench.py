@@ -420,6 +420,12 @@ def run_batched(args, local_rank=0):
     def T(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
 
+    # the library's autotuner picks the cluster engine's block share for B problems of this
+    # n (synthetic problems of its own, timed before and outside this workload's timing);
+    # the handles below, batched and plain alike, are created under its choice
+    st, tuned, tuned_ms = binding.autotune_batch(n, B)
+    if st != binding.PGDTO_OK:
+        raise RuntimeError("pgdto_autotune_batch failed: %s" % st)
     hs = [binding.Handle(c["n"], 1) for c in cfgs]
     x0 = [T(c["x"]) for c in cfgs]
     xs = [t.clone() for t in x0]
@@ -480,7 +486,12 @@ def run_batched(args, local_rank=0):
     peak, _ = peaks()
     for h in hs:
         h.close()
+    binding.autotune_reset()
     res = {"workload": "%d x volume_2d_256x128 (n=%d, m=1, one step each)" % (B, n),
+           "autotune": {"cluster_elems": tuned, "median_ms_synthetic": tuned_ms,
+                        "candidates": [1024, 2048, 4096, 8192],
+                        "how": "pgdto_autotune_batch(n, B): 3 + 5 batched steps of B synthetic problems per "
+                               "candidate share, lowest median kept"},
             "batched": {"ms": t_b, "steps_per_s": B / (t_b / 1e3), "launches": launches_b,
                         "passes_per_instance": passes_b / B,
                         "roofline": {"bound": "hbm", "achieved": bytes_b / (t_b / 1e3) / 1e9, "peak": peak,

@@ -92,9 +92,10 @@ typedef struct {
     int cluster_elems;      /* cluster engine: variables per thread block; a problem's cluster
                                has ceil(n / cluster_elems) blocks rounded up to a power of two,
                                at most 16.  It depends on n alone, so a problem's result is the
-                               same alone and in any batch.  0 = 8192 (the cluster engine runs
-                               two 256-thread blocks per SM; 8192 variables of a block fit its
-                               share of shared memory) */
+                               same alone and in any batch.  0 = the share pgdto_autotune_batch
+                               chose for this device and n's bucket, else 8192 (the cluster
+                               engine runs two 256-thread blocks per SM; 8192 variables of a
+                               block fit its share of shared memory) */
     int eq_mask;            /* bit j set: row j is an equality g_j(x) = G_j (Sec. 3.2.4), always
                                active, lambda_j of either sign, and its violation for the
                                fallback rule is |g_j - G_j|; bits at or above m must be 0 */
@@ -218,6 +219,28 @@ pgdto_status pgdto_step_many(int count, pgdto_handle* const* hs, float* const* x
 pgdto_status pgdto_project_many(int count, pgdto_handle* const* hs, const float* const* z,
                                 const float* const* A, const double* b, float* const* x_out,
                                 double* lambda_out, pgdto_info* infos);
+
+/*
+ * pgdto_autotune_batch -- choose, on the current device, the cluster engine's block share
+ * for batches of `count` single-row problems of n variables.  It builds that batch from a
+ * counter-based hash on the device (its own buffers and handles, freed before it returns),
+ * times 3 + 5 batched steps (pgdto_step_many, from the same starting state each time) for
+ * each share in {1024, 2048, 4096, 8192} with CUDA events on `cuda_stream`, and records the
+ * share with the lowest median time for this device and n's power-of-two bucket
+ * (2^(b-1) < n <= 2^b).  Handles created afterwards with params.cluster_elems = 0 and n in
+ * that bucket take it; handles that exist keep theirs, so a problem's result is the same
+ * alone and in any batch only among handles created under the same table.
+ *   n: 1 .. 131072 (the cluster engine's range under engine = auto); count: 1 .. 4096.
+ *   best_out, ms_out: host, the share chosen and its median batched-step time in ms, or NULL.
+ * Synchronises `cuda_stream`.  Errors: PGDTO_ERR_ARG for sizes outside those ranges,
+ * PGDTO_ERR_OOM / PGDTO_ERR_CUDA from the device; the table is left as it was.
+ * Not thread-safe against concurrent calls on one device.  The paper has no counterpart.
+ */
+pgdto_status pgdto_autotune_batch(int64_t n, int count, int* best_out, double* ms_out, void* cuda_stream);
+
+/* Forget every share pgdto_autotune_batch recorded, on every device (handles created
+ * afterwards use params.cluster_elems, or 8192 when it is 0). */
+void pgdto_autotune_reset(void);
 
 /* ------------------------------------------------------------------ serving
  * A server runs optimizer steps for many concurrent design sessions with continuous

@@ -106,6 +106,9 @@ def load(path=None):
                                                  ctypes.POINTER(Info), P]),
         "pgdto_noalloc_set_test_fault": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
         "pgdto_probe_read": (ctypes.c_int, [P, ctypes.c_int64, P, ctypes.c_int, P]),
+        "pgdto_autotune_batch": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                ctypes.POINTER(ctypes.c_double), P]),
+        "pgdto_autotune_reset": (None, []),
         "pgdto_version": (ctypes.c_char_p, []),
         "pgdto_server_create": (ctypes.c_int, [ctypes.POINTER(H), ctypes.c_uint64, ctypes.c_int,
                                                ctypes.POINTER(Params), P]),
@@ -270,6 +273,19 @@ def noalloc_set_test_fault(fault_inject, timeout_ms):
 def probe_read(buf, out, blocks, stream=None):
     """pgdto_probe_read: one streaming read of the device tensor buf (measurement tooling)."""
     return load().pgdto_probe_read(_dptr(buf), int(buf.numel()), _dptr(out), int(blocks), _stream_ptr(stream))
+
+
+def autotune_batch(n, count, stream=None):
+    """pgdto_autotune_batch: (status, chosen cluster_elems, its median batched-step ms)."""
+    best = ctypes.c_int(0)
+    ms = ctypes.c_double(0.0)
+    st = load().pgdto_autotune_batch(int(n), int(count), ctypes.byref(best), ctypes.byref(ms), _stream_ptr(stream))
+    return st, best.value, ms.value
+
+
+def autotune_reset():
+    """pgdto_autotune_reset: forget the recorded shares on every device."""
+    load().pgdto_autotune_reset()
 
 
 def _ptrs(ts):

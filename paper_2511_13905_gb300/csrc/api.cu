@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -62,6 +63,35 @@ struct pgdto_handle {
 };
 
 static const int64_t kClusterElemsDefault = 8192;
+
+// Cluster-engine block shares chosen by pgdto_autotune_batch, per device and per
+// power-of-two bucket of n (bucket b holds 2^(b-1) < n <= 2^b); 0 = not tuned.  Handles
+// created with params.cluster_elems = 0 take the entry of their device and bucket.
+static std::mutex g_tune_mu;
+static int g_tuned[64][64];
+
+static int n_bucket(int64_t n) {
+    int b = 0;
+    while (b < 63 && (int64_t(1) << b) < n) ++b;
+    return b;
+}
+
+int pgdto_tuned_cluster_elems(int device, int64_t n) {
+    if (device < 0 || device >= 64 || n < 1) return 0;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tuned[device][n_bucket(n)];
+}
+
+void pgdto_set_tuned_cluster_elems(int device, int64_t n, int elems) {
+    if (device < 0 || device >= 64 || n < 1 || elems < 0) return;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[device][n_bucket(n)] = elems;
+}
+
+extern "C" void pgdto_autotune_reset(void) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    memset(g_tuned, 0, sizeof(g_tuned));
+}
 
 // Residency floats per array for a problem split over nb blocks (0 when a block's share
 // does not fit the shared memory).
@@ -229,7 +259,10 @@ extern "C" pgdto_status pgdto_create(pgdto_handle** out, int64_t n, int m, const
     if (mode != PGDTO_COUPLED) {
         int s_max = 0;
         seg_cluster_shape(h->device, &s_max, &h->cl_max);
-        h->cl_size = cluster_size_for(n, p.cluster_elems > 0 ? p.cluster_elems : kClusterElemsDefault, s_max);
+        int64_t share = p.cluster_elems;
+        if (share == 0) share = pgdto_tuned_cluster_elems(h->device, n);
+        if (share == 0) share = kClusterElemsDefault;
+        h->cl_size = cluster_size_for(n, share, s_max);
         h->res_grid = res_elems(h->seg, m, h->blocks, kResMaxElems);
         h->res_cluster = res_elems(h->seg, m, h->cl_size, kResMaxElemsCluster);
         if (p.engine == 2 || (p.engine == 0 && n <= kClusterMaxN)) h->engine = 2;

@@ -1,5 +1,6 @@
-// handle_internal.h -- entry points shared by api.cu and serve.cu that are not part of the
-// public C ABI: a step report read without synchronising the handle's stream.
+// handle_internal.h -- entry points shared by api.cu, serve.cu and tune.cu that are not part
+// of the public C ABI: a step report read without synchronising the handle's stream, and
+// the table of tuned cluster-engine block shares.
 #pragma once
 
 #include "../../include/pgdto.h"
@@ -23,3 +24,8 @@ pgdto_status pgdto_info_collect(pgdto_handle* h, const pgdto_info_slot* slot, pg
 // 1 when the handle's steps run on the grid engine (every SM on the one problem), 0 when
 // they run on one thread-block cluster; the server batches only the latter.
 int pgdto_handle_whole_gpu(const pgdto_handle* h);
+
+// The cluster-engine block share pgdto_autotune_batch chose for problems of n variables on
+// `device` (the table is kept per power-of-two bucket of n), or 0 when none was chosen.
+int pgdto_tuned_cluster_elems(int device, int64_t n);
+void pgdto_set_tuned_cluster_elems(int device, int64_t n, int elems);

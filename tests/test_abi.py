@@ -63,3 +63,11 @@ def test_null_handle_calls(lib):
     assert lib.pgdto_kernel_launches(None) == -1
     lib.pgdto_destroy(None)
     assert b"sm_103a" in lib.pgdto_version()
+
+
+@pytest.mark.parametrize("n,count", [(0, 8), (131073, 8), (4096, 0), (4096, 4097)])
+def test_autotune_rejects_sizes_outside_its_range(lib, n, count):
+    best = ctypes.c_int(-1)
+    assert lib.pgdto_autotune_batch(n, count, ctypes.byref(best), None, None) == binding.PGDTO_ERR_ARG
+    assert best.value == -1
+    lib.pgdto_autotune_reset()
