@@ -315,20 +315,37 @@ __device__ bool grid_allreduce_update(GridCtrl* ctrl, Partials* part2, BlockScra
     __syncthreads();
     if (!sc.flag) return false;
     const int lane = tid & 31, warp = tid >> 5, nw = (int)(blockDim.x >> 5);
-    for (int i = warp; i < nv; i += nw) {
-        DF acc = df_zero();
-        for (int b0 = 0; b0 < nb; b0 += 256) {
-            float2 buf[8];
+    // Warp w sums values w, w + nw, ...; it issues the loads of up to kGatherVals values
+    // (kGatherPer blocks per lane each) before adding any, so the round pays the latency of
+    // the partials' reads once rather than once per value.  Lane l adds blocks l, l + 32,
+    // ... in that order and the lanes combine by the same tree for every value.
+    constexpr int kGatherVals = 5, kGatherPer = 5;
+    for (int j0 = 0; j0 * nw < nv; j0 += kGatherVals) {
+        DF acc[kGatherVals];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int b = b0 + lane + 32 * k;
-                buf[k] = b < nb ? __ldcg(&part->v[i][b]) : make_float2(0.0f, 0.0f);
+        for (int j = 0; j < kGatherVals; ++j) acc[j] = df_zero();
+        for (int b0 = 0; b0 < nb; b0 += 32 * kGatherPer) {
+            float2 buf[kGatherVals][kGatherPer];
+#pragma unroll
+            for (int j = 0; j < kGatherVals; ++j) {
+                const int i = warp + nw * (j0 + j);
+#pragma unroll
+                for (int k = 0; k < kGatherPer; ++k) {
+                    const int b = b0 + lane + 32 * k;
+                    buf[j][k] = (i < nv && b < nb) ? __ldcg(&part->v[i][b]) : make_float2(0.0f, 0.0f);
+                }
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) acc = df_add(acc, DF{buf[k].x, buf[k].y});
+            for (int j = 0; j < kGatherVals; ++j)
+#pragma unroll
+                for (int k = 0; k < kGatherPer; ++k) acc[j] = df_add(acc[j], DF{buf[j][k].x, buf[j][k].y});
         }
-        acc = warp_reduce_df(acc);
-        if (lane == 0) sc.tot[i] = acc;
+#pragma unroll
+        for (int j = 0; j < kGatherVals; ++j) {
+            const int i = warp + nw * (j0 + j);
+            const DF r = warp_reduce_df(acc[j]);
+            if (lane == 0 && i < nv) sc.tot[i] = r;
+        }
     }
     for (int i = warp; i < nm; i += nw) {
         float acc = -INFINITY;

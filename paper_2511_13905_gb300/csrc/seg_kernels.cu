@@ -873,32 +873,46 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 acc.init();
                 const float pm = p[kMidPoint];
                 const bool narrow = (p[K - 1] - p[0]) <= 4e-3f * fmaxf(fabsf(p[0]), fabsf(p[K - 1]));
-                auto all_points = [&](float z, float zl, float av) {
+                // w = z - t a at point t: with z_lo added when the pass reads it (hl), else the
+                // FP32 value alone (adding a zero z_lo would cost an instruction per point)
+                auto wat = [&](auto hl, float t, float z, float zl, float av) {
+                    const float w = fmaf(-t, av, z);
+                    if constexpr (decltype(hl)::value) {
+                        return __fadd_rn(w, zl);
+                    } else {
+                        return w;
+                    }
+                };
+                auto all_points = [&](auto hl, float z, float zl, float av) {
                     const float aa = av * av;
 #pragma unroll
                     for (int k = 0; k < K; ++k) {
-                        const float w = __fadd_rn(fmaf(-p[k], av, z), zl);
+                        const float w = wat(hl, p[k], z, zl, av);
                         const float x = clampf(w, lo, hi);  // free exactly when the clip leaves w
                         acc.f[k] = fmaf(av, x, acc.f[k]);
                         acc.f[K + 3 + k] += (x == w) ? aa : 0.0f;
                     }
                 };
-                auto e = [&](float z, float zl, float av) {
+                // In a narrow pass the decided part is branch-free and an element whose state
+                // changes between the extreme points takes every point under a warp vote, so
+                // the every-point code runs only in warps that hold such an element (with a
+                // zero coefficient in the lanes that do not, which adds nothing).
+                auto e = [&](auto hl, float z, float zl, float av) {
                     if (narrow) {
-                        const float w0 = __fadd_rn(fmaf(-p[0], av, z), zl);
-                        const float w1 = __fadd_rn(fmaf(-p[K - 1], av, z), zl);
+                        const float w0 = wat(hl, p[0], z, zl, av);
+                        const float w1 = wat(hl, p[K - 1], z, zl, av);
                         const float wmn = fminf(w0, w1), wmx = fmaxf(w0, w1);
-                        if (wmx < lo || wmn > hi) {
-                            acc.f[K] = fmaf(av, wmx < lo ? lo : hi, acc.f[K]);
-                            return;
-                        }
-                        if (wmn >= lo && wmx <= hi) {
-                            acc.f[K + 1] = fmaf(av, __fadd_rn(fmaf(-pm, av, z), zl), acc.f[K + 1]);
-                            acc.f[K + 2] = fmaf(av, av, acc.f[K + 2]);
-                            return;
-                        }
+                        const bool sat = wmx < lo || wmn > hi;
+                        const bool fre = wmn >= lo && wmx <= hi;
+                        acc.f[K] = fmaf(sat ? av : 0.0f, wmx < lo ? lo : hi, acc.f[K]);
+                        const float af = fre ? av : 0.0f;
+                        acc.f[K + 1] = fmaf(af, wat(hl, pm, z, zl, av), acc.f[K + 1]);
+                        acc.f[K + 2] = fmaf(af, av, acc.f[K + 2]);
+                        const bool und = !sat && !fre;
+                        if (__any_sync(__activemask(), und)) all_points(hl, z, zl, und ? av : 0.0f);
+                        return;
                     }
-                    all_points(z, zl, av);
+                    all_points(hl, z, zl, av);
                 };
                 auto run = [&](auto rc, auto lc) {
                     constexpr bool R = decltype(rc)::value;
@@ -906,19 +920,20 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                     struct P4 {
                         float4 z, zl, av;
                     };
+                    const BoolC<HL> hl;
                     auto use4 = [&](const P4& q) {
-                        e(q.z.x, q.zl.x, q.av.x);
-                        e(q.z.y, q.zl.y, q.av.y);
-                        e(q.z.z, q.zl.z, q.av.z);
-                        e(q.z.w, q.zl.w, q.av.w);
+                        e(hl, q.z.x, q.zl.x, q.av.x);
+                        e(hl, q.z.y, q.zl.y, q.av.y);
+                        e(hl, q.z.z, q.zl.z, q.av.z);
+                        e(hl, q.z.w, q.zl.w, q.av.w);
                         acc.tick();
                     };
                     auto use1 = [&](int64_t i) {
                         if constexpr (R) {
                             const int q = off + (int)(i - rb);
-                            e(smz[q], HL ? sml[q] : 0.0f, sma[q]);
+                            e(hl, smz[q], HL ? sml[q] : 0.0f, sma[q]);
                         } else {
-                            e(zsrc[i], HL ? a.zlo[i] : 0.0f, a.A[i]);
+                            e(hl, zsrc[i], HL ? a.zlo[i] : 0.0f, a.A[i]);
                         }
                         acc.tick();
                     };
