@@ -347,11 +347,33 @@ __device__ bool grid_allreduce_update(GridCtrl* ctrl, Partials* part2, BlockScra
             if (lane == 0 && i < nv) sc.tot[i] = r;
         }
     }
-    for (int i = warp; i < nm; i += nw) {
-        float acc = -INFINITY;
-        for (int b = lane; b < nb; b += 32) acc = fmaxf(acc, __ldcg(&part->mx[i][b]));
-        acc = warp_reduce_max(acc);
-        if (lane == 0) sc.totmax[i] = acc;
+    // maxima: the same batching (a maximum does not depend on the order)
+    for (int j0 = 0; j0 * nw < nm; j0 += kGatherVals) {
+        float acc[kGatherVals];
+#pragma unroll
+        for (int j = 0; j < kGatherVals; ++j) acc[j] = -INFINITY;
+        for (int b0 = 0; b0 < nb; b0 += 32 * kGatherPer) {
+            float buf[kGatherVals][kGatherPer];
+#pragma unroll
+            for (int j = 0; j < kGatherVals; ++j) {
+                const int i = warp + nw * (j0 + j);
+#pragma unroll
+                for (int k = 0; k < kGatherPer; ++k) {
+                    const int b = b0 + lane + 32 * k;
+                    buf[j][k] = (i < nm && b < nb) ? __ldcg(&part->mx[i][b]) : -INFINITY;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kGatherVals; ++j)
+#pragma unroll
+                for (int k = 0; k < kGatherPer; ++k) acc[j] = fmaxf(acc[j], buf[j][k]);
+        }
+#pragma unroll
+        for (int j = 0; j < kGatherVals; ++j) {
+            const int i = warp + nw * (j0 + j);
+            const float r = warp_reduce_max(acc[j]);
+            if (lane == 0 && i < nm) sc.totmax[i] = r;
+        }
     }
     __syncthreads();
     if (tid < 32) {
