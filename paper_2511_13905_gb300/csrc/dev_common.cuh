@@ -272,9 +272,13 @@ __device__ __forceinline__ void block_reduce(const DF (&v)[NV], const float* mx,
 // there, after reading this round's partials, so it is never more than one round ahead.
 // Returns false if the wait was abandoned (timeout or abort); the caller must then return.
 // Block 0 appends the round's completion time to ctrl->trace.
-template <class Update>
-__device__ bool grid_allreduce_update(GridCtrl* ctrl, Partials* part2, BlockScratch& sc, int nv, int nm,
-                                      long long timeout_cycles, Update&& update) {
+//
+// The part that is the same in every round (publish, arrive, wait, gather) is one
+// out-of-line function: a step runs several rounds, and each inlined copy of this code
+// would be fetched into the instruction cache cold (the caller's L2 traffic between steps
+// evicts the kernel's code), where one shared copy is fetched once per launch.
+static __device__ __noinline__ bool grid_round_gather(GridCtrl* ctrl, Partials* part2, BlockScratch& sc, int nv,
+                                                     int nm, long long timeout_cycles) {
     const int tid = threadIdx.x;
     const int nb = gridDim.x;
     Partials* part = part2 + (sc.gen & 1u);
@@ -376,6 +380,14 @@ __device__ bool grid_allreduce_update(GridCtrl* ctrl, Partials* part2, BlockScra
         }
     }
     __syncthreads();
+    return true;
+}
+
+template <class Update>
+__device__ bool grid_allreduce_update(GridCtrl* ctrl, Partials* part2, BlockScratch& sc, int nv, int nm,
+                                      long long timeout_cycles, Update&& update) {
+    if (!grid_round_gather(ctrl, part2, sc, nv, nm, timeout_cycles)) return false;
+    const int tid = threadIdx.x;
     if (tid < 32) {
         update(sc);
         __syncwarp();

@@ -476,11 +476,15 @@ __device__ __forceinline__ float next_point_f(int lane, float L, float rL, float
 // ...]: C (a x bound over the elements clipped at every point), AZ (a w_m over those free
 // at every point, w_m their value at the reference point t_m = pts[j][kMidPoint]) and AA
 // (a^2 over the same), and each point adds C + AZ - (t_k - t_m) AA and AA back.
+// Out of line: a step calls it from more than one place (the warm-start ladder's round and
+// the later passes, the coupled rows' stage 1 and line search), and one copy of its code
+// is fetched into the instruction cache once per launch instead of once per call site.
 constexpr int kMidPoint = 3;
 
 template <class Bcast, bool CMP = false, bool DEC = false>
-__device__ void search_pass_update(const BlockScratch& sc, int base, volatile RowState* rows, volatile Bcast* bc,
-                                   int nsearch, double tol_lambda, int max_passes, unsigned held = 0u) {
+__device__ __noinline__ void search_pass_update(const BlockScratch& sc, int base, volatile RowState* rows,
+                                                volatile Bcast* bc, int nsearch, double tol_lambda, int max_passes,
+                                                unsigned held = 0u) {
     static_assert(!(CMP && DEC), "one pass layout at a time");
     constexpr int stride = CMP ? 2 * K + 4 : (DEC ? 2 * K + 3 : 2 * K);
     const int lane = threadIdx.x, j = lane >> 3, k = lane & 7, g0 = lane & ~7;
