@@ -73,7 +73,7 @@ typedef struct {
     double c1;              /* Armijo constant of the Newton line search, 1e-4 (App. A.3.3) */
     double c2;              /* curvature constant, 0.9 (App. A.3.3; recorded, not enforced) */
     double tol_lambda;      /* relative width at which a dual root search stops, 1e-10; a row
-                               search also stops once both Newton predictions agree to 100
+                               search also stops once both Newton predictions agree to 1000
                                tol_lambda and to 1e-8 / max_i |a_i| (the final pass takes one
                                exact Newton step from there, and runs again if that step moves
                                lam by more than 1e-7 lam or some free x_i by more than 1e-7) */

@@ -849,7 +849,7 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
                         rowsum(zz[q], av, 0.0f);
                     }
                 } else {
-                    float4 x = LD4L2(a.x, v), g = LD4L2(a.g, v);
+                    float4 x = LD4(a.x, v), g = LD4(a.g, v);
                     float4 dp = first ? make_float4(0.f, 0.f, 0.f, 0.f) : LD4(a.d_prev, v);
                     float4 d, zh, zl;
                     const float xx[4] = {x.x, x.y, x.z, x.w}, gg[4] = {g.x, g.y, g.z, g.w};
@@ -1211,7 +1211,7 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
             [&](int64_t v) {
                 float4 z = LD4(zh_src, v);
                 float4 zl = has_lo ? LD4(a.zlo, v) : make_float4(0.f, 0.f, 0.f, 0.f);
-                float4 x = a.proj ? make_float4(0.f, 0.f, 0.f, 0.f) : LD4L2(a.x, v);
+                float4 x = a.proj ? make_float4(0.f, 0.f, 0.f, 0.f) : LD4(a.x, v);
                 float4 A4[M];
 #pragma unroll
                 for (int j = 0; j < M; ++j) A4[j] = LD4(a.A + (int64_t)j * n, v);
@@ -1225,7 +1225,7 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
                     for (int j = 0; j < M; ++j) av[j] = reinterpret_cast<const float*>(&A4[j])[q];
                     o[q] = e(xx[q], zz[q], l4[q], av);
                 }
-                reinterpret_cast<float4*>(out)[v] = make_float4(o[0], o[1], o[2], o[3]);
+                __stcs(reinterpret_cast<float4*>(out) + v, make_float4(o[0], o[1], o[2], o[3]));
                 acc.tick();
             },
             [&](int64_t i) {

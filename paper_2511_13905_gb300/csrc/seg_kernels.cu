@@ -453,6 +453,10 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
     }
 
     // ---------------------------------------------------------------- phase B
+    // Cache policy: a stream read or written for the last time in the step is evict-first
+    // (LD4, __stcs); the trial point z_hi and the coefficients, which the passes read
+    // again, keep normal priority.  On a problem larger than L2 this keeps the kernel's
+    // code and the round partials resident while hundreds of MB stream past.
     // Residency: when this CTA's share fits the dynamic shared memory, phase B keeps the
     // trial point (z_hi, z_lo) and the coefficients there and phases C and D read them
     // back from it instead of global memory (z is then not written to global memory).
@@ -570,7 +574,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                 for_chunk_x2<VEC>(
                     cb, ce,
                     [&](int64_t v) {
-                        return B4{v, LD4L2(a.x, v), LD4L2(a.g, v), LD4L2(a.A, v),
+                        return B4{v, LD4(a.x, v), LD4(a.g, v), LD4L2(a.A, v),
                                   first ? make_float4(0.f, 0.f, 0.f, 0.f) : LD4(a.d_prev, v)};
                     },
                     [&](const B4& q) {
@@ -589,7 +593,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                             reinterpret_cast<float4*>(sma)[q] = av;
                         } else {
                             reinterpret_cast<float4*>(a.z)[v] = zh;
-                            reinterpret_cast<float4*>(a.zlo)[v] = zl;
+                            __stcs(reinterpret_cast<float4*>(a.zlo) + v, zl);
                         }
                         __stcs(reinterpret_cast<float4*>(a.x_prev) + v, x);
                         __stcs(reinterpret_cast<float4*>(a.g_prev) + v, g);
@@ -1097,15 +1101,15 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                             z = reinterpret_cast<const float4*>(smz)[q];
                             av = reinterpret_cast<const float4*>(sma)[q];
                         } else {
-                            z = LD4L2(a.z_in, v);
-                            av = LD4L2(a.A, v);
+                            z = LD4(a.z_in, v);
+                            av = LD4(a.A, v);
                         }
                         float4 o;
                         o.x = e(0.0f, z.x, 0.0f, av.x);
                         o.y = e(0.0f, z.y, 0.0f, av.y);
                         o.z = e(0.0f, z.z, 0.0f, av.z);
                         o.w = e(0.0f, z.w, 0.0f, av.w);
-                        reinterpret_cast<float4*>(a.x_out)[v] = o;
+                        __stcs(reinterpret_cast<float4*>(a.x_out) + v, o);
                         if (++cnt == kFoldEvery) {
                             fold();
                             cnt = 0;
@@ -1125,7 +1129,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                     [&](int64_t v) {
                         D4 q;
                         q.v = v;
-                        q.x = LD4L2(a.x_prev, v);
+                        q.x = LD4(a.x_prev, v);
                         if (res) {
                             const int k = (off >> 2) + (int)(v - (rb >> 2));
                             q.zh = reinterpret_cast<const float4*>(smz)[k];
@@ -1144,7 +1148,7 @@ __device__ void seg_body(const SegArgs& a, const Sync& sy, BlockScratch& sc, Seg
                         o.y = e(q.x.y, q.zh.y, q.zl.y, q.av.y);
                         o.z = e(q.x.z, q.zh.z, q.zl.z, q.av.z);
                         o.w = e(q.x.w, q.zh.w, q.zl.w, q.av.w);
-                        reinterpret_cast<float4*>(a.x)[q.v] = o;
+                        __stcs(reinterpret_cast<float4*>(a.x) + q.v, o);
                         if (++cnt == kFoldEvery) {
                             fold();
                             cnt = 0;

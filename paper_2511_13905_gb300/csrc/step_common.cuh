@@ -553,14 +553,15 @@ __device__ __noinline__ void search_pass_update(const BlockScratch& sc, int base
     const float w = wd.hi;
     // tolerances relative to the bracket's magnitude (a negative bracket ends at 0).  Where
     // the row's largest |a| is known the search may also stop once the two Newton
-    // predictions agree to 100 tol_lambda of the root and to 1e-8 / max|a|: the final pass
-    // then takes one exact Newton step from their midpoint, which (at the default
-    // tol_lambda) moves x by less than 1e-7 and lam by less than 1e-7 of itself, so it needs
-    // no further pass (its own test runs it again if it does)
+    // predictions agree to 1000 tol_lambda of the root and to 1e-8 / max|a|: the final pass
+    // then takes one exact Newton step from their midpoint, which is within half that gap of
+    // the root, so (at the default tol_lambda) the step moves x by less than 1e-8 and lam by
+    // less than 5e-8 of itself, inside the final pass's acceptance window (1e-7 for both);
+    // its own test runs the pass again if it is not
     const float mag = fmaxf(fabsf(L), fabsf(H));
     const float tol = (float)tol_lambda * mag;
     const float am = rows[jj].famax;
-    const float tolg = am > 0.0f ? fmaxf(tol, fminf(100.0f * tol, __fdividef(1e-8f, am))) : tol;
+    const float tolg = am > 0.0f ? fmaxf(tol, fminf(1000.0f * tol, __fdividef(1e-8f, am))) : tol;
     bool done = false;
     int how = 2;
     if (kH >= 0 && rH.hi == 0.0f && rH.lo == 0.0f) done = true;
