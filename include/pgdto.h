@@ -104,6 +104,12 @@ typedef struct {
                                fixes are summed once and later passes visit the rest (shares that
                                stream from global memory only); 0 (default) = every pass visits
                                every element, which measured faster on the shipped workloads */
+    int stage1;             /* coupled rows, cold start: 1 = Alg. 2's stage 1 first (the m
+                               single-row searches, then the test of each candidate against
+                               every row); 0 (default) = stage 2's Newton iteration from
+                               lam = 0.  Both reach the same optimum; on the 4-row workload
+                               stage 1 cost more passes than it saved.  A warm start (the
+                               handle's previous step) begins at the previous lam either way */
 } pgdto_params;
 
 /* Per-call report. */

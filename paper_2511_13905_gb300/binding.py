@@ -35,7 +35,7 @@ class Params(ctypes.Structure):
                 ("tol_lambda", ctypes.c_double), ("t_warmup", ctypes.c_int), ("maxiter_newton", ctypes.c_int),
                 ("max_passes", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int), ("mode", ctypes.c_int),
                 ("fault_inject", ctypes.c_int), ("engine", ctypes.c_int), ("cluster_elems", ctypes.c_int),
-                ("eq_mask", ctypes.c_int), ("compaction", ctypes.c_int)]
+                ("eq_mask", ctypes.c_int), ("compaction", ctypes.c_int), ("stage1", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

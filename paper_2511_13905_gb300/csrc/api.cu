@@ -148,6 +148,7 @@ extern "C" pgdto_status pgdto_params_default(pgdto_params* p) {
     p->cluster_elems = 0;
     p->eq_mask = 0;
     p->compaction = 0;
+    p->stage1 = 0;
     return PGDTO_OK;
 }
 
@@ -183,7 +184,8 @@ static bool params_ok(const pgdto_params& p) {
            p.eps_alpha >= 0 && p.tol_lambda > 0 && p.tol_lambda < 1e-2 && p.t_warmup >= 0 &&
            p.maxiter_newton >= 1 && p.max_passes >= 1 && p.max_passes <= 100000 && p.barrier_timeout_ms >= 1 &&
            (p.fault_inject == 0 || p.fault_inject == 1) && p.engine >= 0 && p.engine <= 2 && p.cluster_elems >= 0 &&
-           p.eq_mask >= 0 && p.eq_mask < 16 && (p.compaction == 0 || p.compaction == 1);
+           p.eq_mask >= 0 && p.eq_mask < 16 && (p.compaction == 0 || p.compaction == 1) &&
+           (p.stage1 == 0 || p.stage1 == 1);
 }
 
 extern "C" pgdto_status pgdto_create(pgdto_handle** out, int64_t n, int m, const int64_t* seg_offsets, float lo,
@@ -501,6 +503,7 @@ static pgdto_status launch(pgdto_handle* h, bool proj, float* x, const float* g,
         a.timeout_cycles = h->timeout_cycles;
         a.ws = (CoupledWork*)h->work;
         a.eq_mask = h->p.eq_mask;
+        a.stage1 = h->p.stage1;
         // warm start from the previous step's multipliers, still in the handle's report
         a.lam_prev = (!proj && h->warm)
                          ? reinterpret_cast<const double*>(reinterpret_cast<const char*>(h->dev_info) +

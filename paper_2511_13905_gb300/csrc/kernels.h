@@ -174,6 +174,7 @@ struct CoupledArgs {
     CoupledWork* ws;
     int eq_mask;          // bit j: row j is an equality (always active, lam_j of either sign)
     const double* lam_prev;  // warm start: the previous step's lam (device), or null
+    int stage1;              // cold start: 1 = Alg. 2's stage 1 first, 0 = Newton from lam = 0
 };
 
 // A double as an unevaluated sum hi + lo of two floats (host side).

@@ -27,6 +27,7 @@ def test_params_default_are_the_papers(lib):
     assert p.C == 1e12 and p.alpha_max == 1e2 and p.tol_B == 1e-8 and p.tol_N == 1e-6
     assert p.alpha_fallback == 0.2 and p.eps_alpha == 1e-6 and p.t_warmup == 50 and p.omega == 1.0
     assert p.c1 == 1e-4 and p.c2 == 0.9
+    assert p.stage1 == 0 and p.compaction == 0 and p.cluster_elems == 0
     assert lib.pgdto_params_default(None) == binding.PGDTO_ERR_ARG
 
 
@@ -53,6 +54,8 @@ def test_bad_params_rejected(lib):
     p = binding.params_default(C=-1.0)
     assert lib.pgdto_create(ctypes.byref(h), 10, 1, None, 0.0, 1.0, ctypes.byref(p), None) == binding.PGDTO_ERR_ARG
     p = binding.params_default(max_passes=0)
+    assert lib.pgdto_create(ctypes.byref(h), 10, 1, None, 0.0, 1.0, ctypes.byref(p), None) == binding.PGDTO_ERR_ARG
+    p = binding.params_default(stage1=2)
     assert lib.pgdto_create(ctypes.byref(h), 10, 1, None, 0.0, 1.0, ctypes.byref(p), None) == binding.PGDTO_ERR_ARG
 
 

@@ -1,5 +1,6 @@
-"""Parity of the coupled-row CUDA path (Alg. 2: single-row candidates, then Newton on the
-m x m Jacobian) with the FP64 oracle's exact optimum, through the C ABI."""
+"""Parity of the coupled-row CUDA path with the FP64 oracle's exact optimum, through the C
+ABI: stage 2's Newton iteration on the m x m Jacobian from lam = 0 (the default), and with
+Alg. 2's stage 1 (single-row candidates) first (params.stage1 = 1)."""
 
 import json
 import os
@@ -39,11 +40,11 @@ def check(err, what=""):
     assert not bad, "%s parity: %s (all: %s)" % (what, bad, {k: err[k] for k in TOL})
 
 
-def run_project(dev, z, A, b, lo=0.0, hi=1.0):
+def run_project(dev, z, A, b, lo=0.0, hi=1.0, stage1=0):
     import torch
     from paper_2511_13905_gb300 import binding
     m, n = A.shape
-    h = binding.Handle(n, m, lo=lo, hi=hi, mode="coupled")
+    h = binding.Handle(n, m, lo=lo, hi=hi, mode="coupled", stage1=stage1)
     zt, At = T(z, dev), T(A, dev)
     xt = torch.empty_like(zt)
     st, lam, info = h.project(zt, At, b, xt)
@@ -70,12 +71,13 @@ def coupled_problem(n, m, seed, feasible=True):
     return z.astype(np.float32), A.astype(np.float32), b
 
 
+@pytest.mark.parametrize("stage1", [0, 1])
 @pytest.mark.parametrize("n,m,seed,feasible", [
     (1000, 2, 1, True), (4096, 3, 2, True), (65536, 4, 3, True), (100003, 4, 4, True),
     (20000, 2, 5, False), (50000, 4, 6, False), (1 << 20, 4, 7, True)])
-def test_project_coupled(dev, n, m, seed, feasible):
+def test_project_coupled(dev, n, m, seed, feasible, stage1):
     z, A, b = coupled_problem(n, m, seed, feasible)
-    st, lam, x, info = run_project(dev, z, A, b)
+    st, lam, x, info = run_project(dev, z, A, b, stage1=stage1)
     assert st == 0, (st, info.as_dict(m))
     z64, A64 = z.astype(np.float64), A.astype(np.float64)
     lam_ref, rinfo = P.solve_coupled_exact(z64, A64, b, 0.0, 1.0, C)
@@ -85,16 +87,21 @@ def test_project_coupled(dev, n, m, seed, feasible):
           "n=%d m=%d ref=%s info=%s" % (n, m, lam_ref, info.as_dict(m)))
 
 
-def test_project_coupled_stage1_accepts_single_row(dev):
-    """Only the volume row binds: Alg. 2 stage 1 finds it without Newton."""
+@pytest.mark.parametrize("stage1", [0, 1])
+def test_project_coupled_single_binding_row(dev, stage1):
+    """Only the volume row binds: Alg. 2's stage 1 accepts its single-row candidate without
+    Newton; from lam = 0 the Newton iteration reaches the same point."""
     rng = np.random.default_rng(11)
     n = 40000
     z = rng.uniform(0.0, 1.0, n).astype(np.float32)
     A = np.vstack([np.ones(n), rng.uniform(-1, 1, n), rng.uniform(-1, 1, n)]).astype(np.float32)
     b = np.array([0.3 * n, 1e6, 1e6])
-    st, lam, x, info = run_project(dev, z, A, b)
+    st, lam, x, info = run_project(dev, z, A, b, stage1=stage1)
     assert st == 0, info.as_dict(3)
-    assert info.stage == 1 and info.newton_iters == 0
+    if stage1:
+        assert info.stage == 1 and info.newton_iters == 0
+    else:
+        assert info.stage == 2 and info.newton_iters >= 1
     lam_ref, _ = P.solve_coupled_exact(z.astype(np.float64), A.astype(np.float64), b, 0.0, 1.0, C)
     x_ref = P.primal_from_dual(z.astype(np.float64), A.astype(np.float64), lam_ref, 0.0, 1.0)
     check(parity_errors(x, lam, x_ref, lam_ref, A, b, C, 0.0, 1.0), "stage 1")
@@ -112,14 +119,16 @@ def test_project_coupled_all_inactive(dev):
     assert np.array_equal(x, np.clip(z, 0, 1).astype(np.float64))
 
 
-@pytest.mark.parametrize("dims,infeasible", [((32, 16, 16), False), ((64, 32, 32), False),
-                                             ((32, 16, 16), True), (None, False), (None, True)])
-def test_step_config4(dev, dims, infeasible):
+@pytest.mark.parametrize("dims,infeasible,stage1", [((32, 16, 16), False, 0), ((64, 32, 32), False, 0),
+                                                    ((32, 16, 16), True, 0), ((32, 16, 16), False, 1),
+                                                    ((32, 16, 16), True, 1), (None, False, 0), (None, True, 0),
+                                                    (None, True, 1)])
+def test_step_config4(dev, dims, infeasible, stage1):
     import torch
     from paper_2511_13905_gb300 import binding
     cfg = inputs.config4(dims=dims, infeasible=infeasible)
     n, m = cfg["n"], cfg["m"]
-    h = binding.Handle(n, m, mode="coupled")
+    h = binding.Handle(n, m, mode="coupled", stage1=stage1)
     h.set_state(T(cfg["x_prev"], dev), T(cfg["g_prev"], dev), T(cfg["d_prev"], dev), cfg["t"])
     x = T(cfg["x"], dev)
     st, info = h.step(x, T(cfg["g"], dev), T(cfg["A"], dev), cfg["gval"], cfg["G"])
