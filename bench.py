@@ -244,7 +244,20 @@ def time_workload(wl, args, dev, stream, flush, probes, world=1, local_rank=0, e
     def T(a):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
 
+    # a problem small enough for one thread-block cluster: the library's autotuner picks
+    # the cluster's block share for one problem of this n (synthetic problems of its own,
+    # timed before this workload's timing); the handle is created under its choice
+    tuned = None
+    if cfg["mode"] != "coupled" and n <= (1 << 17):
+        st, share, share_ms = binding.autotune_batch(n, 1)
+        if st != binding.PGDTO_OK:
+            raise RuntimeError("pgdto_autotune_batch failed: %s" % st)
+        tuned = {"cluster_elems": share, "median_ms_synthetic": share_ms, "candidates": [1024, 2048, 4096, 8192],
+                 "how": "pgdto_autotune_batch(n, 1): 3 + 5 steps of a synthetic problem per candidate share, "
+                        "lowest median kept"}
     h = binding.Handle(n, m, seg=cfg.get("seg"))
+    if tuned is not None:
+        binding.autotune_reset()
     x0 = T(cfg["x"])
     x = x0.clone()
     g = T(cfg["g"])
@@ -335,6 +348,8 @@ def time_workload(wl, args, dev, stream, flush, probes, world=1, local_rank=0, e
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if tuned is not None:
+        res["autotune"] = tuned
     res["roofline"]["peak_source"] = ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                                       else "fallback")
 
