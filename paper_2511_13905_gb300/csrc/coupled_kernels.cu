@@ -23,6 +23,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <type_traits>
+
 #include "dev_common.cuh"
 #include "kernels.h"
 #include "step_common.cuh"
@@ -155,7 +157,11 @@ __device__ void cupd_after_trial(const CoupledArgs& a, const BlockScratch& sc, C
         rH = smin - b - two_c * H;
         SHs = two_c;
     }
-    const bool closed = down ? rL < 0.0 : (up && rH > 0.0);
+    // the closed form of a row violated even at its saturation bound needs the full pass's
+    // sums (stage 1); without them every violated row goes to the Newton iteration, which
+    // reaches the same regularised optimum
+    const bool full = a.stage1 && !a.lam_prev;
+    const bool closed = full && (down ? rL < 0.0 : (up && rH > 0.0));
     const bool search = row && finite && (up || down) && !closed;
     double q = 0.0;
     if (k == 0) q = rL / SLs;
@@ -285,7 +291,6 @@ __device__ void cupd_after_feasibility(const CoupledArgs& a, const BlockScratch&
     volatile CoupledBcast* bc = &ws->bc;
     volatile RowState* rows = ws->rows;
     volatile NewtonState* nt = &ws->nt;
-    const double two_c = a.two_c;
     const int nc = bc->ncand;
     int accepted = -1;
     for (int c = 0; c < nc && accepted < 0; ++c) {
@@ -790,26 +795,35 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
 #pragma unroll
         for (int j = 0; j < M; ++j) mx[2 * j] = mx[2 * j + 1] = mx[2 * M + j] = bsh[j] = bsl[j] = 0.0f;
         const int eqm = a.eq_mask;
-        auto rowsum = [&](float z, const float (&av)[M], float x) {
+        // Stage 1 (params.stage1 on a cold start) brackets each row's single-row search with
+        // the free-set curvature at 0, the row-minimising and row-maximising bound sums and the
+        // saturation bounds (a division per element and row); stage 2 alone needs only b_j and
+        // the rows' violation at lam = 0, so the lean variant of the pass sums those two
+        const bool full = a.stage1 && !a.lam_prev;
+        auto rowsum = [&](auto fullc, float z, const float (&av)[M], float x) {
+            constexpr bool F = decltype(fullc)::value;
             const bool fr = z >= lo && z <= hi;
             const float xc = clampf(z, lo, hi);
 #pragma unroll
             for (int j = 0; j < M; ++j) {
                 const float aj = av[j];
-                mx[2 * M + j] = fmaxf(mx[2 * M + j], fabsf(aj));
                 const float ph = aj * x;
                 const DF t = two_sum(bsh[j], ph);
                 bsh[j] = t.hi;
                 bsl[j] = __fadd_rn(bsl[j], __fadd_rn(t.lo, fmaf(aj, x, -ph)));
                 acc.f[5 * j + 1] = fmaf(aj, xc, acc.f[5 * j + 1]);
-                acc.f[5 * j + 2] = fr ? fmaf(aj, aj, acc.f[5 * j + 2]) : acc.f[5 * j + 2];
-                acc.f[5 * j + 3] += aj > 0.0f ? aj * lo : (aj < 0.0f ? aj * hi : 0.0f);
-                acc.f[5 * j + 4] += aj > 0.0f ? aj * hi : (aj < 0.0f ? aj * lo : 0.0f);
-                if (aj != 0.0f) {
-                    // saturation bounds: only used widened by 1e-5, so a fast division will do
-                    const float ra = __fdividef(1.0f, aj);
-                    mx[2 * j] = fmaxf(mx[2 * j], (aj > 0.0f ? z - lo : z - hi) * ra);
-                    if ((eqm >> j) & 1) mx[2 * j + 1] = fmaxf(mx[2 * j + 1], -(aj > 0.0f ? z - hi : z - lo) * ra);
+                if constexpr (F) {
+                    mx[2 * M + j] = fmaxf(mx[2 * M + j], fabsf(aj));
+                    acc.f[5 * j + 2] = fr ? fmaf(aj, aj, acc.f[5 * j + 2]) : acc.f[5 * j + 2];
+                    acc.f[5 * j + 3] += aj > 0.0f ? aj * lo : (aj < 0.0f ? aj * hi : 0.0f);
+                    acc.f[5 * j + 4] += aj > 0.0f ? aj * hi : (aj < 0.0f ? aj * lo : 0.0f);
+                    if (aj != 0.0f) {
+                        // saturation bounds: only used widened by 1e-5, so a fast division will do
+                        const float ra = __fdividef(1.0f, aj);
+                        mx[2 * j] = fmaxf(mx[2 * j], (aj > 0.0f ? z - lo : z - hi) * ra);
+                        if ((eqm >> j) & 1)
+                            mx[2 * j + 1] = fmaxf(mx[2 * j + 1], -(aj > 0.0f ? z - hi : z - lo) * ra);
+                    }
                 }
             }
         };
@@ -836,67 +850,74 @@ __global__ void __launch_bounds__(kThreads, 1) coupled_kernel(CoupledArgs a) {
             zh = z.hi;
             zl = z.lo;
         };
-        for_chunk<VEC>(
-            cb, ce,
-            [&](int64_t v) {
-                float4 A4[M];
-#pragma unroll
-                for (int j = 0; j < M; ++j) A4[j] = LD4L2(a.A + (int64_t)j * n, v);
-                if (a.proj) {
-                    float4 z = LD4L2(a.z_in, v);
-                    const float zz[4] = {z.x, z.y, z.z, z.w};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        float av[M];
-#pragma unroll
-                        for (int j = 0; j < M; ++j) av[j] = reinterpret_cast<const float*>(&A4[j])[q];
-                        rowsum(zz[q], av, 0.0f);
+        auto pass = [&](auto fullc) {
+            for_chunk<VEC>(
+                cb, ce,
+                [&](int64_t v) {
+                    float4 A4[M];
+    #pragma unroll
+                    for (int j = 0; j < M; ++j) A4[j] = LD4L2(a.A + (int64_t)j * n, v);
+                    if (a.proj) {
+                        float4 z = LD4L2(a.z_in, v);
+                        const float zz[4] = {z.x, z.y, z.z, z.w};
+    #pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            float av[M];
+    #pragma unroll
+                            for (int j = 0; j < M; ++j) av[j] = reinterpret_cast<const float*>(&A4[j])[q];
+                            rowsum(fullc, zz[q], av, 0.0f);
+                        }
+                    } else {
+                        float4 x = LD4(a.x, v), g = LD4(a.g, v);
+                        float4 dp = first ? make_float4(0.f, 0.f, 0.f, 0.f) : LD4(a.d_prev, v);
+                        float4 d, zh, zl;
+                        const float xx[4] = {x.x, x.y, x.z, x.w}, gg[4] = {g.x, g.y, g.z, g.w};
+                        const float pp[4] = {dp.x, dp.y, dp.z, dp.w};
+                        float dd[4], h4[4], l4[4];
+    #pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            trial(xx[q], gg[q], pp[q], dd[q], h4[q], l4[q]);
+                            float av[M];
+    #pragma unroll
+                            for (int j = 0; j < M; ++j) av[j] = reinterpret_cast<const float*>(&A4[j])[q];
+                            rowsum(fullc, h4[q], av, xx[q]);
+                        }
+                        d = make_float4(dd[0], dd[1], dd[2], dd[3]);
+                        zh = make_float4(h4[0], h4[1], h4[2], h4[3]);
+                        zl = make_float4(l4[0], l4[1], l4[2], l4[3]);
+                        __stcs(reinterpret_cast<float4*>(a.d_new) + v, d);
+                        reinterpret_cast<float4*>(a.z)[v] = zh;
+                        reinterpret_cast<float4*>(a.zlo)[v] = zl;
+                        __stcs(reinterpret_cast<float4*>(a.x_prev) + v, x);
+                        __stcs(reinterpret_cast<float4*>(a.g_prev) + v, g);
                     }
-                } else {
-                    float4 x = LD4(a.x, v), g = LD4(a.g, v);
-                    float4 dp = first ? make_float4(0.f, 0.f, 0.f, 0.f) : LD4(a.d_prev, v);
-                    float4 d, zh, zl;
-                    const float xx[4] = {x.x, x.y, x.z, x.w}, gg[4] = {g.x, g.y, g.z, g.w};
-                    const float pp[4] = {dp.x, dp.y, dp.z, dp.w};
-                    float dd[4], h4[4], l4[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        trial(xx[q], gg[q], pp[q], dd[q], h4[q], l4[q]);
-                        float av[M];
-#pragma unroll
-                        for (int j = 0; j < M; ++j) av[j] = reinterpret_cast<const float*>(&A4[j])[q];
-                        rowsum(h4[q], av, xx[q]);
+                    acc.tick();
+                },
+                [&](int64_t i) {
+                    float av[M];
+    #pragma unroll
+                    for (int j = 0; j < M; ++j) av[j] = a.A[(int64_t)j * n + i];
+                    if (a.proj) {
+                        rowsum(fullc, a.z_in[i], av, 0.0f);
+                    } else {
+                        const float x = a.x[i], g = a.g[i];
+                        float d, zh, zl;
+                        trial(x, g, first ? 0.0f : a.d_prev[i], d, zh, zl);
+                        a.d_new[i] = d;
+                        a.z[i] = zh;
+                        a.zlo[i] = zl;
+                        a.x_prev[i] = x;
+                        a.g_prev[i] = g;
+                        rowsum(fullc, zh, av, x);
                     }
-                    d = make_float4(dd[0], dd[1], dd[2], dd[3]);
-                    zh = make_float4(h4[0], h4[1], h4[2], h4[3]);
-                    zl = make_float4(l4[0], l4[1], l4[2], l4[3]);
-                    __stcs(reinterpret_cast<float4*>(a.d_new) + v, d);
-                    reinterpret_cast<float4*>(a.z)[v] = zh;
-                    reinterpret_cast<float4*>(a.zlo)[v] = zl;
-                    __stcs(reinterpret_cast<float4*>(a.x_prev) + v, x);
-                    __stcs(reinterpret_cast<float4*>(a.g_prev) + v, g);
-                }
-                acc.tick();
-            },
-            [&](int64_t i) {
-                float av[M];
-#pragma unroll
-                for (int j = 0; j < M; ++j) av[j] = a.A[(int64_t)j * n + i];
-                if (a.proj) {
-                    rowsum(a.z_in[i], av, 0.0f);
-                } else {
-                    const float x = a.x[i], g = a.g[i];
-                    float d, zh, zl;
-                    trial(x, g, first ? 0.0f : a.d_prev[i], d, zh, zl);
-                    a.d_new[i] = d;
-                    a.z[i] = zh;
-                    a.zlo[i] = zl;
-                    a.x_prev[i] = x;
-                    a.g_prev[i] = g;
-                    rowsum(zh, av, x);
-                }
-                acc.tick();
-            });
+                    acc.tick();
+                });
+        };
+        if (full) {
+            pass(std::true_type{});
+        } else {
+            pass(std::false_type{});
+        }
         acc.fold();
 #pragma unroll
         for (int j = 0; j < M; ++j) acc.d[5 * j] = df_add(acc.d[5 * j], fast_two_sum(bsh[j], bsl[j]));
