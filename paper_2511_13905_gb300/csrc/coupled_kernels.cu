@@ -100,8 +100,9 @@ size_t coupled_work_ctrl_bytes() { return sizeof(GridCtrl); }
 DeviceInfo* coupled_work_info(CoupledWork* ws) { return &ws->st.info; }
 
 // sc.tot layout of each pass
-//   B:   5 per row (a^T x_t, a^T clip(z), free curvature at 0, S_min, S_max), 2 maxima
-//        per row (the upper saturation bound, minus the lower one)
+//   B:   5 per row (a^T x_t, a^T clip(z), free curvature at 0, S_min, S_max), 3 maxima
+//        per row (the upper saturation bound, minus the lower one, max |a_j|); all but the
+//        first two sums are formed only when stage 1 runs
 //   S1:  2K per row
 //   F:   m per candidate row (sums of every row at that candidate)
 //   E:   [0, m) h sums a_j^T x, [m, 2m) sum |a_j x|, [2m, 2m + 10) J upper triangle
@@ -113,6 +114,23 @@ __device__ __forceinline__ int jidx(int j, int k) {  // row-major upper-triangle
 }
 
 // ----------------------------------------------------------------------- scalar updates
+
+// The Newton iteration's counters and tolerances before the first pass of a step.
+__device__ __forceinline__ void cnewton_reset(CoupledState* ws, const CoupledArgs& a) {
+    volatile NewtonState* nt = &ws->nt;
+    nt->iters = 0;
+    nt->how = 0;
+    nt->stage = 0;
+    nt->passes = 0;
+    nt->stall = 0;
+    nt->trial = 0;
+    nt->phi = INFINITY;
+    nt->fphi = INFINITY;
+    nt->fbase_phi = 0.0f;
+    nt->stale = 0;
+    nt->tol = 1e-8;  // relative tolerance of the line search (the next Newton step corrects)
+    nt->eq_mask = a.eq_mask;
+}
 
 // Phase B: inputs of the single-row searches (Alg. 2 stage 1), as for a single row; an
 // equality row (Sec. 3.2.4) with r(0) < 0 searches below 0 (see the single-row kernel).
@@ -129,9 +147,33 @@ __device__ void cupd_after_trial(const CoupledArgs& a, const BlockScratch& sc, C
     const double sf = df_to_double(sc.tot[5 * jj + 2]);
     const double smin = df_to_double(sc.tot[5 * jj + 3]);
     const double smax = df_to_double(sc.tot[5 * jj + 4]);
+    const bool eq = (a.eq_mask >> jj) & 1;
+    if (!(a.stage1 && !a.lam_prev)) {
+        // stage 2 comes next (from lam = 0 or the previous step's lam): b_j, the status, and
+        // whether any row is violated at lam = 0 are all it needs from this pass
+        const bool finite = isfinite(ax) && isfinite(r0s);
+        const double b = a.bconst[jj] + ax;
+        const double r0 = r0s - b;
+        const bool act = row && finite && (r0 > 0.0 || (eq && r0 < 0.0));
+        if (row && k == 0) {
+            ws->info.b[j] = b;
+            rows[j].reg = two_c;
+            store_row(&rows[j], b, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, r0, 0, 0, 0);
+            publish_lambda(bc, j, 0.0);
+        }
+        const unsigned any = __ballot_sync(kFull, act);
+        const unsigned bad = __ballot_sync(kFull, row && !finite);
+        if (lane == 0) {
+            int status = a.proj ? kOk : bc->status;
+            if (bad) status = kErrNonfinite;
+            bc->status = status;
+            bc->any_active = (status == kOk && any) ? 1 : 0;
+            cnewton_reset(ws, a);
+        }
+        return;
+    }
     const double lsat = (double)sc.totmax[2 * jj];
     const double lneg = -(double)sc.totmax[2 * jj + 1];
-    const bool eq = (a.eq_mask >> jj) & 1;
     const bool finite = isfinite(ax) && isfinite(r0s) && isfinite(sf) && isfinite(smin) && isfinite(smax);
     const double b = a.bconst[jj] + ax;
     const double r0 = r0s - b;
@@ -193,19 +235,7 @@ __device__ void cupd_after_trial(const CoupledArgs& a, const BlockScratch& sc, C
         if (bad) status = kErrNonfinite;
         bc->status = status;
         bc->any_active = (status == kOk && any) ? 1 : 0;
-        volatile NewtonState* nt = &ws->nt;
-        nt->iters = 0;
-        nt->how = 0;
-        nt->stage = 0;
-        nt->passes = 0;
-        nt->stall = 0;
-        nt->trial = 0;
-        nt->phi = INFINITY;
-        nt->fphi = INFINITY;
-        nt->fbase_phi = 0.0f;
-        nt->stale = 0;
-        nt->tol = 1e-8;  // relative tolerance of the line search (the next Newton step corrects)
-        nt->eq_mask = a.eq_mask;
+        cnewton_reset(ws, a);
     }
 }
 
