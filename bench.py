@@ -47,8 +47,8 @@ WORKLOADS = {
 KERNEL_SOURCES = ["paper_2511_13905_gb300/csrc/seg_kernels.cu", "paper_2511_13905_gb300/csrc/dev_common.cuh",
                   "paper_2511_13905_gb300/csrc/coupled_kernels.cu", "paper_2511_13905_gb300/csrc/step_common.cuh",
                   "paper_2511_13905_gb300/csrc/kernels.h"]
-DTYPE = ("f32 bulk streams; double-float (FP32 pairs) step scalars, brackets, roots and reductions; "
-         "f64 in the coupled m x m Newton solve and in the report")
+DTYPE = ("f32 bulk streams; double-float (FP32 pairs) step scalars, brackets, roots, reductions and the "
+         "coupled m x m Newton solve; f64 only in the report")
 TOL = 1e-6
 L2_BYTES = 126.5e6   # GB300 L2 (about 126 MB usable of the 129 MB quoted)
 
