@@ -905,6 +905,68 @@ def run_reference(args, rank, world):
     }
 
 
+def profile_steps(which, steps):
+    """Untimed steps of one workload, the driver of the ncu captures under profiles/: workloads
+    1, 3 and 4 step from the seeded state (reset before each step), workload 2 runs its
+    trajectory from t = 0, and "batched" runs the 256-instance batched step."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2511_13905_gb300 import binding, inputs
+    dev = torch.device("cuda", 0)
+
+    def T(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    if which == "batched":
+        cfgs = [inputs.config1(seed_offset=k) for k in range(256)]
+        hs = [binding.Handle(c["n"], 1) for c in cfgs]
+        x0 = [T(c["x"]) for c in cfgs]
+        xs = [t.clone() for t in x0]
+        gs, As = [T(c["g"]) for c in cfgs], [T(c["A"]) for c in cfgs]
+        prev = [(T(c["x_prev"]), T(c["g_prev"]), T(c["d_prev"])) for c in cfgs]
+        for _ in range(steps):
+            for k, c in enumerate(cfgs):
+                xs[k].copy_(x0[k])
+                hs[k].set_state(prev[k][0], prev[k][1], prev[k][2], c["t"])
+            st, _ = binding.step_many(hs, xs, gs, As, [c["gval"] for c in cfgs], [c["G"] for c in cfgs],
+                                      want_info=False)
+            if st != binding.PGDTO_OK:
+                raise RuntimeError("pgdto_step_many failed: %s" % st)
+        torch.cuda.synchronize()
+        print("profile-step batched: %d batched steps of 256 instances" % steps)
+        return
+    wl = int(which)
+    cfg = make_cfg(wl)
+    n, m = cfg["n"], cfg["m"]
+    h = binding.Handle(n, m, seg=cfg.get("seg"))
+    x = T(cfg["x"])
+    g = T(cfg["g"])
+    if wl == 2:
+        s_dev = T(cfg["s"]).double()
+        for _ in range(steps):
+            xd = x.double()
+            A = (-3.0 * xd * xd * s_dev).float().reshape(1, n)
+            gval = [float(torch.sum(s_dev * (1.0 - xd * xd * xd)).item())]
+            h.step(x, g, A, gval, cfg["G"], want_info=False)
+            if h.last_info()[0] not in (0, binding.PGDTO_NOT_CONVERGED):
+                raise RuntimeError("step failed")
+    else:
+        x0 = x.clone()
+        A = T(cfg["A"])
+        prev = (T(cfg["x_prev"]), T(cfg["g_prev"]), T(cfg["d_prev"]))
+        for _ in range(steps):
+            x.copy_(x0)
+            h.set_state(prev[0], prev[1], prev[2], cfg["t"])
+            h.step(x, g, A, cfg["gval"], cfg["G"], want_info=False)
+            if h.last_info()[0] not in (0, binding.PGDTO_NOT_CONVERGED):
+                raise RuntimeError("step failed")
+    torch.cuda.synchronize()
+    h.close()
+    print("profile-step %d: %d steps" % (wl, steps))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -922,7 +984,12 @@ def main():
     ap.add_argument("--serve-sessions", type=int, default=128)
     ap.add_argument("--serve-steps", type=int, default=16)
     ap.add_argument("--serve-nmax", type=int, default=4 << 20)
+    ap.add_argument("--profile-step", default=None, choices=["1", "2", "3", "4", "batched"],
+                    help="run --steps untimed steps of one workload (for an ncu capture) and print no bench line")
     args = ap.parse_args()
+    if args.profile_step is not None:
+        profile_steps(args.profile_step, args.steps)
+        return
     if args.warmup < 3:
         args.warmup = 3
     rank = int(os.environ.get("RANK", "0"))
