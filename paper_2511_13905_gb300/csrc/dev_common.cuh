@@ -137,7 +137,11 @@ __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
 
 __device__ __forceinline__ unsigned atom_add_relaxed_u32(unsigned* p, unsigned v) {
     unsigned old;
@@ -286,13 +290,13 @@ static __device__ __noinline__ bool grid_round_gather(GridCtrl* ctrl, Partials* 
     for (int i = tid; i < nm; i += blockDim.x) part->mx[i][blockIdx.x] = sc.totmax[i];
     __syncthreads();
     if (tid == 0) {
-        // release: the block's partials are visible to whoever observes this arrival
-        fence_acq_rel_gpu();
-        const unsigned old = atom_add_relaxed_u32(&ctrl->count, 1u);
+        // release: the block's partials (written before the barrier above) are visible to
+        // whoever observes this arrival; acquire: the last block to arrive reads the count
+        // every other block's arrival released, so it sees all of their partials
+        const unsigned old = atom_add_acq_rel_u32(&ctrl->count, 1u);
         const unsigned target = sc.gen + 1u;
         int ok = 1;
         if (old == (unsigned)(nb - 1)) {
-            fence_acq_rel_gpu();  // acquire: every other block's partials
             ctrl->count = 0u;
             st_release_u32(&ctrl->gen, target);  // orders the reset before the next round's arrivals
         } else {
